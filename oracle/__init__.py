@@ -1,0 +1,406 @@
+"""FP64 CPU oracle of the group-by-group far-zone solver.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import or call this package; the product
+path (the CUDA library and its Python binding) never does, and shares no code
+with it.  The oracle takes plain numpy inputs and duck-typed problem objects
+(attributes k, eta, a, lattice, G, box_ijk, nb, P, alpha, self_box_mode).
+
+What each function follows (paper sections / equations / algorithms):
+
+  dyad                  D(R), eq. 5 with psi from eq. 6 (C code, FP64)
+  site_positions        uniform dipole lattice of each box, §2.1 ("uniform separation")
+  aggregate             mapping to uniform basis functions, Alg. 1 (eq. 11 applied: x_b = P_b^T c_b)
+  dipole_field          fields at dipole sites, eq. 12 summed over sources as eq. 14,
+                        brute force one site pair at a time, far / near split of eq. 2
+  disaggregate          inverse mapping, Alg. 3 (r_b = P_b y_b)
+  far_matvec            Z^F c of eq. 2 by brute force
+  operator              alpha c + Z^N c + Z^F c (the synthetic system Z I = V of eq. 1)
+  coupling_block        translation matrix G_w of one displacement, eq. 13
+  far_matvec_grouped    Alg. 2 grouped by displacement: E_j += G_w P_i per far pair
+  gmres                 restarted GMRES without preconditioning (§5), FP64
+  plane_wave_rhs        unit plane-wave excitation (§5) tested with P: v = P e
+
+Parity status: every function above is pinned by the CPU tests in
+tests/test_oracle_pins.py (closed-form Hertzian dipole field, reciprocity,
+translation invariance, counts printed in §2.2, brute force vs grouped, dense
+LU vs GMRES, explicit pure-Python construction on a tiny case).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import time
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+
+FAR, NEAR, ALL = 1, 2, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the C part (gcc, OpenMP) in-tree."""
+    src = os.path.join(_HERE, "ie_oracle.c")
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(src):
+        return _SO
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _SO + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-o", tmp, src, "-lm"])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        d, i, i64, p = ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+        L.or_dyad.argtypes = [d, d, p, p]
+        L.or_site_positions.argtypes = [d, i, i, i64, p, p]
+        L.or_dipole_field.argtypes = [d, d, d, i, i, i64, p, p, i, i, i64, p, p]
+        L.or_coupling_block.argtypes = [d, d, d, i, p, p]
+        L.or_coupling_blocks.argtypes = [d, d, d, i, i64, p, p]
+        L.or_plane_wave.argtypes = [d, d, i, i, i64, p, i64, p, p, p]
+        L.or_num_threads.restype = i
+        _lib = L
+    return _lib
+
+
+def num_threads() -> int:
+    return int(_load().or_num_threads())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c128(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.complex128)
+
+
+# ---------------------------------------------------------------- eq. 5, eq. 6
+def dyad(k: float, eta: float, R) -> np.ndarray:
+    """Free-space dyadic Green's function D(R) (eq. 5, psi of eq. 6), 3x3 complex."""
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    out = np.zeros(9, dtype=np.complex128)
+    _load().or_dyad(k, eta, _ptr(R), _ptr(out))
+    return out.reshape(3, 3)
+
+
+def nu_of(p) -> int:
+    return 3 * p.lattice ** 3
+
+
+def site_positions(p) -> np.ndarray:
+    """(n_boxes, L^3, 3) dipole positions: box centre a(ijk + 1/2 - G/2) + cell-centred offset."""
+    ijk = np.ascontiguousarray(p.box_ijk, dtype=np.int32)
+    ns = p.lattice ** 3
+    pos = np.zeros((ijk.shape[0], ns, 3))
+    _load().or_site_positions(p.a, p.lattice, p.G, ijk.shape[0], _ptr(ijk), _ptr(pos))
+    return pos
+
+
+def _offsets(p) -> np.ndarray:
+    o = np.zeros(len(p.nb) + 1, dtype=np.int64)
+    np.cumsum(np.asarray(p.nb, dtype=np.int64), out=o[1:])
+    return o
+
+
+def _P_block(p, b: int) -> np.ndarray:
+    if p.P is None:
+        return np.eye(nu_of(p), dtype=np.complex128)
+    o = _offsets(p)
+    return p.P[o[b]:o[b + 1]]
+
+
+# ---------------------------------------------------------------- Alg. 1 / Alg. 3
+def aggregate(p, c) -> np.ndarray:
+    """Alg. 1: per box, x_b = P_b^T c_b.  c: [nrhs][n] -> X: [nrhs][n_boxes][192]."""
+    c = _c128(c).reshape(-1, int(np.sum(p.nb)))
+    nrhs = c.shape[0]
+    o = _offsets(p)
+    X = np.zeros((nrhs, len(p.nb), nu_of(p)), dtype=np.complex128)
+    for b in range(len(p.nb)):
+        X[:, b, :] = c[:, o[b]:o[b + 1]] @ _P_block(p, b)      # (P_b^T c_b)^T
+    return X
+
+
+def disaggregate(p, Y, boxes=None) -> np.ndarray:
+    """Alg. 3: per box, r_b = P_b y_b.  Y: [nrhs][len(boxes)][192] -> [nrhs][sum nb over boxes]."""
+    Y = _c128(Y)
+    boxes = np.arange(len(p.nb)) if boxes is None else np.asarray(boxes)
+    parts = [Y[:, i, :] @ _P_block(p, int(b)).T for i, b in enumerate(boxes)]
+    return np.concatenate(parts, axis=1)
+
+
+def basis_rows(p, boxes) -> np.ndarray:
+    """Indices into the basis vector of the listed boxes (in the listed order)."""
+    o = _offsets(p)
+    return np.concatenate([np.arange(o[b], o[b + 1]) for b in boxes])
+
+
+# ---------------------------------------------------------------- eq. 12-14, brute force
+def dipole_field(p, X, mode: int, targets=None) -> np.ndarray:
+    """Brute-force field at the dipole sites of the target boxes (eq. 12 summed as eq. 14).
+
+    X: [nrhs][n_boxes][192] dipole moments.  mode FAR / NEAR / ALL (one-box-buffer split).
+    Returns [nrhs][n_targets][192].
+    """
+    X = _c128(X)
+    nrhs, nbox, nu = X.shape
+    ijk = np.ascontiguousarray(p.box_ijk, dtype=np.int32)
+    targets = np.arange(nbox, dtype=np.int64) if targets is None else np.ascontiguousarray(targets, dtype=np.int64)
+    Y = np.zeros((nrhs, len(targets), nu), dtype=np.complex128)
+    L = _load()
+    for r in range(nrhs):
+        xr = np.ascontiguousarray(X[r])
+        yr = np.zeros((len(targets), nu), dtype=np.complex128)
+        L.or_dipole_field(p.k, p.eta, p.a, p.lattice, p.G, nbox, _ptr(ijk), _ptr(xr), mode,
+                          int(getattr(p, "self_box_mode", 0)), len(targets), _ptr(targets), _ptr(yr))
+        Y[r] = yr
+    return Y
+
+
+def far_matvec(p, c, targets=None) -> np.ndarray:
+    """Z^F c of eq. 2 by brute force: P (sum over far site pairs of D) P^T c.
+
+    Returns the rows of the target boxes ([nrhs][sum nb over targets]).
+    """
+    X = aggregate(p, c)
+    targets = np.arange(len(p.nb)) if targets is None else np.asarray(targets)
+    Y = dipole_field(p, X, FAR, targets)
+    return disaggregate(p, Y, targets)
+
+
+def operator(p, c, which: str = "full", targets=None) -> np.ndarray:
+    """Z c restricted to the target boxes' rows, brute force.
+
+    which: 'far'  -> Z^F c;  'near' -> alpha c + Z^N c (stored near part and self term);
+           'full' -> alpha c + Z^N c + Z^F c.
+    """
+    c = _c128(c).reshape(-1, int(np.sum(p.nb)))
+    targets = np.arange(len(p.nb)) if targets is None else np.asarray(targets)
+    X = aggregate(p, c)
+    mode = {"far": FAR, "near": NEAR, "full": ALL}[which]
+    Y = dipole_field(p, X, mode, targets)
+    out = disaggregate(p, Y, targets)
+    if which != "far":
+        out = out + p.alpha * c[:, basis_rows(p, targets)]
+    return out
+
+
+# ---------------------------------------------------------------- eq. 13, Alg. 2 grouped
+def coupling_block(p, d) -> np.ndarray:
+    """Translation matrix of box displacement d (test box = basis box + d), eq. 13."""
+    d = np.ascontiguousarray(d, dtype=np.int32)
+    nu = nu_of(p)
+    C = np.zeros((nu, nu), dtype=np.complex128)
+    _load().or_coupling_block(p.k, p.eta, p.a, p.lattice, _ptr(d), _ptr(C))
+    return C
+
+
+def coupling_blocks(p, ds) -> np.ndarray:
+    ds = np.ascontiguousarray(ds, dtype=np.int32).reshape(-1, 3)
+    nu = nu_of(p)
+    C = np.zeros((ds.shape[0], nu, nu), dtype=np.complex128)
+    _load().or_coupling_blocks(p.k, p.eta, p.a, p.lattice, ds.shape[0], _ptr(ds), _ptr(C))
+    return C
+
+
+def pair_groups(p, mode: int):
+    """Ordered box pairs (basis b -> test t) grouped by displacement d = ijk_t - ijk_b.
+
+    mode FAR: Chebyshev distance >= 2 (Alg. 2 test ||w|| >= 2a on the box lattice);
+    NEAR: <= 1 (with self_box_mode = 1 the d = 0 group is dropped); ALL: both.
+    Returns (ds (ng,3) int32, list of (src slots, dst slots)).
+    """
+    ijk = np.asarray(p.box_ijk, dtype=np.int64)
+    n = ijk.shape[0]
+    d = ijk[None, :, :] - ijk[:, None, :]           # d[b, t] = ijk_t - ijk_b
+    ch = np.abs(d).max(-1)
+    sel = np.zeros((n, n), dtype=bool)
+    if mode & FAR:
+        sel |= ch >= 2
+    if mode & NEAR:
+        near = ch <= 1
+        if int(getattr(p, "self_box_mode", 0)) == 1:
+            near &= ch != 0
+        sel |= near
+    b_idx, t_idx = np.nonzero(sel)
+    dd = d[b_idx, t_idx]
+    span = 2 * int(np.abs(dd).max(initial=0)) + 1
+    key = ((dd[:, 0] + span) * (2 * span + 1) + (dd[:, 1] + span)) * (2 * span + 1) + (dd[:, 2] + span)
+    order = np.argsort(key, kind="stable")
+    key, b_idx, t_idx, dd = key[order], b_idx[order], t_idx[order], dd[order]
+    starts = np.flatnonzero(np.r_[True, key[1:] != key[:-1]])
+    ends = np.r_[starts[1:], len(key)]
+    ds = dd[starts].astype(np.int32)
+    groups = [(b_idx[s:e], t_idx[s:e]) for s, e in zip(starts, ends)]
+    return ds, groups
+
+
+def dipole_field_grouped(p, X, mode: int, chunk: int = 256) -> np.ndarray:
+    """Alg. 2 with DGFA, grouped by displacement: for every pair, E_t += G_d P_b.
+
+    Each displacement's translation matrix (eq. 13) multiplies all of that
+    displacement's basis-box vectors at once (a library matmul).
+    """
+    X = _c128(X)
+    nrhs, nbox, nu = X.shape
+    ds, groups = pair_groups(p, mode)
+    Y = np.zeros_like(X)
+    for s in range(0, len(ds), chunk):
+        Cs = coupling_blocks(p, ds[s:s + chunk])
+        for i, (src, dst) in enumerate(groups[s:s + chunk]):
+            Y[:, dst, :] += np.einsum("uv,rnv->rnu", Cs[i], X[:, src, :], optimize=True)
+    return Y
+
+
+def far_matvec_grouped(p, c) -> np.ndarray:
+    return disaggregate(p, dipole_field_grouped(p, aggregate(p, c), FAR))
+
+
+def operator_grouped(p, c, which: str = "full") -> np.ndarray:
+    c = _c128(c).reshape(-1, int(np.sum(p.nb)))
+    mode = {"far": FAR, "near": NEAR, "full": ALL}[which]
+    out = disaggregate(p, dipole_field_grouped(p, aggregate(p, c), mode))
+    if which != "far":
+        out = out + p.alpha * c
+    return out
+
+
+# ---------------------------------------------------------------- excitation (§5)
+def plane_wave_fields(p, khat, pol) -> np.ndarray:
+    """Plane-wave samples at every dipole: [nrhs][n_boxes][192]."""
+    khat = np.ascontiguousarray(khat, dtype=np.float64).reshape(-1, 3)
+    pol = np.ascontiguousarray(pol, dtype=np.float64).reshape(-1, 3)
+    ijk = np.ascontiguousarray(p.box_ijk, dtype=np.int32)
+    e = np.zeros((khat.shape[0], ijk.shape[0], nu_of(p)), dtype=np.complex128)
+    _load().or_plane_wave(p.k, p.a, p.lattice, p.G, ijk.shape[0], _ptr(ijk), khat.shape[0],
+                          _ptr(khat), _ptr(pol), _ptr(e))
+    return e
+
+
+def plane_wave_rhs(p, khat, pol) -> np.ndarray:
+    """Excitation vector tested with the basis functions: v = P e, [nrhs][n]."""
+    return disaggregate(p, plane_wave_fields(p, khat, pol))
+
+
+# ---------------------------------------------------------------- GMRES (§5), FP64
+def gmres(matvec, b, restart: int = 50, tol: float = 1e-10, maxiter: int = 1000):
+    """Restarted GMRES(m), x0 = 0, no preconditioner, modified Gram-Schmidt twice,
+    Givens rotations on the Hessenberg matrix.  Stops when the recurrence residual
+    is <= tol * ||b||.  Returns (x, iterations, history of relative residuals)."""
+    b = _c128(b)
+    n = b.shape[0]
+    x = np.zeros(n, dtype=np.complex128)
+    bn = np.linalg.norm(b)
+    if bn == 0:
+        return x, 0, [0.0]
+    hist = []
+    it = 0
+    r = b.copy()
+    beta = np.linalg.norm(r)
+    hist.append(beta / bn)
+    while it < maxiter and beta > tol * bn:
+        V = np.zeros((restart + 1, n), dtype=np.complex128)
+        H = np.zeros((restart + 1, restart), dtype=np.complex128)
+        cs = np.zeros(restart, dtype=np.complex128)
+        sn = np.zeros(restart, dtype=np.complex128)
+        g = np.zeros(restart + 1, dtype=np.complex128)
+        g[0] = beta
+        V[0] = r / beta
+        j_done = 0
+        for j in range(restart):
+            w = matvec(V[j])
+            for _ in range(2):
+                for i in range(j + 1):
+                    h = np.vdot(V[i], w)
+                    H[i, j] += h
+                    w = w - h * V[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            if H[j + 1, j] != 0:
+                V[j + 1] = w / H[j + 1, j]
+            for i in range(j):
+                t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+                H[i + 1, j] = -np.conj(sn[i]) * H[i, j] + np.conj(cs[i]) * H[i + 1, j]
+                H[i, j] = t
+            # rotation [c s; -conj(s) c] with c real that zeroes H[j+1, j]
+            a_, b_ = H[j, j], H[j + 1, j]
+            den = np.sqrt(abs(a_) ** 2 + abs(b_) ** 2)
+            if den == 0:
+                cs[j], sn[j] = 1.0, 0.0
+            elif abs(a_) == 0:
+                cs[j], sn[j] = 0.0, np.conj(b_) / abs(b_)
+            else:
+                cs[j] = abs(a_) / den
+                sn[j] = (a_ / abs(a_)) * np.conj(b_) / den
+            H[j, j] = cs[j] * a_ + sn[j] * b_
+            H[j + 1, j] = 0.0
+            g[j + 1] = -np.conj(sn[j]) * g[j]
+            g[j] = cs[j] * g[j]
+            it += 1
+            j_done = j + 1
+            hist.append(abs(g[j + 1]) / bn)
+            if abs(g[j + 1]) <= tol * bn or it >= maxiter:
+                break
+        y = np.linalg.solve(np.triu(H[:j_done, :j_done]), g[:j_done])
+        x = x + V[:j_done].T @ y
+        r = b - matvec(x)
+        beta = np.linalg.norm(r)
+        hist[-1] = beta / bn
+    return x, it, hist
+
+
+# ---------------------------------------------------------------- small dense forms
+def dense_operator(p) -> np.ndarray:
+    """Z = alpha I + P D_off P^T as a dense matrix, assembled box pair by box pair
+    from the translation matrices (near pairs included, coincident dipoles excluded)."""
+    n = int(np.sum(p.nb))
+    o = _offsets(p)
+    Z = np.zeros((n, n), dtype=np.complex128)
+    ds, groups = pair_groups(p, ALL)
+    Cs = coupling_blocks(p, ds)
+    for i, (src, dst) in enumerate(groups):
+        for b, t in zip(src, dst):
+            Z[o[t]:o[t + 1], o[b]:o[b + 1]] += _P_block(p, t) @ Cs[i] @ _P_block(p, b).T
+    Z += p.alpha * np.eye(n)
+    return Z
+
+
+def operator_norm(p, iters: int = 30, seed: int = 7, matvec=None, log=None):
+    """sigma = ||P D_off P^T||_2 by power iteration on K^H K (K complex symmetric,
+    so K^H v = conj(K conj(v))).  Returns (sigma, history)."""
+    n = int(np.sum(p.nb))
+    g = np.random.Generator(np.random.PCG64(seed))
+    v = g.standard_normal(n) + 1j * g.standard_normal(n)
+    v /= np.linalg.norm(v)
+
+    if matvec is None:
+        class _K:
+            pass
+        q = _K()
+        for name in ("k", "eta", "a", "lattice", "G", "box_ijk", "nb", "P", "self_box_mode"):
+            setattr(q, name, getattr(p, name))
+        q.alpha = 0.0
+        K = lambda c: operator_grouped(q, c[None, :], "full")[0]  # noqa: E731
+    else:
+        K = matvec
+    hist = []
+    sigma = 0.0
+    for it in range(iters):
+        t0 = time.time()
+        w = K(v)
+        sigma = np.linalg.norm(w)
+        u = np.conj(K(np.conj(w)))
+        v = u / np.linalg.norm(u)
+        hist.append(float(sigma))
+        if log:
+            log(f"power it {it}: sigma {sigma:.6e} ({time.time() - t0:.1f}s)")
+    return float(sigma), hist

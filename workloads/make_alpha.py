@@ -1,0 +1,57 @@
+"""Freeze the self-term alpha of each workload with the FP64 oracle.
+
+alpha = alpha_rel * sigma, sigma = ||P D_off P^T||_2 estimated by power iteration
+(oracle.operator_norm), alpha_rel = 1.25, rounded to 3 significant digits.  With
+alpha > sigma the system matrix alpha I + P D_off P^T is nonsingular and GMRES
+contracts the residual by at least sigma/alpha per step.
+
+Usage: python workloads/make_alpha.py tiny shell16 [--iters N]
+Writes workloads/alpha.json (merged with what is there).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+import oracle  # noqa: E402
+import workloads as W  # noqa: E402
+
+ALPHA_REL = 1.25
+BUILDERS = {
+    "tiny": lambda: W.tiny(),
+    "shell16": lambda: W.shell16(),
+    "shell16_identity": lambda: W.shell16(identity=True),
+    "shell32": lambda: W.shell32(),
+}
+
+
+def sig3(x: float) -> float:
+    return float(f"{x:.3g}")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("names", nargs="+")
+    ap.add_argument("--iters", type=int, default=20)
+    args = ap.parse_args()
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "alpha.json")
+    for name in args.names:
+        p = BUILDERS[name]()
+        t0 = time.time()
+        sigma, hist = oracle.operator_norm(p, iters=args.iters, log=lambda s: print(name, s, flush=True))
+        table = json.load(open(path)) if os.path.exists(path) else {}
+        table[name] = dict(alpha=sig3(ALPHA_REL * sigma), sigma=sigma, alpha_rel=ALPHA_REL,
+                           iters=args.iters, history=hist, seconds=round(time.time() - t0, 1),
+                           method="oracle.operator_norm (FP64 power iteration on K^H K)")
+        with open(path, "w") as f:
+            json.dump(table, f, indent=1)
+        print(name, "alpha", table[name]["alpha"], flush=True)
+
+
+if __name__ == "__main__":
+    main()
