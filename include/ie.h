@@ -1,0 +1,237 @@
+/*
+ * ie.h — C ABI of libie, the GB300 (sm_103a) group-by-group far-zone solver.
+ *
+ * The library computes the matrix-vector product of an integral-equation system
+ * Z I = V (eq. 1) split by the one-box-buffer scheme into a stored near part and a
+ * far part (eq. 2), and solves the system with restarted GMRES (§5).  The far part
+ * runs the paper's three stages on every product:
+ *   1. mapping to uniform basis functions, x_b = P_b^T c_b        (Alg. 1, eq. 11)
+ *   2. translation, E_t += G_d x_b for every far box pair,
+ *      grouped by box displacement d = t - b                       (Alg. 2, eq. 13, eq. 14)
+ *   3. inverse mapping, r_t = P_t E_t                              (Alg. 3, eq. 17)
+ * with G_d built directly from the free-space dyadic Green's function (eq. 5, eq. 6).
+ *
+ * Geometry: boxes of edge `box_edge` on a G^3 grid, box (i,j,k) centred at
+ * box_edge*((i,j,k) + 1/2 - G/2); each box holds a 4x4x4 cell-centred lattice of
+ * x/y/z Hertzian dipoles (192 unknowns), site s = ix + 4 iy + 16 iz, unknown
+ * u = 3 s + component.  Two boxes are far when their Chebyshev distance is >= 2.
+ *
+ * Conventions for every call below:
+ *  - Vectors are caller-owned DEVICE buffers of complex64 (interleaved re, im
+ *    float32), laid out [rhs][n] where n = sum of nb over boxes, boxes in the
+ *    caller's box order, box b's nb_b coefficients contiguous.
+ *  - Dipole-space vectors are [rhs][n_boxes][192] complex64.
+ *  - All calls are stream-ordered on `stream` (a cudaStream_t passed as void*,
+ *    NULL = legacy default stream) and return without waiting, except
+ *    ie_plan_create, ie_plan_destroy and ie_solve, which synchronise it.
+ *  - A plan owns all of its device memory.  Nothing throws across the ABI; every
+ *    call returns an ie_status, and ie_last_error() gives a message for the
+ *    calling thread's last failure.
+ *  - Calls on one plan must not overlap in time on different streams (the plan's
+ *    scratch vectors are shared); distinct plans are independent.
+ */
+#ifndef IE_H_
+#define IE_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ie_plan_s *ie_plan;
+typedef struct ie_solver_s *ie_solver;
+
+typedef enum {
+    IE_OK = 0,
+    IE_ERR_INVALID = 1,        /* bad argument or geometry                          */
+    IE_ERR_OOM = 2,            /* device allocation failed                          */
+    IE_ERR_CUDA = 3,           /* a CUDA runtime call failed                        */
+    IE_ERR_NOT_CONVERGED = 4,  /* solve stopped at max_iters; best iterate written  */
+    IE_ERR_TIMEOUT = 5,        /* a bounded device wait gave up                     */
+    IE_ERR_UNSUPPORTED = 6     /* precision or option not prepared in this plan     */
+} ie_status;
+
+/* Arithmetic of the translation stage (stage 2).
+ *  FP32    plain path: FP32 coupling blocks, FP32 FMA, partial sums combined in FP64.
+ *  BF16X3  tcgen05 tensor cores, each FP32 operand split into bf16 hi + lo and the
+ *          three products hi*hi + hi*lo + lo*hi accumulated in FP32.
+ *  FP16X3  as BF16X3 with fp16 halves.
+ *  BF16X1  tcgen05, one bf16 product (hi*hi) — the cheapest, least accurate form. */
+typedef enum { IE_PREC_FP32 = 1, IE_PREC_BF16X3 = 2, IE_PREC_FP16X3 = 3, IE_PREC_BF16X1 = 4 } ie_prec;
+#define IE_PRECMASK(p) (1u << (unsigned)(p))
+
+/* Which part of Z a product applies. */
+typedef enum {
+    IE_FAR = 1,    /* Z^F c (three stages above)                                    */
+    IE_NEAR = 2,   /* alpha c + Z^N c (stored near blocks, eq. 2)                   */
+    IE_FULL = 3    /* alpha c + Z^N c + Z^F c                                       */
+} ie_which;
+
+typedef struct {
+    double k;              /* wavenumber (2 pi for wavelength 1)                       */
+    double eta;            /* intrinsic impedance                                      */
+    double box_edge;       /* a                                                        */
+    int lattice;           /* dipoles per box edge; must be 4                          */
+    int grid_n;            /* G (box centres, hence plane-wave phases, use it)         */
+    int n_boxes;           /* >= 1                                                     */
+    const int32_t *box_ijk;/* HOST, n_boxes x 3, unique, any order                     */
+    const int32_t *nb;     /* HOST, n_boxes basis counts in [1,192]; NULL iff P NULL   */
+    const double *P;       /* HOST, packed complex128 (re,im): box b's nb_b x 192
+                              row-major block follows box b-1's. NULL = identity
+                              mapping (nb = 192 per box, dipole unknowns directly).   */
+    double alpha;          /* self term of the synthetic system                        */
+    int self_box_mode;     /* 0: near part includes the box itself minus coincident
+                              dipoles; 1: the box itself is left out                   */
+    unsigned prec_mask;    /* IE_PRECMASK(...) of every precision the plan must serve  */
+    int max_rhs;           /* largest nrhs any later call will pass (>= 1)             */
+} ie_problem;
+
+typedef struct {
+    int n_boxes;
+    int64_t n;                 /* basis unknowns                                      */
+    int64_t n_far_pairs;       /* ordered (basis box, test box) far pairs             */
+    int64_t n_far_disp;        /* distinct far displacements (= coupling blocks)      */
+    int64_t n_near_pairs;      /* stored near blocks (self blocks included)           */
+    int64_t n_work_simt;       /* work items of the FP32 translation                  */
+    int64_t n_work_tc;         /* work items of the tensor-core translation           */
+    size_t device_bytes;       /* device memory the plan holds                        */
+    double plan_seconds;       /* host wall time of ie_plan_create                    */
+    double translate_ms;       /* with profiling on: summed device time of the
+                                  translation kernel (CUDA events on its stream)      */
+    int64_t translate_launches;/* with profiling on: launches timed                   */
+} ie_plan_stats;
+
+/* Build a plan: validate the geometry, group far box pairs by displacement, generate
+ * every far coupling block G_d (eq. 13) and the near blocks P_a G_{b-a} P_b^T on the
+ * device in FP64 arithmetic, stored in the layouts of the requested precisions.
+ * Host inputs are copied; they may be freed on return.  Synchronises `stream`.
+ * Errors: IE_ERR_INVALID (lattice != 4, n_boxes < 1, duplicate boxes, nb outside
+ * [1,192], P/nb mismatch, max_rhs < 1, empty prec_mask), IE_ERR_OOM, IE_ERR_CUDA. */
+ie_status ie_plan_create(const ie_problem *prob, void *stream, ie_plan *out);
+
+/* Device bytes ie_plan_create would allocate for `prob` (for admission control);
+ * host-only, no device work.  Errors: as ie_plan_create's validation. */
+ie_status ie_plan_footprint(const ie_problem *prob, size_t *bytes);
+
+ie_status ie_plan_stats_get(ie_plan plan, ie_plan_stats *out);
+
+/* Profiling of the translation kernel: with enable = 1 (counters reset), every
+ * translation launched outside stream capture is bracketed by CUDA events on its
+ * stream and its duration added to translate_ms (the call then waits for it). */
+ie_status ie_plan_profile(ie_plan plan, int enable);
+
+/* Release every device allocation of the plan (synchronises the device first). */
+ie_status ie_plan_destroy(ie_plan plan);
+
+/* y = op(c) for nrhs right-hand sides (op from `which`, translation arithmetic from
+ * `prec`).  c, y: device complex64 [nrhs][n]; y is overwritten; c and y must not
+ * alias.  Errors: IE_ERR_INVALID (null pointers, nrhs outside [1,max_rhs]),
+ * IE_ERR_UNSUPPORTED (prec not in the plan's prec_mask), IE_ERR_CUDA. */
+ie_status ie_matvec(ie_plan plan, int which, int prec, const void *c, void *y, int nrhs, void *stream);
+
+/* ---- the three far-zone stages and the near product, one call each ---------- */
+
+/* Stage 1 (Alg. 1): X[r][b][u] = sum_i P_b[i][u] c[r][o_b + i].  X: device complex64
+ * [nrhs][n_boxes][192]. */
+ie_status ie_aggregate(ie_plan plan, const void *c, void *X, int nrhs, void *stream);
+
+/* Stage 2 (Alg. 2): Y[r][t] = sum over far b of G_{t-b} X[r][b], in `prec`.
+ * X, Y: device complex64 [nrhs][n_boxes][192]; Y overwritten. */
+ie_status ie_translate(ie_plan plan, int prec, const void *X, void *Y, int nrhs, void *stream);
+
+/* Stage 3 (Alg. 3): r[r][o_b + i] = sum_u P_b[i][u] Y[r][b][u] (overwrites r). */
+ie_status ie_disaggregate(ie_plan plan, const void *Y, void *r, int nrhs, void *stream);
+
+/* Near product (eq. 2, stored Z^N) plus the self term: y = alpha c + Z^N c. */
+ie_status ie_near(ie_plan plan, const void *c, void *y, int nrhs, void *stream);
+
+/* Coupling blocks G_d for `nd` displacements d (HOST int32 nd x 3; any d, near or
+ * far; d = 0 has its coincident 3x3 diagonal blocks zeroed), written to the device
+ * buffer `out` as complex64 [nd][192][192] row-major (row = test unknown).  Uses
+ * the plan's k, eta and box edge; the plan's own store is not touched. */
+ie_status ie_coupling_blocks(ie_plan plan, const int32_t *d, int nd, void *out, void *stream);
+
+/* Plane-wave excitation tested with the basis functions (§5): v = P e with
+ * e[r][b][3s+a] = pol_r[a] exp(-j k khat_r . r_s).  khat, pol: HOST double nrhs x 3;
+ * v: device complex64 [nrhs][n]. */
+ie_status ie_rhs_plane_wave(ie_plan plan, const double *khat, const double *pol, int nrhs, void *v,
+                            void *stream);
+
+/* ---- GMRES ------------------------------------------------------------------ */
+
+typedef struct {
+    int restart;         /* m of GMRES(m) (default 50)                                  */
+    int max_iters;       /* total inner iterations allowed (default 1000)               */
+    double tol;          /* stop at ||v - Z c|| <= tol ||v|| per right-hand side        */
+    int prec;            /* translation arithmetic inside GMRES (default IE_PREC_FP32)  */
+    int refine;          /* 1: outer iterative refinement (see ie_solve)                */
+    int refine_prec;     /* arithmetic of the refinement residual (default FP32)        */
+    double inner_tol;    /* inner GMRES relative tolerance when refining (default 1e-3) */
+    int max_refine;      /* outer steps allowed (default 20)                            */
+} ie_solve_opts;
+
+typedef struct {
+    int iterations;      /* inner GMRES iterations (max over right-hand sides)          */
+    int matvecs;         /* operator applications (all precisions)                      */
+    int refinements;     /* outer refinement steps taken                                */
+    int converged;       /* 1 when every right-hand side met tol                        */
+    double relres;       /* max over right-hand sides of the final relative residual:
+                            the recurrence estimate without refinement, the FP64
+                            refinement residual with it                                 */
+    double seconds;      /* host wall time of the call                                  */
+} ie_solve_info;
+
+/* Fill `o` with the defaults above. */
+void ie_solve_opts_default(ie_solve_opts *o);
+
+/* Solve Z c = v for nrhs independent right-hand sides with restarted GMRES (§5):
+ * x0 = 0, Arnoldi by classical Gram-Schmidt applied twice with FP64 dot products,
+ * Givens rotations and the small least-squares solve in FP64, Krylov vectors in
+ * FP32 on the device.  With refine = 1, c is kept in FP64, each outer step forms
+ * r = v - Z c with `refine_prec` products and FP64 vector arithmetic, solves
+ * Z d = r with GMRES in `prec` to inner_tol and adds d, until ||r|| <= tol ||v||.
+ * v, c: device complex64 [nrhs][n]; c overwritten.  Synchronises `stream`.
+ * Returns IE_ERR_NOT_CONVERGED (with the best iterate in c and info filled) when
+ * the limits are reached first. */
+ie_status ie_solve(ie_plan plan, const void *v, void *c, int nrhs, const ie_solve_opts *opts,
+                   ie_solve_info *info, void *stream);
+
+/* ---- solver objects: the same GMRES with device-resident state, stepped
+ * without host synchronisation (for request loops that interleave many solves). */
+
+/* Allocate the device state of a GMRES(opts->restart) solve of up to nrhs
+ * right-hand sides on `plan` (refine must be 0). */
+ie_status ie_solver_create(ie_plan plan, int nrhs, const ie_solve_opts *opts, ie_solver *out);
+
+/* Device bytes ie_solver_create would allocate. */
+ie_status ie_solver_footprint(ie_plan plan, int nrhs, const ie_solve_opts *opts, size_t *bytes);
+
+/* Enqueue the start of a solve of Z c = v (x0 = 0); v and c must stay valid until
+ * the solve is finished.  Nothing waits. */
+ie_status ie_solver_start(ie_solver s, const void *v, void *c, void *stream);
+
+/* Enqueue `cycles` restart cycles (each up to `restart` iterations; kernels of a
+ * converged right-hand side do nothing) and the solution update.  Nothing waits. */
+ie_status ie_solver_advance(ie_solver s, int cycles, void *stream);
+
+/* Non-blocking: *done = 1 once everything enqueued on the solver has finished and
+ * every right-hand side converged or hit max_iters; then info is filled. */
+ie_status ie_solver_poll(ie_solver s, int *done, ie_solve_info *info);
+
+ie_status ie_solver_destroy(ie_solver s);
+
+/* ---- diagnostics -------------------------------------------------------------- */
+const char *ie_status_str(ie_status s);
+const char *ie_last_error(void);   /* thread-local; "" if none */
+const char *ie_version(void);
+
+/* Kernels this process has launched through libie so far: direct launches plus the
+ * kernel nodes of every replay of a captured GMRES cycle. */
+int64_t ie_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IE_H_ */

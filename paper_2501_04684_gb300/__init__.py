@@ -1,0 +1,314 @@
+"""Python binding of libie, the GB300 (sm_103a) group-by-group far-zone solver.
+
+Argument marshalling only: every function below forwards to the C ABI declared in
+include/ie.h (same names), passing device pointers of caller-owned torch tensors
+and the CUDA stream handle.  All arithmetic runs in libie's CUDA kernels; there is
+no CPU fallback, and importing the binding fails loudly when libie.so is missing.
+
+Vectors are complex64 CUDA tensors laid out [rhs][n] (basis space) or
+[rhs][n_boxes][192] (dipole space).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libie.so")
+
+IE_OK, IE_ERR_INVALID, IE_ERR_OOM, IE_ERR_CUDA, IE_ERR_NOT_CONVERGED, IE_ERR_TIMEOUT, IE_ERR_UNSUPPORTED = range(7)
+IE_PREC_FP32, IE_PREC_BF16X3, IE_PREC_FP16X3, IE_PREC_BF16X1 = 1, 2, 3, 4
+IE_FAR, IE_NEAR, IE_FULL = 1, 2, 3
+PREC_NAMES = {IE_PREC_FP32: "fp32", IE_PREC_BF16X3: "bf16x3", IE_PREC_FP16X3: "fp16x3", IE_PREC_BF16X1: "bf16x1"}
+
+EXPORTED = [
+    "ie_plan_create", "ie_plan_footprint", "ie_plan_stats_get", "ie_plan_destroy", "ie_matvec",
+    "ie_aggregate", "ie_translate", "ie_disaggregate", "ie_near", "ie_coupling_blocks", "ie_rhs_plane_wave",
+    "ie_solve_opts_default", "ie_solve", "ie_solver_create", "ie_solver_footprint", "ie_solver_start",
+    "ie_solver_advance", "ie_solver_poll", "ie_solver_destroy", "ie_status_str", "ie_last_error", "ie_version",
+    "ie_plan_profile", "ie_kernel_launches",
+]
+
+
+def precmask(*precs) -> int:
+    m = 0
+    for p in precs:
+        m |= 1 << p
+    return m
+
+
+class ie_problem(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_double), ("eta", ctypes.c_double), ("box_edge", ctypes.c_double),
+                ("lattice", ctypes.c_int), ("grid_n", ctypes.c_int), ("n_boxes", ctypes.c_int),
+                ("box_ijk", ctypes.c_void_p), ("nb", ctypes.c_void_p), ("P", ctypes.c_void_p),
+                ("alpha", ctypes.c_double), ("self_box_mode", ctypes.c_int), ("prec_mask", ctypes.c_uint),
+                ("max_rhs", ctypes.c_int)]
+
+
+class ie_plan_stats(ctypes.Structure):
+    _fields_ = [("n_boxes", ctypes.c_int), ("n", ctypes.c_int64), ("n_far_pairs", ctypes.c_int64),
+                ("n_far_disp", ctypes.c_int64), ("n_near_pairs", ctypes.c_int64), ("n_work_simt", ctypes.c_int64),
+                ("n_work_tc", ctypes.c_int64), ("device_bytes", ctypes.c_size_t), ("plan_seconds", ctypes.c_double),
+                ("translate_ms", ctypes.c_double), ("translate_launches", ctypes.c_int64)]
+
+
+class ie_solve_opts(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("max_iters", ctypes.c_int), ("tol", ctypes.c_double),
+                ("prec", ctypes.c_int), ("refine", ctypes.c_int), ("refine_prec", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("max_refine", ctypes.c_int)]
+
+
+class ie_solve_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("matvecs", ctypes.c_int), ("refinements", ctypes.c_int),
+                ("converged", ctypes.c_int), ("relres", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libie.so (built in-tree by __graft_entry__.build() / build.py)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libie CUDA library not built ({LIB_PATH} missing); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, u, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint, ctypes.c_double, ctypes.c_size_t
+    P = ctypes.POINTER
+    L.ie_plan_create.argtypes = [P(ie_problem), vp, P(vp)]
+    L.ie_plan_footprint.argtypes = [P(ie_problem), P(sz)]
+    L.ie_plan_stats_get.argtypes = [vp, P(ie_plan_stats)]
+    L.ie_plan_destroy.argtypes = [vp]
+    L.ie_plan_profile.argtypes = [vp, i]
+    L.ie_matvec.argtypes = [vp, i, i, vp, vp, i, vp]
+    L.ie_aggregate.argtypes = [vp, vp, vp, i, vp]
+    L.ie_translate.argtypes = [vp, i, vp, vp, i, vp]
+    L.ie_disaggregate.argtypes = [vp, vp, vp, i, vp]
+    L.ie_near.argtypes = [vp, vp, vp, i, vp]
+    L.ie_coupling_blocks.argtypes = [vp, vp, i, vp, vp]
+    L.ie_rhs_plane_wave.argtypes = [vp, vp, vp, i, vp, vp]
+    L.ie_solve_opts_default.argtypes = [P(ie_solve_opts)]
+    L.ie_solve_opts_default.restype = None
+    L.ie_solve.argtypes = [vp, vp, vp, i, P(ie_solve_opts), P(ie_solve_info), vp]
+    L.ie_solver_create.argtypes = [vp, i, P(ie_solve_opts), P(vp)]
+    L.ie_solver_footprint.argtypes = [vp, i, P(ie_solve_opts), P(sz)]
+    L.ie_solver_start.argtypes = [vp, vp, vp, vp]
+    L.ie_solver_advance.argtypes = [vp, i, vp]
+    L.ie_solver_poll.argtypes = [vp, P(i), P(ie_solve_info)]
+    L.ie_solver_destroy.argtypes = [vp]
+    L.ie_status_str.argtypes = [i]
+    L.ie_status_str.restype = ctypes.c_char_p
+    L.ie_last_error.restype = ctypes.c_char_p
+    L.ie_version.restype = ctypes.c_char_p
+    L.ie_kernel_launches.restype = ctypes.c_int64
+    for name in EXPORTED:          # every declared symbol must resolve
+        getattr(L, name)
+    _lib = L
+    return L
+
+
+class IEError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        L = lib()
+        self.status = status
+        msg = L.ie_last_error().decode(errors="replace")
+        super().__init__(f"{where}: {L.ie_status_str(status).decode()} ({msg})")
+
+
+def _check(status: int, where: str, allow=(IE_OK,)):
+    if status not in allow:
+        raise IEError(status, where)
+    return status
+
+
+def _ptr(t) -> int:
+    """Device (or host numpy) pointer of a tensor / array."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return stream
+
+
+def make_problem(k, eta, box_edge, grid_n, box_ijk, nb, P, alpha, prec_mask, max_rhs=1, self_box_mode=0,
+                 lattice=4):
+    """Build an ie_problem struct; keeps the host arrays alive on the returned object."""
+    ijk = np.ascontiguousarray(box_ijk, dtype=np.int32)
+    nb_a = None if nb is None else np.ascontiguousarray(nb, dtype=np.int32)
+    P_a = None if P is None else np.ascontiguousarray(np.asarray(P, dtype=np.complex128))
+    pr = ie_problem(k=k, eta=eta, box_edge=box_edge, lattice=lattice, grid_n=grid_n, n_boxes=ijk.shape[0],
+                    box_ijk=ijk.ctypes.data, nb=None if nb_a is None else nb_a.ctypes.data,
+                    P=None if P_a is None else P_a.ctypes.data, alpha=alpha, self_box_mode=self_box_mode,
+                    prec_mask=prec_mask, max_rhs=max_rhs)
+    pr._keep = (ijk, nb_a, P_a)
+    return pr
+
+
+def problem_from(p, prec_mask: int, max_rhs: int = 1):
+    """ie_problem from a workloads.Problem-like object."""
+    return make_problem(p.k, p.eta, p.a, p.G, p.box_ijk, None if p.P is None else p.nb, p.P, p.alpha, prec_mask,
+                        max_rhs, getattr(p, "self_box_mode", 0), p.lattice)
+
+
+# ---------------------------------------------------------------- C ABI, same names
+def ie_plan_create(problem: ie_problem, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().ie_plan_create(ctypes.byref(problem), _stream(stream), ctypes.byref(h)), "ie_plan_create")
+    return h.value
+
+
+def ie_plan_footprint(problem: ie_problem) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().ie_plan_footprint(ctypes.byref(problem), ctypes.byref(b)), "ie_plan_footprint")
+    return b.value
+
+
+def ie_plan_stats_get(plan: int) -> dict:
+    s = ie_plan_stats()
+    _check(lib().ie_plan_stats_get(plan, ctypes.byref(s)), "ie_plan_stats_get")
+    return {f: getattr(s, f) for f, _ in s._fields_}
+
+
+def ie_plan_profile(plan: int, enable: bool) -> None:
+    _check(lib().ie_plan_profile(plan, 1 if enable else 0), "ie_plan_profile")
+
+
+def ie_plan_destroy(plan: int) -> None:
+    _check(lib().ie_plan_destroy(plan), "ie_plan_destroy")
+
+
+def ie_matvec(plan, which, prec, c, y, nrhs, stream=None):
+    return _check(lib().ie_matvec(plan, which, prec, _ptr(c), _ptr(y), nrhs, _stream(stream)), "ie_matvec")
+
+
+def ie_aggregate(plan, c, X, nrhs, stream=None):
+    return _check(lib().ie_aggregate(plan, _ptr(c), _ptr(X), nrhs, _stream(stream)), "ie_aggregate")
+
+
+def ie_translate(plan, prec, X, Y, nrhs, stream=None):
+    return _check(lib().ie_translate(plan, prec, _ptr(X), _ptr(Y), nrhs, _stream(stream)), "ie_translate")
+
+
+def ie_disaggregate(plan, Y, r, nrhs, stream=None):
+    return _check(lib().ie_disaggregate(plan, _ptr(Y), _ptr(r), nrhs, _stream(stream)), "ie_disaggregate")
+
+
+def ie_near(plan, c, y, nrhs, stream=None):
+    return _check(lib().ie_near(plan, _ptr(c), _ptr(y), nrhs, _stream(stream)), "ie_near")
+
+
+def ie_coupling_blocks(plan, d, out, stream=None):
+    d = np.ascontiguousarray(d, dtype=np.int32).reshape(-1, 3)
+    return _check(lib().ie_coupling_blocks(plan, d.ctypes.data, d.shape[0], _ptr(out), _stream(stream)),
+                  "ie_coupling_blocks")
+
+
+def ie_rhs_plane_wave(plan, khat, pol, v, stream=None):
+    khat = np.ascontiguousarray(khat, dtype=np.float64).reshape(-1, 3)
+    pol = np.ascontiguousarray(pol, dtype=np.float64).reshape(-1, 3)
+    return _check(lib().ie_rhs_plane_wave(plan, khat.ctypes.data, pol.ctypes.data, khat.shape[0], _ptr(v),
+                                          _stream(stream)), "ie_rhs_plane_wave")
+
+
+def solve_opts(**kw) -> ie_solve_opts:
+    o = ie_solve_opts()
+    lib().ie_solve_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def ie_solve(plan, v, c, nrhs, opts: ie_solve_opts | None = None, stream=None):
+    """Returns (status, info dict); IE_ERR_NOT_CONVERGED is returned, not raised."""
+    info = ie_solve_info()
+    o = opts or solve_opts()
+    st = lib().ie_solve(plan, _ptr(v), _ptr(c), nrhs, ctypes.byref(o), ctypes.byref(info), _stream(stream))
+    _check(st, "ie_solve", allow=(IE_OK, IE_ERR_NOT_CONVERGED))
+    return st, {f: getattr(info, f) for f, _ in info._fields_}
+
+
+def ie_solver_create(plan, nrhs, opts: ie_solve_opts | None = None) -> int:
+    h = ctypes.c_void_p()
+    o = opts or solve_opts()
+    _check(lib().ie_solver_create(plan, nrhs, ctypes.byref(o), ctypes.byref(h)), "ie_solver_create")
+    return h.value
+
+
+def ie_solver_footprint(plan, nrhs, opts: ie_solve_opts | None = None) -> int:
+    b = ctypes.c_size_t()
+    o = opts or solve_opts()
+    _check(lib().ie_solver_footprint(plan, nrhs, ctypes.byref(o), ctypes.byref(b)), "ie_solver_footprint")
+    return b.value
+
+
+def ie_solver_start(solver, v, c, stream=None):
+    return _check(lib().ie_solver_start(solver, _ptr(v), _ptr(c), _stream(stream)), "ie_solver_start")
+
+
+def ie_solver_advance(solver, cycles, stream=None):
+    return _check(lib().ie_solver_advance(solver, cycles, _stream(stream)), "ie_solver_advance")
+
+
+def ie_solver_poll(solver):
+    done = ctypes.c_int()
+    info = ie_solve_info()
+    _check(lib().ie_solver_poll(solver, ctypes.byref(done), ctypes.byref(info)), "ie_solver_poll")
+    return bool(done.value), {f: getattr(info, f) for f, _ in info._fields_}
+
+
+def ie_solver_destroy(solver):
+    return _check(lib().ie_solver_destroy(solver), "ie_solver_destroy")
+
+
+def ie_kernel_launches() -> int:
+    return int(lib().ie_kernel_launches())
+
+
+def ie_version() -> str:
+    return lib().ie_version().decode()
+
+
+class Plan:
+    """Owning wrapper of an ie_plan handle."""
+
+    def __init__(self, problem: ie_problem, stream=None):
+        self.problem = problem
+        self.handle = ie_plan_create(problem, stream)
+        self.stats = ie_plan_stats_get(self.handle)
+
+    @property
+    def n(self) -> int:
+        return int(self.stats["n"])
+
+    @property
+    def n_boxes(self) -> int:
+        return int(self.stats["n_boxes"])
+
+    def close(self):
+        if self.handle:
+            ie_plan_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

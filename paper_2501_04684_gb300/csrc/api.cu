@@ -1,0 +1,628 @@
+// libie C ABI: plan construction (geometry, one-box-buffer split, displacement
+// grouping, coupling-block and near-block generation) and the products.
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <algorithm>
+#include <atomic>
+#include <unordered_set>
+
+#include "ie_internal.h"
+
+namespace ie {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+const char *last_error() { return g_err; }
+
+static std::atomic<int64_t> g_launches{0};
+static thread_local int g_capture_depth = 0;
+void count_launches(int64_t n) {
+    if (g_capture_depth == 0) g_launches += n;
+}
+void capture_begin() { g_capture_depth++; }
+void capture_end() { g_capture_depth--; }
+
+ie_status dalloc(ie_plan p, void **ptr, size_t bytes) {
+    *ptr = nullptr;
+    if (bytes == 0) return IE_OK;
+    cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? IE_ERR_OOM : IE_ERR_CUDA;
+    }
+    p->allocs.push_back(*ptr);
+    p->bytes += bytes;
+    return IE_OK;
+}
+
+ie_status prepare_translate_simt();
+ie_status prepare_translate_tc();
+
+ie_status prepare_kernels() {
+    IE_TRY(prepare_translate_simt());
+    IE_TRY(prepare_translate_tc());
+    return IE_OK;
+}
+
+namespace {
+
+bool wants_tc(unsigned mask) {
+    return mask & (IE_PRECMASK(IE_PREC_BF16X3) | IE_PRECMASK(IE_PREC_FP16X3) | IE_PRECMASK(IE_PREC_BF16X1));
+}
+bool wants_bf16(unsigned mask) {
+    return mask & (IE_PRECMASK(IE_PREC_BF16X3) | IE_PRECMASK(IE_PREC_BF16X1));
+}
+bool wants_fp16(unsigned mask) { return mask & IE_PRECMASK(IE_PREC_FP16X3); }
+
+ie_status validate(const ie_problem *pr) {
+    if (!pr) return set_error("null problem"), IE_ERR_INVALID;
+    if (pr->lattice != kLattice) return set_error("lattice must be 4 (got %d)", pr->lattice), IE_ERR_INVALID;
+    if (pr->n_boxes < 1) return set_error("n_boxes must be >= 1"), IE_ERR_INVALID;
+    if (!pr->box_ijk) return set_error("box_ijk is null"), IE_ERR_INVALID;
+    if ((pr->P == nullptr) != (pr->nb == nullptr))
+        return set_error("P and nb must both be given or both be null"), IE_ERR_INVALID;
+    if (pr->max_rhs < 1 || pr->max_rhs > 64) return set_error("max_rhs must be in [1, 64]"), IE_ERR_INVALID;
+    if (!(pr->k > 0) || !(pr->box_edge > 0) || !(pr->eta > 0))
+        return set_error("k, eta and box_edge must be positive"), IE_ERR_INVALID;
+    unsigned known = IE_PRECMASK(IE_PREC_FP32) | IE_PRECMASK(IE_PREC_BF16X3) | IE_PRECMASK(IE_PREC_FP16X3) |
+                     IE_PRECMASK(IE_PREC_BF16X1);
+    if (pr->prec_mask == 0 || (pr->prec_mask & ~known)) return set_error("bad prec_mask"), IE_ERR_INVALID;
+    if (pr->self_box_mode != 0 && pr->self_box_mode != 1) return set_error("self_box_mode must be 0 or 1"), IE_ERR_INVALID;
+    if (pr->nb)
+        for (int b = 0; b < pr->n_boxes; ++b)
+            if (pr->nb[b] < 1 || pr->nb[b] > kNU)
+                return set_error("nb[%d] = %d outside [1,192]", b, pr->nb[b]), IE_ERR_INVALID;
+    for (int b = 0; b < pr->n_boxes; ++b)
+        for (int c = 0; c < 3; ++c) {
+            int v = pr->box_ijk[3 * b + c];
+            if (v < -(1 << 20) || v > (1 << 20)) return set_error("box index out of range"), IE_ERR_INVALID;
+        }
+    return IE_OK;
+}
+
+// Dense lookup of the occupied boxes over their bounding box.
+struct BoxGrid {
+    int lo[3], ext[3];
+    std::vector<int32_t> slot;
+    int at(int x, int y, int z) const {
+        x -= lo[0], y -= lo[1], z -= lo[2];
+        if (x < 0 || y < 0 || z < 0 || x >= ext[0] || y >= ext[1] || z >= ext[2]) return -1;
+        return slot[((size_t)x * ext[1] + y) * ext[2] + z];
+    }
+};
+
+ie_status build_grid(const ie_problem *pr, BoxGrid &g) {
+    for (int c = 0; c < 3; ++c) {
+        int lo = pr->box_ijk[c], hi = lo;
+        for (int b = 0; b < pr->n_boxes; ++b) {
+            lo = std::min(lo, (int)pr->box_ijk[3 * b + c]);
+            hi = std::max(hi, (int)pr->box_ijk[3 * b + c]);
+        }
+        g.lo[c] = lo;
+        g.ext[c] = hi - lo + 1;
+    }
+    size_t cells = (size_t)g.ext[0] * g.ext[1] * g.ext[2];
+    if (cells > ((size_t)1 << 28)) return set_error("box bounding grid too large"), IE_ERR_INVALID;
+    g.slot.assign(cells, -1);
+    for (int b = 0; b < pr->n_boxes; ++b) {
+        const int32_t *q = pr->box_ijk + 3 * b;
+        size_t i = ((size_t)(q[0] - g.lo[0]) * g.ext[1] + (q[1] - g.lo[1])) * g.ext[2] + (q[2] - g.lo[2]);
+        if (g.slot[i] != -1) return set_error("duplicate box (%d,%d,%d)", q[0], q[1], q[2]), IE_ERR_INVALID;
+        g.slot[i] = b;
+    }
+    return IE_OK;
+}
+
+// Far pairs (Chebyshev distance >= 2) by counting sort on the displacement.
+struct FarGroups {
+    std::vector<int32_t> disp;       // n_d x 3
+    std::vector<int64_t> start;      // n_d + 1
+    std::vector<int32_t> src, dst;   // sorted by displacement, then source
+};
+
+void far_groups(const ie_problem *pr, const BoxGrid &g, bool fill, FarGroups &out, int64_t &npairs, int64_t &nd) {
+    int span[3] = {2 * g.ext[0] - 1, 2 * g.ext[1] - 1, 2 * g.ext[2] - 1};
+    size_t nkeys = (size_t)span[0] * span[1] * span[2];
+    std::vector<int64_t> count(nkeys + 1, 0);
+    const int32_t *ijk = pr->box_ijk;
+    int n = pr->n_boxes;
+    auto key = [&](int dx, int dy, int dz) {
+        return ((size_t)(dx + g.ext[0] - 1) * span[1] + (dy + g.ext[1] - 1)) * span[2] + (dz + g.ext[2] - 1);
+    };
+    for (int b = 0; b < n; ++b)
+        for (int t = 0; t < n; ++t) {
+            int dx = ijk[3 * t] - ijk[3 * b], dy = ijk[3 * t + 1] - ijk[3 * b + 1], dz = ijk[3 * t + 2] - ijk[3 * b + 2];
+            int ch = std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz)));
+            if (ch >= 2) count[key(dx, dy, dz)]++;
+        }
+    npairs = 0;
+    nd = 0;
+    for (size_t k = 0; k < nkeys; ++k)
+        if (count[k]) {
+            npairs += count[k];
+            nd++;
+        }
+    if (!fill) return;
+    out.disp.resize(3 * nd);
+    out.start.resize(nd + 1);
+    std::vector<int64_t> pos(nkeys, -1);
+    int64_t s = 0, di = 0;
+    for (size_t k = 0; k < nkeys; ++k)
+        if (count[k]) {
+            int dz = (int)(k % span[2]) - (g.ext[2] - 1);
+            int dy = (int)((k / span[2]) % span[1]) - (g.ext[1] - 1);
+            int dx = (int)(k / ((size_t)span[2] * span[1])) - (g.ext[0] - 1);
+            out.disp[3 * di] = dx;
+            out.disp[3 * di + 1] = dy;
+            out.disp[3 * di + 2] = dz;
+            out.start[di] = s;
+            pos[k] = s;
+            s += count[k];
+            di++;
+        }
+    out.start[nd] = s;
+    out.src.resize(npairs);
+    out.dst.resize(npairs);
+    for (int b = 0; b < n; ++b)
+        for (int t = 0; t < n; ++t) {
+            int dx = ijk[3 * t] - ijk[3 * b], dy = ijk[3 * t + 1] - ijk[3 * b + 1], dz = ijk[3 * t + 2] - ijk[3 * b + 2];
+            int ch = std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz)));
+            if (ch >= 2) {
+                int64_t &p = pos[key(dx, dy, dz)];
+                out.src[p] = b;
+                out.dst[p] = t;
+                p++;
+            }
+        }
+}
+
+// Near pairs per target box a: sources b with Chebyshev distance <= 1.
+void near_lists(const ie_problem *pr, const BoxGrid &g, const std::vector<int32_t> &nb, std::vector<int32_t> &start,
+                std::vector<int32_t> &src, std::vector<int64_t> &boff, int64_t &elems) {
+    int n = pr->n_boxes;
+    start.assign(n + 1, 0);
+    src.clear();
+    boff.clear();
+    elems = 0;
+    for (int a = 0; a < n; ++a) {
+        start[a] = (int32_t)src.size();
+        const int32_t *q = pr->box_ijk + 3 * a;
+        for (int ex = -1; ex <= 1; ++ex)
+            for (int ey = -1; ey <= 1; ++ey)
+                for (int ez = -1; ez <= 1; ++ez) {
+                    if (pr->self_box_mode == 1 && ex == 0 && ey == 0 && ez == 0) continue;
+                    int b = g.at(q[0] - ex, q[1] - ey, q[2] - ez);
+                    if (b < 0) continue;
+                    src.push_back(b);
+                    boff.push_back(elems);
+                    elems += (int64_t)nb[a] * nb[b];
+                }
+    }
+    start[n] = (int32_t)src.size();
+}
+
+size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, int64_t nnear, int64_t near_elems) {
+    size_t b = 0;
+    auto add = [&](size_t x) { b += (x + 255) / 256 * 256; };
+    int64_t nbox = pr->n_boxes;
+    if (pr->P) add((size_t)n * kNU * sizeof(float2));
+    add(nbox * sizeof(int32_t));
+    add((nbox + 1) * sizeof(int64_t));
+    add(nbox * 3 * sizeof(int32_t));
+    add(nd * 3 * sizeof(int32_t));
+    add(npairs * sizeof(int32_t));
+    add(npairs * sizeof(int32_t));
+    add((size_t)nd * kNU * kNU * sizeof(float2));
+    if (wants_bf16(pr->prec_mask)) add((size_t)nd * kTcDispElems * sizeof(uint16_t));
+    if (wants_fp16(pr->prec_mask)) {
+        add((size_t)nd * kTcDispElems * sizeof(uint16_t));
+        add(nd * sizeof(int32_t));
+    }
+    add((nbox + 1) * sizeof(int32_t));
+    add(nnear * sizeof(int32_t));
+    add(nnear * sizeof(int64_t));
+    add(near_elems * sizeof(float2));
+    size_t col = (size_t)pr->max_rhs * nbox;
+    add(col * kNU * sizeof(float2));                       // X
+    add((size_t)kSlabs * col * kNU * sizeof(float2));      // slabs
+    if (wants_tc(pr->prec_mask)) {
+        add(2 * col * 2 * kNU * sizeof(uint16_t));
+        add(col * sizeof(int32_t));
+    }
+    add(sizeof(int) * 4);
+    add((size_t)pr->max_rhs * n * sizeof(float2));         // tmp
+    // work lists (generous: one item per pair per precision family)
+    add((size_t)(npairs / 8 + nd + 1) * sizeof(WorkItem) * 4);
+    return b;
+}
+
+}  // namespace
+
+// Work list of one translation kernel for `nrhs`: every displacement group cut into
+// runs of at most (tile columns / nrhs) pairs; the tensor-core list repeats each run
+// for its three M-blocks and orders runs by size (largest first) for the persistent
+// kernel's static round-robin.
+ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out) {
+    auto &cache = tc ? p->tc_work : p->simt_work;
+    auto it = cache.find(nrhs);
+    if (it != cache.end()) {
+        *out = &it->second;
+        return IE_OK;
+    }
+    int cols = tc ? tc_tile_columns() : simt_tile_columns();
+    int per = cols / nrhs;
+    if (per < 1) return set_error("nrhs %d exceeds the tile width %d", nrhs, cols), IE_ERR_INVALID;
+    std::vector<WorkItem> items;
+    for (int64_t d = 0; d < p->n_far_disp; ++d) {
+        int64_t s = p->h_gstart[d], e = p->h_gstart[d + 1];
+        for (int64_t q = s; q < e; q += per) {
+            int np = (int)std::min<int64_t>(per, e - q);
+            if (tc) {
+                for (int mb = 0; mb < 3; ++mb) items.push_back({(int32_t)d, (int32_t)q, np, mb});
+            } else {
+                items.push_back({(int32_t)d, (int32_t)q, np, 0});
+            }
+        }
+    }
+    if (tc)
+        std::stable_sort(items.begin(), items.end(),
+                         [](const WorkItem &a, const WorkItem &b) { return a.npairs > b.npairs; });
+    WorkList wl;
+    wl.n = (int64_t)items.size();
+    if (wl.n) {
+        IE_TRY(dalloc_t(p, &wl.d_items, items.size()));
+        IE_CK(cudaMemcpy(wl.d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice));
+    }
+    if (tc)
+        p->n_work_tc = wl.n;
+    else
+        p->n_work_simt = wl.n;
+    cache[nrhs] = wl;
+    *out = &cache[nrhs];
+    return IE_OK;
+}
+
+ie_status translate_timed(ie_plan p, int prec, const float2 *X, float2 *Yslab, int nrhs, cudaStream_t st,
+                          const int *gate) {
+    bool timed = false;
+    if (p->profile) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        IE_CK(cudaStreamIsCapturing(st, &cs));
+        timed = cs == cudaStreamCaptureStatusNone;
+    }
+    if (timed) IE_CK(cudaEventRecord(p->prof_ev[0], st));
+    if (prec == IE_PREC_FP32)
+        IE_TRY(launch_translate_simt(p, X, Yslab, nrhs, st, gate));
+    else
+        IE_TRY(launch_translate_tc(p, prec, Yslab, nrhs, st, gate));
+    if (timed) {
+        IE_CK(cudaEventRecord(p->prof_ev[1], st));
+        IE_CK(cudaEventSynchronize(p->prof_ev[1]));
+        float ms = 0;
+        IE_CK(cudaEventElapsedTime(&ms, p->prof_ev[0], p->prof_ev[1]));
+        p->translate_ms += ms;
+        p->translate_launches++;
+    }
+    return IE_OK;
+}
+
+ie_status far_product(ie_plan p, int prec, const float2 *c, float2 *y, int nrhs, bool accumulate, cudaStream_t st,
+                      const int *gate) {
+    size_t stride = slab_stride(p);
+    IE_TRY(launch_aggregate(p, c, p->d_X, nrhs, st, gate));
+    for (int s = 0; s < kSlabs; ++s)
+        IE_TRY(launch_zero(p->d_Yslab + s * stride, (size_t)nrhs * p->nbox * kNU * sizeof(float2), st, gate));
+    if (prec != IE_PREC_FP32) IE_TRY(launch_split_tc(p, p->d_X, nrhs, prec == IE_PREC_FP16X3, st, gate));
+    IE_TRY(translate_timed(p, prec, p->d_X, p->d_Yslab, nrhs, st, gate));
+    IE_TRY(launch_disaggregate(p, p->d_Yslab, kSlabs, stride, y, nrhs, accumulate, st, gate));
+    return IE_OK;
+}
+
+ie_status apply(ie_plan p, int which, int prec, const float2 *c, float2 *y, int nrhs, cudaStream_t st,
+                const int *gate) {
+    if (which == IE_FAR) return far_product(p, prec, c, y, nrhs, false, st, gate);
+    IE_TRY(launch_near(p, c, y, nrhs, st, gate));
+    if (which == IE_FULL) IE_TRY(far_product(p, prec, c, y, nrhs, true, st, gate));
+    return IE_OK;
+}
+
+}  // namespace ie
+
+using namespace ie;
+
+static ie_status check_prec(ie_plan p, int prec) {
+    if (prec < IE_PREC_FP32 || prec > IE_PREC_BF16X1) return set_error("unknown precision %d", prec), IE_ERR_INVALID;
+    if (!(p->prec_mask & IE_PRECMASK(prec)))
+        return set_error("precision %d not prepared by this plan", prec), IE_ERR_UNSUPPORTED;
+    return IE_OK;
+}
+
+static ie_status check_rhs(ie_plan p, int nrhs) {
+    if (nrhs < 1 || nrhs > p->max_rhs) return set_error("nrhs %d outside [1, %d]", nrhs, p->max_rhs), IE_ERR_INVALID;
+    return IE_OK;
+}
+
+extern "C" {
+
+const char *ie_status_str(ie_status s) {
+    switch (s) {
+        case IE_OK: return "IE_OK";
+        case IE_ERR_INVALID: return "IE_ERR_INVALID";
+        case IE_ERR_OOM: return "IE_ERR_OOM";
+        case IE_ERR_CUDA: return "IE_ERR_CUDA";
+        case IE_ERR_NOT_CONVERGED: return "IE_ERR_NOT_CONVERGED";
+        case IE_ERR_TIMEOUT: return "IE_ERR_TIMEOUT";
+        case IE_ERR_UNSUPPORTED: return "IE_ERR_UNSUPPORTED";
+    }
+    return "IE_ERR_?";
+}
+
+const char *ie_last_error(void) { return last_error(); }
+const char *ie_version(void) { return "libie 0.1 (sm_103a)"; }
+int64_t ie_kernel_launches(void) { return g_launches.load(); }
+
+ie_status ie_plan_footprint(const ie_problem *pr, size_t *bytes) {
+    IE_TRY(validate(pr));
+    if (!bytes) return set_error("null bytes"), IE_ERR_INVALID;
+    BoxGrid g;
+    IE_TRY(build_grid(pr, g));
+    std::vector<int32_t> nb(pr->n_boxes);
+    int64_t n = 0;
+    for (int b = 0; b < pr->n_boxes; ++b) n += (nb[b] = pr->nb ? pr->nb[b] : kNU);
+    FarGroups fg;
+    int64_t npairs = 0, nd = 0;
+    far_groups(pr, g, false, fg, npairs, nd);
+    std::vector<int32_t> st, src;
+    std::vector<int64_t> boff;
+    int64_t elems = 0;
+    near_lists(pr, g, nb, st, src, boff, elems);
+    *bytes = plan_bytes(pr, n, npairs, nd, (int64_t)src.size(), elems);
+    return IE_OK;
+}
+
+ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
+    auto t0 = std::chrono::steady_clock::now();
+    if (!out) return set_error("null out"), IE_ERR_INVALID;
+    *out = nullptr;
+    IE_TRY(validate(pr));
+    BoxGrid g;
+    IE_TRY(build_grid(pr, g));
+    IE_TRY(prepare_kernels());
+    cudaStream_t st = (cudaStream_t)stream;
+
+    ie_plan p = new ie_plan_s();
+    auto fail = [&](ie_status s) {
+        ie_plan_destroy(p);
+        return s;
+    };
+    p->k = pr->k;
+    p->eta = pr->eta;
+    p->a = pr->box_edge;
+    p->alpha = pr->alpha;
+    p->G = pr->grid_n;
+    p->nbox = pr->n_boxes;
+    p->self_mode = pr->self_box_mode;
+    p->max_rhs = pr->max_rhs;
+    p->prec_mask = pr->prec_mask;
+    p->identity = (pr->P == nullptr);
+    p->ijk.assign(pr->box_ijk, pr->box_ijk + 3 * (size_t)pr->n_boxes);
+    p->nb.resize(p->nbox);
+    p->off.resize(p->nbox + 1);
+    p->off[0] = 0;
+    for (int b = 0; b < p->nbox; ++b) {
+        p->nb[b] = pr->nb ? pr->nb[b] : kNU;
+        p->off[b + 1] = p->off[b] + p->nb[b];
+    }
+    p->n = p->off[p->nbox];
+
+    FarGroups fg;
+    far_groups(pr, g, true, fg, p->n_far_pairs, p->n_far_disp);
+    p->h_disp = fg.disp;
+    p->h_gstart = fg.start;
+    std::vector<int32_t> nstart, nsrc;
+    std::vector<int64_t> nboff;
+    near_lists(pr, g, p->nb, nstart, nsrc, nboff, p->near_elems);
+    p->n_near_pairs = (int64_t)nsrc.size();
+
+    ie_status s;
+#define PT(expr)                   \
+    do {                           \
+        s = (expr);                \
+        if (s != IE_OK) return fail(s); \
+    } while (0)
+#define PC(expr)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            set_error("%s:%d %s: %s", __FILE__, __LINE__, #expr, cudaGetErrorString(e_));     \
+            return fail(IE_ERR_CUDA);                                                         \
+        }                                                                                     \
+    } while (0)
+
+    // geometry and mapping
+    PT(dalloc_t(p, &p->d_nb, p->nbox));
+    PT(dalloc_t(p, &p->d_off, p->nbox + 1));
+    PT(dalloc_t(p, &p->d_ijk, 3 * (size_t)p->nbox));
+    PC(cudaMemcpyAsync(p->d_nb, p->nb.data(), p->nbox * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    PC(cudaMemcpyAsync(p->d_off, p->off.data(), (p->nbox + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    PC(cudaMemcpyAsync(p->d_ijk, p->ijk.data(), 3 * p->nbox * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (!p->identity) {
+        std::vector<float2> P32((size_t)p->n * kNU);
+        for (size_t i = 0; i < P32.size(); ++i) P32[i] = make_float2((float)pr->P[2 * i], (float)pr->P[2 * i + 1]);
+        PT(dalloc_t(p, &p->d_P, P32.size()));
+        PC(cudaMemcpyAsync(p->d_P, P32.data(), P32.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+        PC(cudaStreamSynchronize(st));
+    }
+
+    // far groups and coupling blocks
+    if (p->n_far_disp) {
+        PT(dalloc_t(p, &p->d_disp, fg.disp.size()));
+        PT(dalloc_t(p, &p->d_src, fg.src.size()));
+        PT(dalloc_t(p, &p->d_dst, fg.dst.size()));
+        PC(cudaMemcpyAsync(p->d_disp, fg.disp.data(), fg.disp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        PC(cudaMemcpyAsync(p->d_src, fg.src.data(), fg.src.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        PC(cudaMemcpyAsync(p->d_dst, fg.dst.data(), fg.dst.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        PT(dalloc_t(p, &p->d_Csimt, (size_t)p->n_far_disp * kNU * kNU));
+        PT(launch_coupling_simt(p, p->d_disp, p->n_far_disp, p->d_Csimt, false, st));
+        if (wants_bf16(p->prec_mask)) {
+            PT(dalloc_t(p, &p->d_Cbf16, (size_t)p->n_far_disp * kTcDispElems));
+            PT(launch_coupling_tc(p, p->d_Cbf16, nullptr, false, st));
+        }
+        if (wants_fp16(p->prec_mask)) {
+            PT(dalloc_t(p, &p->d_Cfp16, (size_t)p->n_far_disp * kTcDispElems));
+            PT(dalloc_t(p, &p->d_Cexp16, (size_t)p->n_far_disp));
+            PT(launch_coupling_tc(p, p->d_Cfp16, p->d_Cexp16, true, st));
+        }
+    }
+
+    // near blocks
+    PT(dalloc_t(p, &p->d_near_start, nstart.size()));
+    PC(cudaMemcpyAsync(p->d_near_start, nstart.data(), nstart.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (p->n_near_pairs) {
+        PT(dalloc_t(p, &p->d_near_src, nsrc.size()));
+        PT(dalloc_t(p, &p->d_near_boff, nboff.size()));
+        PT(dalloc_t(p, &p->d_Nblk, (size_t)p->near_elems));
+        PC(cudaMemcpyAsync(p->d_near_src, nsrc.data(), nsrc.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        PC(cudaMemcpyAsync(p->d_near_boff, nboff.data(), nboff.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+        PT(launch_near_blocks(p, st));
+    }
+
+    // scratch
+    size_t col = (size_t)p->max_rhs * p->nbox;
+    PT(dalloc_t(p, &p->d_X, col * kNU));
+    PT(dalloc_t(p, &p->d_Yslab, (size_t)kSlabs * col * kNU));
+    if (wants_tc(p->prec_mask)) {
+        PT(dalloc_t(p, &p->d_Xtc, 2 * col * 2 * kNU));
+        PT(dalloc_t(p, &p->d_Xexp, col));
+    }
+    PT(dalloc_t(p, &p->d_err, 4));
+    PC(cudaMemsetAsync(p->d_err, 0, 4 * sizeof(int), st));
+    PT(dalloc_t(p, &p->d_tmp, (size_t)p->max_rhs * p->n));
+    PC(cudaStreamSynchronize(st));
+    PC(cudaGetLastError());
+    int dev = 0;
+    PC(cudaGetDevice(&dev));
+    PC(cudaDeviceGetAttribute(&p->tc_sms, cudaDevAttrMultiProcessorCount, dev));
+    p->plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = p;
+    return IE_OK;
+#undef PT
+#undef PC
+}
+
+ie_status ie_plan_stats_get(ie_plan p, ie_plan_stats *o) {
+    if (!p || !o) return set_error("null argument"), IE_ERR_INVALID;
+    o->n_boxes = p->nbox;
+    o->n = p->n;
+    o->n_far_pairs = p->n_far_pairs;
+    o->n_far_disp = p->n_far_disp;
+    o->n_near_pairs = p->n_near_pairs;
+    o->n_work_simt = p->n_work_simt;
+    o->n_work_tc = p->n_work_tc;
+    o->device_bytes = p->bytes;
+    o->plan_seconds = p->plan_seconds;
+    o->translate_ms = p->translate_ms;
+    o->translate_launches = p->translate_launches;
+    return IE_OK;
+}
+
+ie_status ie_plan_profile(ie_plan p, int enable) {
+    if (!p) return set_error("null plan"), IE_ERR_INVALID;
+    if (enable && !p->prof_ev[0]) {
+        IE_CK(cudaEventCreate(&p->prof_ev[0]));
+        IE_CK(cudaEventCreate(&p->prof_ev[1]));
+    }
+    p->profile = enable ? 1 : 0;
+    if (enable) {
+        p->translate_ms = 0;
+        p->translate_launches = 0;
+    }
+    return IE_OK;
+}
+
+ie_status ie_plan_destroy(ie_plan p) {
+    if (!p) return IE_OK;
+    cudaDeviceSynchronize();
+    destroy_cached_solvers(p);
+    for (void *q : p->allocs) cudaFree(q);
+    for (auto &e : p->prof_ev)
+        if (e) cudaEventDestroy(e);
+    delete p;
+    return IE_OK;
+}
+
+ie_status ie_matvec(ie_plan p, int which, int prec, const void *c, void *y, int nrhs, void *stream) {
+    if (!p || !c || !y) return set_error("null argument"), IE_ERR_INVALID;
+    if (which < IE_FAR || which > IE_FULL) return set_error("bad which %d", which), IE_ERR_INVALID;
+    IE_TRY(check_rhs(p, nrhs));
+    if (which != IE_NEAR) IE_TRY(check_prec(p, prec));
+    if (c == y) return set_error("c and y must not alias"), IE_ERR_INVALID;
+    return apply(p, which, prec, (const float2 *)c, (float2 *)y, nrhs, (cudaStream_t)stream);
+}
+
+ie_status ie_aggregate(ie_plan p, const void *c, void *X, int nrhs, void *stream) {
+    if (!p || !c || !X) return set_error("null argument"), IE_ERR_INVALID;
+    IE_TRY(check_rhs(p, nrhs));
+    return launch_aggregate(p, (const float2 *)c, (float2 *)X, nrhs, (cudaStream_t)stream);
+}
+
+ie_status ie_translate(ie_plan p, int prec, const void *X, void *Y, int nrhs, void *stream) {
+    if (!p || !X || !Y) return set_error("null argument"), IE_ERR_INVALID;
+    IE_TRY(check_rhs(p, nrhs));
+    IE_TRY(check_prec(p, prec));
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t stride = slab_stride(p);
+    for (int s = 0; s < kSlabs; ++s)
+        IE_TRY(launch_zero(p->d_Yslab + s * stride, (size_t)nrhs * p->nbox * kNU * sizeof(float2), st));
+    if (prec != IE_PREC_FP32) IE_TRY(launch_split_tc(p, (const float2 *)X, nrhs, prec == IE_PREC_FP16X3, st));
+    IE_TRY(translate_timed(p, prec, (const float2 *)X, p->d_Yslab, nrhs, st, nullptr));
+    return launch_sum_slabs(p, p->d_Yslab, kSlabs, stride, (float2 *)Y, nrhs, st);
+}
+
+ie_status ie_disaggregate(ie_plan p, const void *Y, void *r, int nrhs, void *stream) {
+    if (!p || !Y || !r) return set_error("null argument"), IE_ERR_INVALID;
+    IE_TRY(check_rhs(p, nrhs));
+    return launch_disaggregate(p, (const float2 *)Y, 1, 0, (float2 *)r, nrhs, false, (cudaStream_t)stream);
+}
+
+ie_status ie_near(ie_plan p, const void *c, void *y, int nrhs, void *stream) {
+    if (!p || !c || !y) return set_error("null argument"), IE_ERR_INVALID;
+    IE_TRY(check_rhs(p, nrhs));
+    return launch_near(p, (const float2 *)c, (float2 *)y, nrhs, (cudaStream_t)stream);
+}
+
+ie_status ie_coupling_blocks(ie_plan p, const int32_t *d, int nd, void *outp, void *stream) {
+    if (!p || !d || !outp || nd < 0) return set_error("bad argument"), IE_ERR_INVALID;
+    if (nd == 0) return IE_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *dd = nullptr;
+    IE_CK(cudaMallocAsync(&dd, (size_t)nd * 3 * sizeof(int32_t), st));
+    IE_CK(cudaMemcpyAsync(dd, d, (size_t)nd * 3 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    IE_TRY(launch_coupling_simt(p, dd, nd, (float2 *)outp, true, st));
+    IE_CK(cudaFreeAsync(dd, st));
+    return IE_OK;
+}
+
+ie_status ie_rhs_plane_wave(ie_plan p, const double *khat, const double *pol, int nrhs, void *v, void *stream) {
+    if (!p || !khat || !pol || !v) return set_error("null argument"), IE_ERR_INVALID;
+    if (nrhs < 1) return set_error("nrhs must be >= 1"), IE_ERR_INVALID;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *dk = nullptr;
+    IE_CK(cudaMallocAsync(&dk, (size_t)nrhs * 6 * sizeof(double), st));
+    IE_CK(cudaMemcpyAsync(dk, khat, (size_t)nrhs * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+    IE_CK(cudaMemcpyAsync(dk + 3 * nrhs, pol, (size_t)nrhs * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
+    IE_TRY(launch_plane_wave(p, dk, dk + 3 * nrhs, nrhs, (float2 *)v, st));
+    IE_CK(cudaFreeAsync(dk, st));
+    return IE_OK;
+}
+
+}  // extern "C"

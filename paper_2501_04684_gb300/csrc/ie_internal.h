@@ -1,0 +1,184 @@
+// Internal declarations of libie (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/ie.h"
+
+namespace ie {
+
+constexpr int kLattice = 4;
+constexpr int kSites = 64;          // 4^3 dipole sites per box
+constexpr int kNU = 192;            // 3 unknowns per site
+constexpr int kSlabs = 8;           // FP32 partial-sum slabs of the far field (see translate_simt.cu)
+
+// Tensor-core store of one coupling block: 3 M-blocks (128 real-embedded rows) x
+// 3 K-chunks (64 source unknowns) x {hi, lo}, each a 128 x 64 16-bit image laid out
+// exactly as the SW128 K-major shared-memory operand of tcgen05.mma (16 KB).
+constexpr int kTcImageElems = 128 * 64;
+constexpr int kTcImagesPerDisp = 3 * 3 * 2;
+constexpr size_t kTcDispElems = (size_t)kTcImageElems * kTcImagesPerDisp;   // 147,456
+
+void set_error(const char *fmt, ...);
+const char *last_error();
+
+// Process-wide count of kernels this library has put on the GPU (direct launches
+// plus the kernel nodes of every graph replay); captures do not count.
+void count_launches(int64_t n);
+void capture_begin();
+void capture_end();
+
+#define IE_CK(call)                                                                    \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            ::ie::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+            return IE_ERR_CUDA;                                                        \
+        }                                                                              \
+    } while (0)
+
+#define IE_CK_LAUNCH()                                                                 \
+    do {                                                                               \
+        ::ie::count_launches(1);                                                       \
+        cudaError_t e_ = cudaGetLastError();                                           \
+        if (e_ != cudaSuccess) {                                                       \
+            ::ie::set_error("%s:%d launch: %s", __FILE__, __LINE__, cudaGetErrorString(e_)); \
+            return IE_ERR_CUDA;                                                        \
+        }                                                                              \
+    } while (0)
+
+#define IE_TRY(expr)                                                                   \
+    do {                                                                               \
+        ie_status s_ = (expr);                                                         \
+        if (s_ != IE_OK) return s_;                                                    \
+    } while (0)
+
+// Work item of the translation kernels: one displacement group, a run of its pairs.
+struct WorkItem {
+    int32_t disp;        // index of the displacement (coupling block)
+    int32_t pair0;       // first pair (global index into src/dst)
+    int32_t npairs;      // pairs in this item (x nrhs columns)
+    int32_t mb;          // tensor-core M-block (0..2); unused by the FP32 path
+};
+
+struct WorkList {
+    WorkItem *d_items = nullptr;
+    int64_t n = 0;
+};
+
+}  // namespace ie
+
+struct ie_plan_s {
+    // problem constants
+    double k = 0, eta = 0, a = 0, alpha = 0;
+    int G = 0, nbox = 0, self_mode = 0, max_rhs = 1;
+    unsigned prec_mask = 0;
+    bool identity = false;
+    int64_t n = 0;                     // basis unknowns
+    std::vector<int32_t> ijk, nb;
+    std::vector<int64_t> off;          // nbox + 1
+
+    // device geometry and mapping
+    int32_t *d_nb = nullptr;
+    int64_t *d_off = nullptr;
+    int32_t *d_ijk = nullptr;
+    float2 *d_P = nullptr;             // [n][192] complex64 (null for identity)
+
+    // far zone, grouped by displacement
+    int64_t n_far_disp = 0, n_far_pairs = 0;
+    std::vector<int32_t> h_disp;       // n_far_disp x 3
+    std::vector<int64_t> h_gstart;     // n_far_disp + 1 (pair offsets)
+    int32_t *d_disp = nullptr;         // n_far_disp x 3
+    int32_t *d_src = nullptr, *d_dst = nullptr;   // [n_far_pairs], sorted by displacement
+    float2 *d_Csimt = nullptr;         // [n_far_disp][192 (k)][192 (m)] complex64
+    uint16_t *d_Cbf16 = nullptr;       // [n_far_disp][kTcDispElems] bf16 images
+    uint16_t *d_Cfp16 = nullptr;       // [n_far_disp][kTcDispElems] fp16 images
+    int32_t *d_Cexp16 = nullptr;       // [n_far_disp] power-of-two scale of the fp16 images
+
+    // near zone: per target box a run of (source box, block offset)
+    int64_t n_near_pairs = 0;
+    int64_t near_elems = 0;
+    int32_t *d_near_start = nullptr;   // nbox + 1
+    int32_t *d_near_src = nullptr;     // n_near_pairs
+    int64_t *d_near_boff = nullptr;    // n_near_pairs (element offset into d_Nblk)
+    float2 *d_Nblk = nullptr;          // blocks, nb_a x nb_b column-major each
+
+    // scratch (sized for max_rhs)
+    float2 *d_X = nullptr;             // [max_rhs][nbox][192]
+    float2 *d_Yslab = nullptr;         // [kSlabs][max_rhs][nbox][192]
+    uint16_t *d_Xtc = nullptr;         // [2 hl][max_rhs][nbox][2 reim][192] 16-bit
+    int32_t *d_Xexp = nullptr;         // [max_rhs][nbox] power-of-two scale of d_Xtc columns
+    int *d_err = nullptr;              // device error word of bounded waits
+    float2 *d_tmp = nullptr;           // [max_rhs][n] scratch of products
+
+    std::map<int, ie::WorkList> simt_work, tc_work;   // keyed by nrhs
+    std::vector<void *> allocs;
+    size_t bytes = 0;
+    double plan_seconds = 0;
+    int64_t n_work_simt = 0, n_work_tc = 0;
+    int tc_sms = 0;
+    // solver objects reused by ie_solve, keyed by (nrhs, restart, max_iters, tol, prec)
+    std::vector<std::pair<std::string, ie_solver>> solvers;
+    // profiling of the translation kernel
+    int profile = 0;
+    cudaEvent_t prof_ev[2] = {nullptr, nullptr};
+    double translate_ms = 0;
+    int64_t translate_launches = 0;
+};
+
+namespace ie {
+
+ie_status dalloc(ie_plan p, void **ptr, size_t bytes);
+template <class T>
+ie_status dalloc_t(ie_plan p, T **ptr, size_t count) {
+    return dalloc(p, reinterpret_cast<void **>(ptr), count * sizeof(T));
+}
+
+// kernels (launchers), each stream-ordered.  `gate` (device int, may be null): when
+// it reads 0 the kernels return at once (used by GMRES after convergence).
+ie_status prepare_kernels();
+ie_status launch_coupling_simt(const ie_plan p, const int32_t *d_disp, int64_t nd, float2 *out, bool row_major,
+                               cudaStream_t st);
+ie_status launch_coupling_tc(const ie_plan p, uint16_t *out, int32_t *exps, bool fp16, cudaStream_t st);
+ie_status launch_near_blocks(ie_plan p, cudaStream_t st);
+ie_status launch_aggregate(const ie_plan p, const float2 *c, float2 *X, int nrhs, cudaStream_t st,
+                           const int *gate = nullptr);
+ie_status launch_split_tc(const ie_plan p, const float2 *X, int nrhs, bool fp16, cudaStream_t st,
+                          const int *gate = nullptr);
+ie_status launch_disaggregate(const ie_plan p, const float2 *Yslab, int nslab, size_t slab_stride, float2 *r,
+                              int nrhs, bool accumulate, cudaStream_t st, const int *gate = nullptr);
+ie_status launch_sum_slabs(const ie_plan p, const float2 *Yslab, int nslab, size_t slab_stride, float2 *Y, int nrhs,
+                           cudaStream_t st);
+ie_status launch_zero(void *ptr, size_t bytes, cudaStream_t st, const int *gate = nullptr);
+ie_status launch_near(const ie_plan p, const float2 *c, float2 *y, int nrhs, cudaStream_t st,
+                      const int *gate = nullptr);
+ie_status launch_translate_simt(ie_plan p, const float2 *X, float2 *Yslab, int nrhs, cudaStream_t st,
+                                const int *gate = nullptr);
+ie_status launch_translate_tc(ie_plan p, int prec, float2 *Yslab, int nrhs, cudaStream_t st,
+                              const int *gate = nullptr);
+ie_status launch_plane_wave(const ie_plan p, const double *d_khat, const double *d_pol, int nrhs, float2 *v,
+                            cudaStream_t st);
+
+// y = op(c) (see ie_matvec); accumulate adds the far part into y.
+ie_status far_product(ie_plan p, int prec, const float2 *c, float2 *y, int nrhs, bool accumulate, cudaStream_t st,
+                      const int *gate = nullptr);
+ie_status apply(ie_plan p, int which, int prec, const float2 *c, float2 *y, int nrhs, cudaStream_t st,
+                const int *gate = nullptr);
+ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out);
+void destroy_cached_solvers(ie_plan p);
+// launch the translation kernel of `prec` (with the profiling brackets when enabled)
+ie_status translate_timed(ie_plan p, int prec, const float2 *X, float2 *Yslab, int nrhs, cudaStream_t st,
+                          const int *gate);
+int simt_tile_columns();
+int tc_tile_columns();
+
+size_t slab_stride(const ie_plan p);   // elements between far-field slabs
+
+}  // namespace ie

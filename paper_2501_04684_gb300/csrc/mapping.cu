@@ -1,0 +1,296 @@
+// K2 / K4: mapping to uniform basis functions (Alg. 1, x_b = P_b^T c_b) and inverse
+// mapping (Alg. 3, r_b = P_b y_b); the 16-bit hi/lo split of the mapped vectors for
+// the tensor-core translation; the plane-wave excitation (§5) tested with P.
+//
+// Layouts: c, r: [rhs][n] complex64 (box b's coefficients at off[b] .. off[b+1]);
+// P: [n][192] complex64 (row off[b]+i is basis function i of box b);
+// X, Y: [rhs][nbox][192] complex64.  All HBM-bound: one CTA per (box, rhs).
+#include "ie_internal.h"
+
+namespace ie {
+namespace {
+
+// x[u] = sum_i P[i][u] c[i]: 192 threads, one per dipole unknown u.  FP32 products
+// in runs of 16, runs summed in FP64.
+__global__ void aggregate_kernel(const float2 *__restrict__ P, const int32_t *__restrict__ nb,
+                                 const int64_t *__restrict__ off, int64_t n, int nbox,
+                                 const float2 *__restrict__ c, float2 *__restrict__ X, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    __shared__ float2 cs[kNU];
+    int b = blockIdx.x, r = blockIdx.y, u = threadIdx.x;
+    int nbb = nb[b];
+    const float2 *cb = c + (int64_t)r * n + off[b];
+    for (int i = u; i < nbb; i += blockDim.x) cs[i] = cb[i];
+    __syncthreads();
+    const float2 *Pb = P + off[b] * kNU;
+    double ar = 0, ai = 0;
+    for (int i0 = 0; i0 < nbb; i0 += 16) {
+        float pr = 0.f, pi = 0.f;
+        int i1 = min(nbb, i0 + 16);
+        for (int i = i0; i < i1; ++i) {
+            float2 p = Pb[(int64_t)i * kNU + u];
+            float2 cv = cs[i];
+            pr = fmaf(p.x, cv.x, fmaf(-p.y, cv.y, pr));
+            pi = fmaf(p.x, cv.y, fmaf(p.y, cv.x, pi));
+        }
+        ar += pr;
+        ai += pi;
+    }
+    X[((int64_t)r * nbox + b) * kNU + u] = make_float2((float)ar, (float)ai);
+}
+
+__global__ void copy_kernel(const float4 *__restrict__ a, float4 *__restrict__ b, int64_t n4,
+                            const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n4) b[i] = a[i];
+}
+
+// 16-bit hi/lo split of X for the tensor-core path.  Layout [hl][rhs][nbox][reim][192]:
+// row (rhs, box, reim) of 192 contiguous 16-bit values = one operand row (K-major).
+// FP16: the column is scaled by 2^-e so that max |x| < 2^14; e is stored.
+template <bool FP16>
+__global__ void split_kernel(const float2 *__restrict__ X, int nbox, int nrhs, uint16_t *__restrict__ Xtc,
+                             int32_t *__restrict__ Xexp, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    int b = blockIdx.x, r = blockIdx.y, u = threadIdx.x;
+    int64_t col = (int64_t)r * nbox + b;
+    float2 x = X[col * kNU + u];
+    float scale = 1.f;
+    if (FP16) {
+        __shared__ float red[8];
+        __shared__ float s_scale;
+        float m = fmaxf(fabsf(x.x), fabsf(x.y));
+        for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((u & 31) == 0) red[u >> 5] = m;
+        __syncthreads();
+        if (u == 0) {
+            float mm = 0.f;
+            for (int w = 0; w < kNU / 32; ++w) mm = fmaxf(mm, red[w]);
+            int e = 0;
+            if (mm > 0.f) {
+                frexpf(mm, &e);
+                e -= 14;
+            }
+            Xexp[col] = e;
+            s_scale = ldexpf(1.f, -e);
+        }
+        __syncthreads();
+        scale = s_scale;
+    } else if (u == 0) {
+        Xexp[col] = 0;
+    }
+    int64_t plane = (int64_t)nrhs * nbox * 2 * kNU;
+    uint16_t *row_re = Xtc + (col * 2) * kNU;
+    uint16_t *row_im = row_re + kNU;
+    float v[2] = {x.x * scale, x.y * scale};
+    uint16_t hi[2], lo[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        if (FP16) {
+            __half h = __float2half_rn(v[t]);
+            hi[t] = __half_as_ushort(h);
+            lo[t] = __half_as_ushort(__float2half_rn(v[t] - __half2float(h)));
+        } else {
+            __nv_bfloat16 h = __float2bfloat16_rn(v[t]);
+            hi[t] = __bfloat16_as_ushort(h);
+            lo[t] = __bfloat16_as_ushort(__float2bfloat16_rn(v[t] - __bfloat162float(h)));
+        }
+    }
+    row_re[u] = hi[0];
+    row_im[u] = hi[1];
+    row_re[plane + u] = lo[0];
+    row_im[plane + u] = lo[1];
+}
+
+// r[i] (+)= sum_u P[i][u] y[u], y = sum over slabs (FP64).  One warp per basis row,
+// lanes over u; FP32 products and tree reduction.
+__global__ void disaggregate_kernel(const float2 *__restrict__ P, const int32_t *__restrict__ nb,
+                                    const int64_t *__restrict__ off, int64_t n, int nbox,
+                                    const float2 *__restrict__ Yslab, int nslab, size_t slab_stride,
+                                    float2 *__restrict__ out, int accumulate, int identity,
+                                    const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    __shared__ float2 ys[kNU];
+    int b = blockIdx.x, r = blockIdx.y;
+    int64_t col = (int64_t)r * nbox + b;
+    for (int u = threadIdx.x; u < kNU; u += blockDim.x) {
+        double sr = 0, si = 0;
+        for (int s = 0; s < nslab; ++s) {
+            float2 v = Yslab[s * slab_stride + col * kNU + u];
+            sr += v.x;
+            si += v.y;
+        }
+        ys[u] = make_float2((float)sr, (float)si);
+    }
+    __syncthreads();
+    float2 *ob = out + (int64_t)r * n + off[b];
+    int nbb = nb[b];
+    if (identity) {
+        for (int u = threadIdx.x; u < kNU; u += blockDim.x) {
+            float2 v = ys[u];
+            if (accumulate) {
+                float2 o = ob[u];
+                v.x += o.x;
+                v.y += o.y;
+            }
+            ob[u] = v;
+        }
+        return;
+    }
+    const float2 *Pb = P + off[b] * kNU;
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < nbb; i += nw) {
+        float pr = 0.f, pi = 0.f;
+        const float2 *row = Pb + (int64_t)i * kNU;
+#pragma unroll
+        for (int t = 0; t < kNU / 32; ++t) {
+            float2 p = row[lane + 32 * t];
+            float2 y = ys[lane + 32 * t];
+            pr = fmaf(p.x, y.x, fmaf(-p.y, y.y, pr));
+            pi = fmaf(p.x, y.y, fmaf(p.y, y.x, pi));
+        }
+        for (int o = 16; o; o >>= 1) {
+            pr += __shfl_xor_sync(0xffffffffu, pr, o);
+            pi += __shfl_xor_sync(0xffffffffu, pi, o);
+        }
+        if (lane == 0) {
+            if (accumulate) {
+                float2 o = ob[i];
+                pr += o.x;
+                pi += o.y;
+            }
+            ob[i] = make_float2(pr, pi);
+        }
+    }
+}
+
+__global__ void zero_kernel(float4 *__restrict__ p, int64_t n4, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (; i < n4; i += stride) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void sum_slabs_kernel(const float2 *__restrict__ Yslab, int nslab, size_t slab_stride, int64_t count,
+                                 float2 *__restrict__ Y) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    double sr = 0, si = 0;
+    for (int s = 0; s < nslab; ++s) {
+        float2 v = Yslab[s * slab_stride + i];
+        sr += v.x;
+        si += v.y;
+    }
+    Y[i] = make_float2((float)sr, (float)si);
+}
+
+// Plane wave at the dipole sites, e[3s+a] = pol[a] exp(-j k khat . r_s) (FP64 phase),
+// then v_b = P_b e_b as in disaggregate_kernel.
+__global__ void plane_wave_kernel(double k, double a, int G, const int32_t *__restrict__ ijk,
+                                  const float2 *__restrict__ P, const int32_t *__restrict__ nb,
+                                  const int64_t *__restrict__ off, int64_t n,
+                                  const double *__restrict__ khat, const double *__restrict__ pol,
+                                  float2 *__restrict__ v, int identity) {
+    __shared__ float2 es[kNU];
+    int b = blockIdx.x, r = blockIdx.y;
+    double h = a / kLattice;
+    for (int s = threadIdx.x; s < kSites; s += blockDim.x) {
+        int ii[3] = {s & 3, (s >> 2) & 3, s >> 4};
+        double ph = 0;
+        for (int c = 0; c < 3; ++c) {
+            double pos = a * ((double)ijk[3 * b + c] + 0.5 - 0.5 * G) + h * (ii[c] + 0.5) - 0.5 * a;
+            ph += khat[3 * r + c] * pos;
+        }
+        double sn, cs;
+        sincos(-k * ph, &sn, &cs);
+        for (int c = 0; c < 3; ++c) es[3 * s + c] = make_float2((float)(pol[3 * r + c] * cs), (float)(pol[3 * r + c] * sn));
+    }
+    __syncthreads();
+    float2 *vb = v + (int64_t)r * n + off[b];
+    if (identity) {
+        for (int u = threadIdx.x; u < kNU; u += blockDim.x) vb[u] = es[u];
+        return;
+    }
+    const float2 *Pb = P + off[b] * kNU;
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < nb[b]; i += nw) {
+        double pr = 0, pi = 0;
+        const float2 *row = Pb + (int64_t)i * kNU;
+        for (int t = 0; t < kNU / 32; ++t) {
+            float2 p = row[lane + 32 * t];
+            float2 e = es[lane + 32 * t];
+            pr += (double)p.x * e.x - (double)p.y * e.y;
+            pi += (double)p.x * e.y + (double)p.y * e.x;
+        }
+        for (int o = 16; o; o >>= 1) {
+            pr += __shfl_xor_sync(0xffffffffu, pr, o);
+            pi += __shfl_xor_sync(0xffffffffu, pi, o);
+        }
+        if (lane == 0) vb[i] = make_float2((float)pr, (float)pi);
+    }
+}
+
+}  // namespace
+
+ie_status launch_aggregate(const ie_plan p, const float2 *c, float2 *X, int nrhs, cudaStream_t st, const int *gate) {
+    if (p->identity) {
+        // n == nbox * 192 and [rhs][n] == [rhs][nbox][192]
+        int64_t n4 = (int64_t)nrhs * p->n / 2;
+        copy_kernel<<<(unsigned)((n4 + 255) / 256), 256, 0, st>>>(reinterpret_cast<const float4 *>(c),
+                                                                  reinterpret_cast<float4 *>(X), n4, gate);
+    } else {
+        aggregate_kernel<<<dim3(p->nbox, nrhs), kNU, 0, st>>>(p->d_P, p->d_nb, p->d_off, p->n, p->nbox, c, X, gate);
+    }
+    IE_CK_LAUNCH();
+    return IE_OK;
+}
+
+ie_status launch_split_tc(const ie_plan p, const float2 *X, int nrhs, bool fp16, cudaStream_t st, const int *gate) {
+    if (fp16)
+        split_kernel<true><<<dim3(p->nbox, nrhs), kNU, 0, st>>>(X, p->nbox, nrhs, p->d_Xtc, p->d_Xexp, gate);
+    else
+        split_kernel<false><<<dim3(p->nbox, nrhs), kNU, 0, st>>>(X, p->nbox, nrhs, p->d_Xtc, p->d_Xexp, gate);
+    IE_CK_LAUNCH();
+    return IE_OK;
+}
+
+ie_status launch_disaggregate(const ie_plan p, const float2 *Yslab, int nslab, size_t stride, float2 *r, int nrhs,
+                              bool accumulate, cudaStream_t st, const int *gate) {
+    disaggregate_kernel<<<dim3(p->nbox, nrhs), 256, 0, st>>>(p->d_P, p->d_nb, p->d_off, p->n, p->nbox, Yslab, nslab,
+                                                             stride, r, accumulate ? 1 : 0, p->identity ? 1 : 0, gate);
+    IE_CK_LAUNCH();
+    return IE_OK;
+}
+
+ie_status launch_zero(void *ptr, size_t bytes, cudaStream_t st, const int *gate) {
+    if (bytes == 0) return IE_OK;
+    if (bytes % 16) {
+        set_error("launch_zero: size %zu not a multiple of 16", bytes);
+        return IE_ERR_INVALID;
+    }
+    int64_t n4 = (int64_t)(bytes / 16);
+    int64_t grid = (n4 + 255) / 256;
+    if (grid > 4096) grid = 4096;
+    zero_kernel<<<(unsigned)grid, 256, 0, st>>>(reinterpret_cast<float4 *>(ptr), n4, gate);
+    IE_CK_LAUNCH();
+    return IE_OK;
+}
+
+ie_status launch_sum_slabs(const ie_plan p, const float2 *Yslab, int nslab, size_t stride, float2 *Y, int nrhs,
+                           cudaStream_t st) {
+    int64_t count = (int64_t)nrhs * p->nbox * kNU;
+    sum_slabs_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(Yslab, nslab, stride, count, Y);
+    IE_CK_LAUNCH();
+    return IE_OK;
+}
+
+ie_status launch_plane_wave(const ie_plan p, const double *d_khat, const double *d_pol, int nrhs, float2 *v,
+                            cudaStream_t st) {
+    plane_wave_kernel<<<dim3(p->nbox, nrhs), 256, 0, st>>>(p->k, p->a, p->G, p->d_ijk, p->d_P, p->d_nb, p->d_off,
+                                                           p->n, d_khat, d_pol, v, p->identity ? 1 : 0);
+    IE_CK_LAUNCH();
+    return IE_OK;
+}
+
+}  // namespace ie

@@ -1,0 +1,163 @@
+// K3 (plain path): translation stage (Alg. 2) in FP32 on the SIMT cores.
+//
+// Far pairs are grouped by box displacement d (Alg. 2 with eq. 13's matrix shared
+// by every pair of the group), so each group is one dense complex GEMM
+//     Y[:, dst_p] += G_d X[:, src_p]   for the pairs p of the group,
+// with M = K = 192 and N = pairs x rhs.  A work item is one group's run of at most
+// 64 columns; one CTA computes its full 192 x 64 output tile over K = 192 in chunks
+// of 16 (cp.async double buffering) and scatter-adds the tile into the target boxes.
+//
+// Accuracy: each tile sums 192 complex products in FP32 registers.  Contributions
+// of different displacements meet in one of kSlabs FP32 partial fields (slab =
+// d mod kSlabs, red.global.add.v4.f32), and the slabs are added in FP64 by the
+// inverse-mapping kernel, so no FP32 sum runs over more than ~N_far/kSlabs terms.
+#include "ie_internal.h"
+
+namespace ie {
+namespace {
+
+constexpr int kTileN = 64;
+constexpr int kKC = 16;
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+struct SmemSimt {
+    float2 A[2][kKC][kNU];      // A^T chunk: [k][m]
+    float2 B[2][kKC][kTileN];   // B chunk:   [k][col]
+};
+
+__global__ void __launch_bounds__(kThreads, 1)
+translate_simt_kernel(const WorkItem *__restrict__ items, const float2 *__restrict__ C,
+                      const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                      const float2 *__restrict__ X, float2 *__restrict__ Yslab, size_t slab_stride,
+                      int nbox, int nrhs, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmemSimt &S = *reinterpret_cast<SmemSimt *>(smem_raw);
+    const WorkItem it = items[blockIdx.x];
+    const int tid = threadIdx.x;
+    const int ncols = it.npairs * nrhs;
+    const float2 *Cd = C + (int64_t)it.disp * kNU * kNU;
+
+    // B loader: thread -> (column, 4 consecutive k)
+    const int lcol = tid & (kTileN - 1);
+    const int lkq = tid >> 6;                    // 0..3
+    int lc = lcol < ncols ? lcol : 0;
+    const int lpair = it.pair0 + lc / nrhs;
+    const int lr = lc % nrhs;
+    const float2 *xcol = X + ((int64_t)lr * nbox + src[lpair]) * kNU;
+
+    auto load_chunk = [&](int kc, int buf) {
+        // A: 16 x 192 float2 = 1536 x 16 B, 6 per thread
+        const float4 *ga = reinterpret_cast<const float4 *>(Cd + (int64_t)kc * kKC * kNU);
+        float4 *sa = reinterpret_cast<float4 *>(&S.A[buf][0][0]);
+#pragma unroll
+        for (int t = 0; t < 6; ++t) cp_async16(sa + tid + t * kThreads, ga + tid + t * kThreads);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            int kk = lkq * 4 + t;
+            cp_async8(&S.B[buf][kk][lcol], xcol + kc * kKC + kk);
+        }
+        cp_commit();
+    };
+
+    const int tm = tid >> 3;     // 0..31: rows {2tm, 2tm+1} + 64 j
+    const int tn = tid & 7;      // 0..7:  cols {2tn, 2tn+1} + 16 j
+    float2 acc[6][8];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = make_float2(0.f, 0.f);
+
+    constexpr int nK = kNU / kKC;   // 12
+    load_chunk(0, 0);
+    for (int kc = 0; kc < nK; ++kc) {
+        int buf = kc & 1;
+        if (kc + 1 < nK) {
+            load_chunk(kc + 1, buf ^ 1);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kKC; ++kk) {
+            float2 a[6], b[8];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                float4 v = *reinterpret_cast<const float4 *>(&S.A[buf][kk][2 * tm + 64 * j]);
+                a[2 * j] = make_float2(v.x, v.y);
+                a[2 * j + 1] = make_float2(v.z, v.w);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float4 v = *reinterpret_cast<const float4 *>(&S.B[buf][kk][2 * tn + 16 * j]);
+                b[2 * j] = make_float2(v.x, v.y);
+                b[2 * j + 1] = make_float2(v.z, v.w);
+            }
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    acc[i][j].x = fmaf(a[i].x, b[j].x, acc[i][j].x);
+                    acc[i][j].x = fmaf(-a[i].y, b[j].y, acc[i][j].x);
+                    acc[i][j].y = fmaf(a[i].x, b[j].y, acc[i][j].y);
+                    acc[i][j].y = fmaf(a[i].y, b[j].x, acc[i][j].y);
+                }
+        }
+        __syncthreads();
+    }
+
+    float2 *Ys = Yslab + (size_t)(it.disp % kSlabs) * slab_stride;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        int col = 2 * tn + 16 * (j >> 1) + (j & 1);
+        if (col >= ncols) continue;
+        int pair = it.pair0 + col / nrhs;
+        int r = col % nrhs;
+        float2 *ycol = Ys + ((int64_t)r * nbox + dst[pair]) * kNU;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            float4 v = make_float4(acc[2 * i][j].x, acc[2 * i][j].y, acc[2 * i + 1][j].x, acc[2 * i + 1][j].y);
+            atomicAdd(reinterpret_cast<float4 *>(ycol + 2 * tm + 64 * i), v);
+        }
+    }
+}
+
+}  // namespace
+
+size_t slab_stride(const ie_plan p) { return (size_t)p->max_rhs * p->nbox * kNU; }
+
+ie_status prepare_translate_simt() {
+    IE_CK(cudaFuncSetAttribute(translate_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sizeof(SmemSimt)));
+    return IE_OK;
+}
+
+ie_status launch_translate_simt(ie_plan p, const float2 *X, float2 *Yslab, int nrhs, cudaStream_t st,
+                                const int *gate) {
+    WorkList *wl = nullptr;
+    IE_TRY(work_list(p, false, nrhs, &wl));
+    if (wl->n == 0) return IE_OK;
+    translate_simt_kernel<<<(unsigned)wl->n, kThreads, sizeof(SmemSimt), st>>>(
+        wl->d_items, p->d_Csimt, p->d_src, p->d_dst, X, Yslab, slab_stride(p), p->nbox, nrhs, gate);
+    IE_CK_LAUNCH();
+    return IE_OK;
+}
+
+int simt_tile_columns() { return kTileN; }
+
+}  // namespace ie

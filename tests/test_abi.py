@@ -1,0 +1,81 @@
+"""CPU checks of the C ABI: the library loads, exports every symbol include/ie.h
+declares, and rejects bad problems in its host-side validation (no GPU needed)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_2501_04684_gb300 as ie
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2501_04684_gb300 import build
+    return build.build()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "ie.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(ie_[a-z_]+)\s*\(", src)) - {"ie_problem"})
+
+
+def test_header_and_binding_agree():
+    assert declared_functions() == sorted(ie.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(built):
+    out = subprocess.run(["nm", "-D", "--defined-only", built], capture_output=True, text=True, check=True).stdout
+    syms = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [f for f in declared_functions() if f not in syms]
+    assert not missing, missing
+    L = ie.lib()
+    for f in declared_functions():
+        assert hasattr(L, f)
+    assert "sm_103a" in ie.ie_version()
+
+
+def test_status_strings(built):
+    L = ie.lib()
+    for s in range(7):
+        assert L.ie_status_str(s).decode().startswith("IE_")
+
+
+def _tiny_problem(**over):
+    p = W.tiny()
+    kw = dict(k=p.k, eta=p.eta, box_edge=p.a, grid_n=p.G, box_ijk=p.box_ijk, nb=p.nb, P=p.P, alpha=1.0,
+              prec_mask=ie.precmask(ie.IE_PREC_FP32), max_rhs=1)
+    kw.update(over)
+    return ie.make_problem(**kw)
+
+
+def test_footprint_is_host_only_and_counts_pairs(built):
+    b = ie.ie_plan_footprint(_tiny_problem())
+    # 316 coupling blocks of 192 x 192 complex64 at least
+    assert b > 316 * 192 * 192 * 8
+    b2 = ie.ie_plan_footprint(_tiny_problem(prec_mask=ie.precmask(ie.IE_PREC_FP32, ie.IE_PREC_BF16X3)))
+    assert b2 > b + 316 * 147456 * 2 - 1
+
+
+@pytest.mark.parametrize("bad", [
+    dict(lattice=3),
+    dict(max_rhs=0),
+    dict(prec_mask=0),
+    dict(nb=np.full(64, 193, dtype=np.int32)),
+    dict(box_ijk=np.zeros((64, 3), dtype=np.int32)),          # duplicates
+    dict(nb=None),                                           # P given without nb
+])
+def test_validation_rejects(built, bad):
+    pr = _tiny_problem(**bad)
+    with pytest.raises(ie.IEError) as e:
+        ie.ie_plan_footprint(pr)
+    assert e.value.status == ie.IE_ERR_INVALID
+    h = ctypes.c_void_p()
+    assert ie.lib().ie_plan_create(ctypes.byref(pr), None, ctypes.byref(h)) == ie.IE_ERR_INVALID
+    assert h.value is None
