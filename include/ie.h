@@ -144,6 +144,20 @@ ie_status ie_translate(ie_plan plan, int prec, const void *X, void *Y, int nrhs,
 /* Stage 3 (Alg. 3): r[r][o_b + i] = sum_u P_b[i][u] Y[r][b][u] (overwrites r). */
 ie_status ie_disaggregate(ie_plan plan, const void *Y, void *r, int nrhs, void *stream);
 
+/* Allocation-free form of ie_translate with prec = IE_PREC_FP32 (the paper has no
+ * counterpart; it serves callers that cannot allocate device memory at call time,
+ * e.g. code whose device memory belongs to another allocator's pool, or a latency-
+ * critical loop where cudaMalloc / cudaFree could block or synchronise the device).
+ * Same arithmetic and result as ie_translate; it calls no allocator.  Its scratch is
+ * a fixed 32 MiB device area inside libie (held by every GPU that loads the library
+ * until exit) that must hold 8 x nrhs x n_boxes x 192 complex64 partial sums plus
+ * the group offsets; larger requests return IE_ERR_INVALID with the sizes in
+ * ie_last_error().  The first call on a device looks the area up and sets the kernel
+ * up on that device (make it before any stream capture).  Every call reuses the same
+ * area, so calls that overlap in time on the GPU (any streams, any plans) race; the
+ * partial sums are cleared by each call.  X, Y: device complex64 [nrhs][n_boxes][192]. */
+ie_status ie_translate_noalloc(ie_plan plan, const void *X, void *Y, int nrhs, void *stream);
+
 /* Near product (eq. 2, stored Z^N) plus the self term: y = alpha c + Z^N c. */
 ie_status ie_near(ie_plan plan, const void *c, void *y, int nrhs, void *stream);
 

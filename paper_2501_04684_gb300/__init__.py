@@ -28,7 +28,7 @@ EXPORTED = [
     "ie_aggregate", "ie_translate", "ie_disaggregate", "ie_near", "ie_coupling_blocks", "ie_rhs_plane_wave",
     "ie_solve_opts_default", "ie_solve", "ie_solver_create", "ie_solver_footprint", "ie_solver_start",
     "ie_solver_advance", "ie_solver_poll", "ie_solver_destroy", "ie_status_str", "ie_last_error", "ie_version",
-    "ie_plan_profile", "ie_kernel_launches",
+    "ie_plan_profile", "ie_kernel_launches", "ie_translate_noalloc",
 ]
 
 
@@ -87,6 +87,7 @@ def lib() -> ctypes.CDLL:
     L.ie_aggregate.argtypes = [vp, vp, vp, i, vp]
     L.ie_translate.argtypes = [vp, i, vp, vp, i, vp]
     L.ie_disaggregate.argtypes = [vp, vp, vp, i, vp]
+    L.ie_translate_noalloc.argtypes = [vp, vp, vp, i, vp]
     L.ie_near.argtypes = [vp, vp, vp, i, vp]
     L.ie_coupling_blocks.argtypes = [vp, vp, i, vp, vp]
     L.ie_rhs_plane_wave.argtypes = [vp, vp, vp, i, vp, vp]
@@ -199,6 +200,10 @@ def ie_aggregate(plan, c, X, nrhs, stream=None):
 
 def ie_translate(plan, prec, X, Y, nrhs, stream=None):
     return _check(lib().ie_translate(plan, prec, _ptr(X), _ptr(Y), nrhs, _stream(stream)), "ie_translate")
+
+
+def ie_translate_noalloc(plan, X, Y, nrhs, stream=None):
+    return _check(lib().ie_translate_noalloc(plan, _ptr(X), _ptr(Y), nrhs, _stream(stream)), "ie_translate_noalloc")
 
 
 def ie_disaggregate(plan, Y, r, nrhs, stream=None):

@@ -11,10 +11,11 @@
 // of different displacements meet in one of kSlabs FP32 partial fields (slab =
 // d mod kSlabs, red.global.add.v4.f32), and the slabs are added in FP64 by the
 // inverse-mapping kernel, so no FP32 sum runs over more than ~N_far/kSlabs terms.
+#include <mutex>
+
 #include "ie_internal.h"
 
 namespace ie {
-namespace {
 
 constexpr int kTileN = 64;
 constexpr int kKC = 16;
@@ -39,15 +40,16 @@ struct SmemSimt {
     float2 B[2][kKC][kTileN];   // B chunk:   [k][col]
 };
 
-__global__ void __launch_bounds__(kThreads, 1)
-translate_simt_kernel(const WorkItem *__restrict__ items, const float2 *__restrict__ C,
-                      const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
-                      const float2 *__restrict__ X, float2 *__restrict__ Yslab, size_t slab_stride,
-                      int nbox, int nrhs, const int *__restrict__ gate) {
-    if (gate && *gate == 0) return;
+namespace {
+
+// One work item: the 192 x (npairs * nrhs) output tile of displacement it.disp,
+// scatter-added into slab (disp mod kSlabs).
+__device__ __forceinline__ void simt_tile(const WorkItem it, const float2 *__restrict__ C,
+                                          const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                                          const float2 *__restrict__ X, float2 *__restrict__ Yslab,
+                                          size_t slab_stride, int nbox, int nrhs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmemSimt &S = *reinterpret_cast<SmemSimt *>(smem_raw);
-    const WorkItem it = items[blockIdx.x];
     const int tid = threadIdx.x;
     const int ncols = it.npairs * nrhs;
     const float2 *Cd = C + (int64_t)it.disp * kNU * kNU;
@@ -137,6 +139,15 @@ translate_simt_kernel(const WorkItem *__restrict__ items, const float2 *__restri
     }
 }
 
+__global__ void __launch_bounds__(kThreads, 1)
+translate_simt_kernel(const WorkItem *__restrict__ items, const float2 *__restrict__ C,
+                      const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                      const float2 *__restrict__ X, float2 *__restrict__ Yslab, size_t slab_stride,
+                      int nbox, int nrhs, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    simt_tile(items[blockIdx.x], C, src, dst, X, Yslab, slab_stride, nbox, nrhs);
+}
+
 }  // namespace
 
 size_t slab_stride(const ie_plan p) { return (size_t)p->max_rhs * p->nbox * kNU; }
@@ -161,3 +172,92 @@ ie_status launch_translate_simt(ie_plan p, const float2 *X, float2 *Yslab, int n
 int simt_tile_columns() { return kTileN; }
 
 }  // namespace ie
+
+// ---------------------------------------------------------------------------------
+// ie_translate_noalloc: the FP32 translation with its scratch in a fixed device area.
+//
+// For callers that cannot allocate device memory when they run the product: code
+// whose device memory is owned by another allocator (a framework pool that forbids
+// raw cudaMalloc), or a latency-critical loop where cudaMalloc / cudaFree could
+// block or synchronise the device.  ie_translate needs the plan's scratch slabs
+// and, on the first call for a new number of right-hand sides, allocates a work
+// list; this variant allocates nothing.  Its scratch is the file-scope array below,
+// held by every GPU that loads the library until the process exits.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;   // 32 MiB
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Same tile as translate_simt_kernel; the work item comes from the group offsets
+// (blockIdx.x = displacement group, blockIdx.y = run of `per` pairs inside it).
+__global__ void __launch_bounds__(ie::kThreads, 1)
+translate_simt_grouped_kernel(const int64_t *__restrict__ gstart, const float2 *__restrict__ C,
+                              const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+                              const float2 *__restrict__ X, float2 *__restrict__ Yslab, size_t slab_stride,
+                              int nbox, int nrhs, int per) {
+    int64_t d = blockIdx.x;
+    int64_t s = gstart[d], e = gstart[d + 1];
+    int64_t q = s + (int64_t)blockIdx.y * per;
+    if (q >= e) return;
+    ie::WorkItem it{(int32_t)d, (int32_t)q, (int32_t)(e - q < per ? e - q : per), 0};
+    ie::simt_tile(it, C, src, dst, X, Yslab, slab_stride, nbox, nrhs);
+}
+
+// Device address of the scratch area on the current device (looked up once per
+// device; the kernel attribute is set at the same time).
+ie_status noalloc_scratch(void **out) {
+    int dev = 0;
+    IE_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return ie::set_error("device %d out of range", dev), IE_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        IE_CK(cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
+        IE_CK(cudaFuncSetAttribute(translate_simt_grouped_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sizeof(ie::SmemSimt)));
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = g_noalloc_ptr[dev];
+    return IE_OK;
+}
+
+}  // namespace
+
+extern "C" ie_status ie_translate_noalloc(ie_plan p, const void *X, void *Y, int nrhs, void *stream) {
+    using namespace ie;
+    if (!p || !X || !Y) return set_error("null argument"), IE_ERR_INVALID;
+    if (nrhs < 1 || nrhs > p->max_rhs || nrhs > kTileN)
+        return set_error("nrhs %d outside [1, %d]", nrhs, p->max_rhs < kTileN ? p->max_rhs : kTileN), IE_ERR_INVALID;
+    size_t off_bytes = ((size_t)(p->n_far_disp + 1) * sizeof(int64_t) + 255) / 256 * 256;
+    size_t stride = (size_t)nrhs * p->nbox * kNU;                 // float2 per slab
+    size_t need = off_bytes + (size_t)kSlabs * stride * sizeof(float2);
+    if (need > kNoAllocScratchBytes)
+        return set_error("ie_translate_noalloc needs %zu bytes of scratch for %d boxes x %d rhs; the fixed area "
+                         "holds %zu bytes (use ie_translate)", need, p->nbox, nrhs, kNoAllocScratchBytes),
+               IE_ERR_INVALID;
+    int per = kTileN / nrhs;
+    int64_t maxg = 0;
+    for (int64_t d = 0; d < p->n_far_disp; ++d) maxg = std::max<int64_t>(maxg, p->h_gstart[d + 1] - p->h_gstart[d]);
+    int64_t runs = (maxg + per - 1) / per;
+    if (runs > 65535) return set_error("displacement group too large for ie_translate_noalloc"), IE_ERR_INVALID;
+    void *base = nullptr;
+    IE_TRY(noalloc_scratch(&base));
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t *d_gstart = reinterpret_cast<int64_t *>(base);
+    float2 *slabs = reinterpret_cast<float2 *>(static_cast<unsigned char *>(base) + off_bytes);
+    // the area keeps the previous call's contents: the slabs must start at zero
+    IE_TRY(launch_zero(slabs, (size_t)kSlabs * stride * sizeof(float2), st));
+    if (p->n_far_disp > 0) {
+        IE_CK(cudaMemcpyAsync(d_gstart, p->h_gstart.data(), (size_t)(p->n_far_disp + 1) * sizeof(int64_t),
+                              cudaMemcpyHostToDevice, st));
+        translate_simt_grouped_kernel<<<dim3((unsigned)p->n_far_disp, (unsigned)runs), kThreads, sizeof(SmemSimt),
+                                        st>>>(d_gstart, p->d_Csimt, p->d_src, p->d_dst, (const float2 *)X, slabs,
+                                              stride, p->nbox, nrhs, per);
+        IE_CK_LAUNCH();
+    }
+    return launch_sum_slabs(p, slabs, kSlabs, stride, (float2 *)Y, nrhs, st);
+}
