@@ -1,15 +1,395 @@
-// K3 (tensor-core path): placeholder until the tcgen05 kernel lands.
+// K3 (tensor-core path): translation stage (Alg. 2) on the 5th-generation tensor
+// cores (tcgen05.mma, accumulators in TMEM), sm_103a.
+//
+// Complex GEMM in real form.  For one displacement d the coupling block G = Gr + j Gi
+// (192 x 192, eq. 13) is stored as a 384 x 192 real matrix A with row 2m = Gr[m][:],
+// row 2m+1 = Gi[m][:]; a source vector x = xr + j xi becomes two B rows (xr and xi).
+// The product A B^T then holds Gr xr, Gr xi, Gi xr, Gi xi in adjacent TMEM lanes /
+// columns, and the epilogue forms y = (Gr xr - Gi xi) + j (Gr xi + Gi xr) with one lane
+// exchange.  Split precision: every operand is hi + lo in 16 bits (bf16 or fp16), and
+// D = Ahi Bhi + Ahi Blo + Alo Bhi is accumulated in FP32 (BF16X1: Ahi Bhi only).
+//
+// Work item = (displacement, M-block of 128 real rows, run of <= 128 complex columns).
+// Persistent CTAs walk the size-sorted item list round-robin.  Warp roles:
+//   warps 0-3  producers: per K-chunk of 64, one elected thread bulk-copies the two
+//              pre-swizzled 16 KB A images (TMA engine, mbarrier complete_tx); all 128
+//              threads gather the B rows of the item's columns with 16-byte cp.async
+//              into the SW128 K-major layout (chunk c of row n at c ^ (n mod 8)).
+//   warp 4     MMA issuer: one thread issues tcgen05.mma (M=128, N<=256, K=16) from the
+//              two-stage ring into one of two TMEM accumulators (2 x 256 columns).
+//   warps 5-8  epilogue: tcgen05.ld of their TMEM lane quarter, complex recombination,
+//              power-of-two rescaling (fp16), red.global.add into the slab (d mod 8).
+// Every mbarrier wait is bounded; a wait that gives up sets the device error word,
+// the CTA drains its own copies, frees its TMEM and returns.
+#include <algorithm>
+
 #include "ie_internal.h"
 
 namespace ie {
+namespace {
 
-int tc_tile_columns() { return 128; }
+constexpr int kTcTileCols = 128;                 // complex columns per work item (N <= 256)
+constexpr int kStages = 2;
+constexpr int kProducerThreads = 128;
+constexpr int kEpilogueThreads = 128;
+constexpr int kThreadsTc = kProducerThreads + 32 + kEpilogueThreads;   // 288
+constexpr int kImgBytes = 128 * 64 * 2;          // 16 KB
+constexpr int kBBytes = 256 * 128;               // 32 KB (256 rows x 64 x 16 bit)
+constexpr int kStageBytes = 2 * kImgBytes + 2 * kBBytes;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*barriers*/ + 1024 /*alignment*/;
+constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kSpinLimit = 1u << 24;
 
-ie_status prepare_translate_tc() { return IE_OK; }
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-ie_status launch_translate_tc(ie_plan, int, float2 *, int, cudaStream_t, const int *) {
-    set_error("tensor-core translation not built");
-    return IE_ERR_UNSUPPORTED;
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false when the limit is hit or another thread already gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (i > 32) __nanosleep(64);
+    }
+    *abort_flag = 1;
+    return false;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);     // start address
+    d |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset
+    d |= (uint64_t)1 << 46;                      // descriptor version
+    d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulate, A and B both bf16 or both fp16,
+// both K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t f16_idesc(int n, bool fp16) {
+    uint32_t d = 0;
+    d |= 1u << 4;                        // D: F32
+    d |= (fp16 ? 0u : 1u) << 7;          // A: F16 = 0, BF16 = 1
+    d |= (fp16 ? 0u : 1u) << 10;         // B
+    d |= (uint32_t)(n >> 3) << 17;
+    d |= (uint32_t)(128 >> 4) << 24;
+    return d;
+}
+
+__device__ __forceinline__ void umma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct TcArgs {
+    const WorkItem *items;
+    int64_t n_items;
+    const uint16_t *C;          // [disp][18 images]
+    const int32_t *Cexp;        // [disp] or null
+    const uint16_t *Xtc;        // [hl][col][reim][192]
+    const int32_t *Xexp;        // [col]
+    int64_t plane;              // elements per hl plane of Xtc
+    const int32_t *src, *dst;
+    float *Yslab;               // float view of the complex64 slabs
+    size_t slab_stride;         // complex elements between slabs
+    int nbox, nrhs;
+    int *err;
+    const int *gate;
+};
+
+template <bool FP16, bool X3>
+__global__ void __launch_bounds__(kThreadsTc, 1) translate_tc_kernel(TcArgs a) {
+    if (a.gate && *a.gate == 0) return;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *bars = smem + kStages * kStageBytes;
+    uint64_t *full = reinterpret_cast<uint64_t *>(bars);          // [kStages]
+    uint64_t *empty = full + kStages;                              // [kStages]
+    uint64_t *accfull = empty + kStages;                           // [2]
+    uint64_t *accempty = accfull + 2;                              // [2]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accempty + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(smem_u32(&full[s]), kProducerThreads + 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&accfull[b]), 1);
+            mbar_init(smem_u32(&accempty[b]), kEpilogueThreads);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    const int64_t first = blockIdx.x, step = gridDim.x;
+    if (warp < 4) {
+        // ---------------- producers
+        const int tid = threadIdx.x;
+        int64_t il = 0;
+        int64_t armed[kStages];
+        for (int s = 0; s < kStages; ++s) armed[s] = -1;
+        bool ok = true;
+        for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
+            const WorkItem it = a.items[i];
+            const int ncols = it.npairs * a.nrhs;
+            const int nreal = 2 * ncols;
+            const uint16_t *Cd = a.C + (int64_t)it.disp * kTcDispElems;
+            for (int kc = 0; kc < 3 && ok; ++kc) {
+                const int64_t g = il * 3 + kc;
+                const int s = (int)(g % kStages);
+                const uint32_t ph = (uint32_t)((g / kStages) & 1);
+                if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char *st = smem + s * kStageBytes;
+                const uint32_t sA = smem_u32(st), sB = smem_u32(st + 2 * kImgBytes);
+                if (tid == 0) {
+                    const uint32_t fb = smem_u32(&full[s]);
+                    mbar_arrive_expect_tx(fb, X3 ? 2 * kImgBytes : kImgBytes);
+                    armed[s] = g;
+                    const uint16_t *img = Cd + (int64_t)((it.mb * 3 + kc) * 2) * kTcImageElems;
+                    bulk_copy_g2s(sA, img, kImgBytes, fb);
+                    if (X3) bulk_copy_g2s(sA + kImgBytes, img + kTcImageElems, kImgBytes, fb);
+                }
+                for (int n = tid; n < nreal; n += kProducerThreads) {
+                    const int j = n >> 1, part = n & 1;
+                    const int p = it.pair0 + j / a.nrhs, r = j % a.nrhs;
+                    const int64_t row = 2 * ((int64_t)r * a.nbox + a.src[p]) + part;
+                    const uint16_t *gsrc = a.Xtc + row * kNU + kc * 64;
+                    const uint32_t rbase = (uint32_t)((n >> 3) * 1024 + (n & 7) * 128);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const uint32_t off = rbase + (uint32_t)((c ^ (n & 7)) * 16);
+                        cp_async16(sB + off, gsrc + c * 8);
+                        if (X3) cp_async16(sB + kBBytes + off, gsrc + a.plane + c * 8);
+                    }
+                }
+                cp_async_wait_all();
+                fence_proxy_async();
+                mbar_arrive(smem_u32(&full[s]));
+            }
+        }
+        cp_async_wait_all();
+        if (!ok) {
+            atomicExch(a.err, 1);
+            // drain: every stage this CTA armed completes once its bulk bytes land
+            if (tid == 0) {
+                for (int s = 0; s < kStages; ++s) {
+                    if (armed[s] < 0) continue;
+                    const uint32_t ph = (uint32_t)((armed[s] / kStages) & 1);
+                    for (uint32_t w = 0; w < kSpinLimit && !mbar_try_wait(smem_u32(&full[s]), ph); ++w) __nanosleep(64);
+                }
+            }
+        }
+    } else if (warp == 4) {
+        // ---------------- MMA issuer
+        int64_t il = 0;
+        bool ok = true;
+        for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
+            const WorkItem it = a.items[i];
+            const int ncols = it.npairs * a.nrhs;
+            const int nmma = (2 * ncols + 15) & ~15;
+            const uint32_t idesc = f16_idesc(nmma, FP16);
+            const int buf = (int)(il & 1);
+            const uint32_t aph = (uint32_t)((il >> 1) & 1);
+            if (!mbar_wait(smem_u32(&accempty[buf]), aph ^ 1, abort_flag)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t dt = tmem_base + (uint32_t)(buf * 256);
+            for (int kc = 0; kc < 3 && ok; ++kc) {
+                const int64_t g = il * 3 + kc;
+                const int s = (int)(g % kStages);
+                const uint32_t ph = (uint32_t)((g / kStages) & 1);
+                if (!mbar_wait(smem_u32(&full[s]), ph, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                if (lane == 0) {
+                    unsigned char *st = smem + s * kStageBytes;
+                    const uint32_t sA = smem_u32(st), sB = smem_u32(st + 2 * kImgBytes);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint64_t ah = sw128_desc(sA + k * 32), bh = sw128_desc(sB + k * 32);
+                        umma(dt, ah, bh, idesc, (kc | k) ? 1u : 0u);
+                        if (X3) {
+                            const uint64_t al = sw128_desc(sA + kImgBytes + k * 32);
+                            const uint64_t bl = sw128_desc(sB + kBBytes + k * 32);
+                            umma(dt, ah, bl, idesc, 1u);
+                            umma(dt, al, bh, idesc, 1u);
+                        }
+                    }
+                    umma_commit(smem_u32(&empty[s]));
+                    if (kc == 2) umma_commit(smem_u32(&accfull[buf]));
+                }
+                __syncwarp();
+            }
+        }
+        if (!ok) atomicExch(a.err, 1);
+    } else {
+        // ---------------- epilogue
+        const int q = warp & 3;                        // TMEM lane quarter
+        const int64_t slab_f = (int64_t)a.slab_stride * 2;
+        int64_t il = 0;
+        bool ok = true;
+        for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
+            const WorkItem it = a.items[i];
+            const int ncols = it.npairs * a.nrhs;
+            const int buf = (int)(il & 1);
+            const uint32_t aph = (uint32_t)((il >> 1) & 1);
+            if (!mbar_wait(smem_u32(&accfull[buf]), aph, abort_flag)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const int ed = FP16 ? a.Cexp[it.disp] : 0;
+            const int m0 = 64 * it.mb + 16 * q;        // first complex row of this warp
+            float *Ys = a.Yslab + (int64_t)(it.disp % kSlabs) * slab_f;
+            const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256);
+            for (int c0 = 0; c0 < 2 * ncols; c0 += 16) {
+                float v[16];
+                tmem_ld16(tbase + (uint32_t)c0, v);
+#pragma unroll
+                for (int jj = 0; jj < 8; ++jj) {
+                    const int j = (c0 >> 1) + jj;
+                    if (j >= ncols) break;             // warp-uniform
+                    const float ob = __shfl_xor_sync(0xffffffffu, v[2 * jj + 1], 1);
+                    float val = (lane & 1) ? v[2 * jj] + ob : v[2 * jj] - ob;
+                    const int p = it.pair0 + j / a.nrhs, r = j % a.nrhs;
+                    const int64_t col = (int64_t)r * a.nbox + a.dst[p];
+                    if (FP16) val = ldexpf(val, ed + a.Xexp[(int64_t)r * a.nbox + a.src[p]]);
+                    atomicAdd(Ys + col * (2 * kNU) + 2 * m0 + lane, val);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(smem_u32(&accempty[buf]));
+        }
+        if (!ok) atomicExch(a.err, 1);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 4) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols));
+    }
+}
+
+template <bool FP16, bool X3>
+ie_status set_attr() {
+    IE_CK(cudaFuncSetAttribute(translate_tc_kernel<FP16, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    return IE_OK;
+}
+
+}  // namespace
+
+int tc_tile_columns() { return kTcTileCols; }
+
+ie_status prepare_translate_tc() {
+    IE_TRY((set_attr<false, true>()));
+    IE_TRY((set_attr<true, true>()));
+    IE_TRY((set_attr<false, false>()));
+    return IE_OK;
+}
+
+ie_status launch_translate_tc(ie_plan p, int prec, float2 *Yslab, int nrhs, cudaStream_t st, const int *gate) {
+    const bool fp16 = prec == IE_PREC_FP16X3;
+    const uint16_t *C = fp16 ? p->d_Cfp16 : p->d_Cbf16;
+    if (!C) return set_error("tensor-core coupling store for precision %d not built", prec), IE_ERR_UNSUPPORTED;
+    WorkList *wl = nullptr;
+    IE_TRY(work_list(p, true, nrhs, &wl));
+    if (wl->n == 0) return IE_OK;
+    TcArgs a;
+    a.items = wl->d_items;
+    a.n_items = wl->n;
+    a.C = C;
+    a.Cexp = fp16 ? p->d_Cexp16 : nullptr;
+    a.Xtc = p->d_Xtc;
+    a.Xexp = p->d_Xexp;
+    a.plane = (int64_t)nrhs * p->nbox * 2 * kNU;
+    a.src = p->d_src;
+    a.dst = p->d_dst;
+    a.Yslab = reinterpret_cast<float *>(Yslab);
+    a.slab_stride = slab_stride(p);
+    a.nbox = p->nbox;
+    a.nrhs = nrhs;
+    a.err = p->d_err;
+    a.gate = gate;
+    int grid = (int)std::min<int64_t>(wl->n, p->tc_sms > 0 ? p->tc_sms : 148);
+    if (prec == IE_PREC_BF16X3)
+        translate_tc_kernel<false, true><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
+    else if (prec == IE_PREC_FP16X3)
+        translate_tc_kernel<true, true><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
+    else if (prec == IE_PREC_BF16X1)
+        translate_tc_kernel<false, false><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
+    else
+        return set_error("not a tensor-core precision: %d", prec), IE_ERR_INVALID;
+    IE_CK_LAUNCH();
+    return IE_OK;
 }
 
 }  // namespace ie

@@ -1,0 +1,133 @@
+"""GPU parity of the tcgen05 translation and the mixed-precision solve against the
+FP64 oracle, through the C ABI.
+
+Stated bounds (relative L2), from the split arithmetic: bf16 hi + lo keeps ~16
+significant bits and the dropped lo*lo term is ~2^-16 of each product, so BF16X3
+<= 5e-5; fp16 hi + lo keeps ~22 bits, FP16X3 <= 2e-6; one bf16 product (8 bits)
+BF16X1 <= 1e-2.  The mixed solve (inner GMRES on BF16X3 products, FP64 refinement
+residual from FP32 products) must reach a true residual <= 1e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2501_04684_gb300 as ie
+import workloads as W
+from gpu_util import dev, empty, host, plan_for, rel_l2
+from test_gpu_parity import ragged_problem
+
+pytestmark = pytest.mark.gpu
+BOUND = {ie.IE_PREC_BF16X3: 5e-5, ie.IE_PREC_FP16X3: 2e-6, ie.IE_PREC_BF16X1: 1e-2}
+TC = [ie.IE_PREC_BF16X3, ie.IE_PREC_FP16X3, ie.IE_PREC_BF16X1]
+ALL = [ie.IE_PREC_FP32] + TC
+
+
+def _name(p):
+    return ie.PREC_NAMES[p]
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    p = W.tiny()
+    p.alpha = W.alpha_for("tiny")
+    return p
+
+
+@pytest.mark.parametrize("prec", TC, ids=_name)
+def test_tc_translate_tiny(prec, tiny):
+    Xr = oracle.aggregate(tiny, W.coefficients(tiny, 1, 400))
+    Yr = oracle.dipole_field(tiny, Xr, oracle.FAR)
+    with plan_for(tiny, precs=ALL) as plan:
+        Y = empty(Xr.shape)
+        ie.ie_translate(plan.handle, prec, dev(Xr), Y, 1)
+        assert rel_l2(host(Y), Yr) <= BOUND[prec]
+
+
+@pytest.mark.parametrize("prec", TC, ids=_name)
+def test_tc_translate_ragged_multi_rhs(prec):
+    p, c = ragged_problem(seed=410, nrhs=3)
+    Xr = oracle.aggregate(p, c)
+    Yr = oracle.dipole_field(p, Xr, oracle.FAR)
+    with plan_for(p, precs=ALL, max_rhs=3) as plan:
+        Y = empty(Xr.shape)
+        ie.ie_translate(plan.handle, prec, dev(Xr), Y, 3)
+        got = host(Y)
+        for r in range(3):
+            assert rel_l2(got[r], Yr[r]) <= BOUND[prec]
+
+
+@pytest.mark.parametrize("prec", TC, ids=_name)
+def test_tc_full_matvec_tiny(prec, tiny):
+    c = W.coefficients(tiny, 2, 401)
+    ref = oracle.operator(tiny, c, "full")
+    with plan_for(tiny, precs=ALL, max_rhs=2) as plan:
+        y = empty((2, tiny.n))
+        ie.ie_matvec(plan.handle, ie.IE_FULL, prec, dev(c), y, 2)
+        assert rel_l2(host(y), ref) <= BOUND[prec]
+
+
+def test_tc_degenerate_and_large_dynamic_range():
+    """One far pair each way, and P scaled by 2^20 (fp16 needs its per-block scaling)."""
+    g = W.rng(402)
+    ijk = np.array([(0, 0, 0), (2, 0, 0), (0, 7, 1)], dtype=np.int32)
+    nb = np.array([1, 192, 40], dtype=np.int32)
+    P = W.random_P(g, nb) * 2.0 ** 20
+    p = W.Problem(name="deg", G=10, box_ijk=ijk, nb=nb, P=P, alpha=1.0)
+    c = W.coefficients(p, 1, 403)
+    ref = oracle.far_matvec(p, c)
+    with plan_for(p, precs=ALL) as plan:
+        for prec in TC:
+            y = empty((1, p.n))
+            ie.ie_matvec(plan.handle, ie.IE_FAR, prec, dev(c), y, 1)
+            assert rel_l2(host(y), ref) <= BOUND[prec], _name(prec)
+
+
+@pytest.mark.parametrize("prec", [ie.IE_PREC_BF16X3, ie.IE_PREC_FP16X3], ids=_name)
+def test_tc_full_size_shell16_sampled(prec):
+    p = W.shell16()
+    c = W.coefficients(p, 1, W.SEED_C["shell16"])
+    targets = W.subsample_boxes(p, 12, W.SEED_SUBSAMPLE["shell16"])
+    with plan_for(p, precs=[ie.IE_PREC_FP32, prec]) as plan:
+        y = empty((1, p.n))
+        ie.ie_matvec(plan.handle, ie.IE_FAR, prec, dev(c), y, 1)
+        got = host(y)[:, oracle.basis_rows(p, targets)]
+    ref = oracle.far_matvec(p, c, targets=targets)
+    assert rel_l2(got, ref) <= BOUND[prec]
+
+
+@pytest.mark.parametrize("inner", [ie.IE_PREC_BF16X3, ie.IE_PREC_BF16X1], ids=_name)
+def test_mixed_solve_with_refinement_tiny(inner, tiny):
+    Z = oracle.dense_operator(tiny)
+    kh, pol = W.plane_wave_spec(2, seed=404)
+    v = oracle.plane_wave_rhs(tiny, kh, pol)
+    with plan_for(tiny, precs=ALL, max_rhs=2) as plan:
+        x = empty((2, tiny.n))
+        st, info = ie.ie_solve(plan.handle, dev(v), x, 2,
+                               ie.solve_opts(tol=1e-5, prec=inner, refine=1, refine_prec=ie.IE_PREC_FP32,
+                                             inner_tol=1e-3 if inner == ie.IE_PREC_BF16X3 else 1e-2))
+        assert st == ie.IE_OK, info
+        xs = host(x)
+    for r in range(2):
+        res = np.linalg.norm(v[r] - Z @ xs[r]) / np.linalg.norm(v[r])
+        assert res <= 1e-5, (r, res)
+
+
+def test_mixed_solve_shell16_true_residual():
+    p = W.shell16()
+    p.alpha = W.alpha_for("shell16")
+    kh, pol = W.plane_wave_spec(1)
+    targets = W.subsample_boxes(p, 12, W.SEED_SUBSAMPLE["shell16"])
+    with plan_for(p, precs=[ie.IE_PREC_FP32, ie.IE_PREC_BF16X3]) as plan:
+        v = empty((1, p.n))
+        ie.ie_rhs_plane_wave(plan.handle, kh, pol, v)
+        x = empty((1, p.n))
+        st, info = ie.ie_solve(plan.handle, v, x, 1,
+                               ie.solve_opts(tol=1e-5, prec=ie.IE_PREC_BF16X3, refine=1,
+                                             refine_prec=ie.IE_PREC_FP32, inner_tol=1e-3))
+        assert st == ie.IE_OK, info
+        xs = host(x)
+    vref = oracle.plane_wave_rhs(p, kh, pol)
+    rows = oracle.basis_rows(p, targets)
+    Zx = oracle.operator(p, xs, "full", targets=targets)
+    res = np.linalg.norm(Zx - vref[:, rows]) / np.linalg.norm(vref[:, rows])
+    assert res <= 1e-5, res
