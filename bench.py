@@ -186,7 +186,7 @@ def main():
 
     p = W.shell16()
     p.alpha = W.alpha_for("shell16")
-    precs = [ie.IE_PREC_FP32]
+    precs = [ie.IE_PREC_FP32, ie.IE_PREC_BF16X3, ie.IE_PREC_FP16X3, ie.IE_PREC_BF16X1]
     t0 = time.perf_counter()
     plan = ie.Plan(ie.problem_from(p, ie.precmask(*precs)), stream)
     plan_s = time.perf_counter() - t0
@@ -195,38 +195,49 @@ def main():
     v = torch.zeros((1, p.n), dtype=torch.complex64, device=dev)
     ie.ie_rhs_plane_wave(plan.handle, kh, pol, v, stream)
     x = torch.zeros_like(v)
-    path = dict(name="plain", opts=ie.solve_opts(tol=1e-6, restart=50, prec=ie.IE_PREC_FP32), dtype="f32")
+    paths = {name: dict(spec, opts=ie.solve_opts(**spec["opts"])) for name, spec in solve_paths(ie).items()}
 
-    def solve_once():
+    def solve_once(path):
         s, info = ie.ie_solve(plan.handle, v, x, 1, path["opts"], stream)
         if s != ie.IE_OK:
             raise RuntimeError(f"solve did not converge: {info}")
         return info
 
-    # warm-up (graph capture, work lists)
-    for _ in range(max(3, args.warmup)):
-        info = solve_once()
-    torch.cuda.synchronize()
-
-    # ---- timed region: K solves, CUDA events on the solve stream
-    launches0 = ie.ie_kernel_launches()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    infos = []
-    barrier(world)
-    torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        for k in range(args.steps):
-            ev[k][0].record(stream)
-            infos.append(solve_once())
-            ev[k][1].record(stream)
+    def time_path(path, steps, clocks=False):
+        for _ in range(max(3, args.warmup)):
+            solve_once(path)
         torch.cuda.synchronize()
-    barrier(world)
-    launches = ie.ie_kernel_launches() - launches0
-    lat = [a.elapsed_time(b) for a, b in ev]
-    total_ms = max_over_ranks(sum(lat), world)
-    solves_per_s = world * args.steps / (total_ms / 1e3)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        infos = []
+        barrier(world)
+        torch.cuda.synchronize()
+        l0 = ie.ie_kernel_launches()
+        clk = Clocks(local) if clocks else None
+        if clk:
+            clk.__enter__()
+        try:
+            for k in range(steps):
+                ev[k][0].record(stream)
+                infos.append(solve_once(path))
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+        finally:
+            if clk:
+                clk.__exit__()
+        barrier(world)
+        lat = [a.elapsed_time(b) for a, b in ev]
+        total = max_over_ranks(sum(lat), world)
+        return dict(solves_per_s=world * steps / (total / 1e3), ms=total / steps,
+                    p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+                    iterations=infos[-1]["iterations"], matvecs=infos[-1]["matvecs"],
+                    refinements=infos[-1]["refinements"], relres=infos[-1]["relres"],
+                    launches=ie.ie_kernel_launches() - l0, clocks=clk.summary() if clk else None)
 
-    # ---- far-zone products and the translation kernel (events on the launching stream)
+    # ---- timed region: K solves of the headline path (CUDA events on the solve stream)
+    head = time_path(paths[HEADLINE], args.steps, clocks=True)
+    others = {name: time_path(path, args.steps) for name, path in paths.items() if name != HEADLINE}
+
+    # ---- far-zone products per precision and the translation kernel's own time
     nfar = max(5, args.steps)
     c = torch.from_numpy(W.coefficients(p, 1, W.SEED_C["shell16"]).astype(np.complex64)).to(dev)
     y = torch.zeros_like(c)
@@ -241,7 +252,7 @@ def main():
             ie.ie_matvec(plan.handle, ie.IE_FAR, prec, c, y, 1, stream)
         e1.record(stream)
         torch.cuda.synchronize()
-        mv_ms = e0.elapsed_time(e1) / nfar
+        mv_ms = max_over_ranks(e0.elapsed_time(e1), world) / nfar
         ie.ie_plan_profile(plan.handle, True)
         for _ in range(nfar):
             ie.ie_matvec(plan.handle, ie.IE_FAR, prec, c, y, 1, stream)
@@ -249,7 +260,7 @@ def main():
         s2 = ie.ie_plan_stats_get(plan.handle)
         ie.ie_plan_profile(plan.handle, False)
         k_ms = s2["translate_ms"] / max(1, s2["translate_launches"])
-        far[ie.PREC_NAMES[prec]] = dict(matvecs_per_s=1e3 / mv_ms, ms=mv_ms, translate_kernel_ms=k_ms)
+        far[ie.PREC_NAMES[prec]] = dict(matvecs_per_s=world * 1e3 / mv_ms, ms=mv_ms, translate_kernel_ms=k_ms)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     vh = v.cpu().pin_memory()
@@ -259,7 +270,7 @@ def main():
     e0.record(stream)
     for _ in range(args.steps):
         v.copy_(vh, non_blocking=True)
-        solve_once()
+        solve_once(paths[HEADLINE])
         xh.copy_(x, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -268,39 +279,81 @@ def main():
            "h2d_bytes_per_step": int(vh.numel() * vh.element_size()),
            "d2h_bytes_per_step": int(xh.numel() * xh.element_size())}
 
-    # ---- roofline of the dominant kernel (translation, FP32 SIMT path)
-    flops_per_launch = st["n_far_pairs"] * 1 * 8 * 192 * 192
-    k_ms = far["fp32"]["translate_kernel_ms"]
-    achieved = flops_per_launch / (k_ms / 1e3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_SIMT_PEAK_TFLOPS, "traffic": None,
-                "kernel": "translate_simt_kernel", "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    # ---- roofline of the dominant kernel of the headline path
+    pairs = st["n_far_pairs"]
+    peaks = measured_peaks()
+    tc_flops = 3 * pairs * 8 * 192 * 192                      # three bf16 products per complex MAC term
+    tc_ms = far["bf16x3"]["translate_kernel_ms"]
+    tc_ach = tc_flops / (tc_ms / 1e3) / 1e12
+    roofline = {"bound": "tensor", "achieved": tc_ach, "peak": peaks["bf16"], "unit": "TFLOP/s",
+                "frac": tc_ach / peaks["bf16"], "traffic": None, "kernel": "translate_tc_kernel<bf16,x3>",
+                "peak_source": peaks["source"]}
+    simt_ach = pairs * 8 * 192 * 192 / (far["fp32"]["translate_kernel_ms"] / 1e3) / 1e12
+    roofline_fp32 = {"bound": "alu", "achieved": simt_ach, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": simt_ach / FP32_SIMT_PEAK_TFLOPS, "kernel": "translate_simt_kernel",
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
 
+    hp = paths[HEADLINE]
     result = {
-        "metric": METRIC, "value": solves_per_s, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": path["dtype"], "data": "synthetic",
-        "config": {"workload": WORKLOAD, "path": path["name"], "tol": path["opts"].tol, "nrhs": 1,
-                   "l2": "no flush needed: each product streams 4.9 GB of coupling blocks (> 129 MB L2)",
+        "metric": METRIC, "value": head["solves_per_s"], "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": hp["dtype"], "data": "synthetic",
+        "config": {"workload": WORKLOAD, "path": HEADLINE, "path_desc": hp["desc"], "tol": hp["opts"].tol,
+                   "nrhs": 1, "l2": "no flush needed: each product streams >= 4.9 GB of coupling blocks (> 129 MB L2)",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "solve": {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                  "iterations": infos[-1]["iterations"], "matvecs": infos[-1]["matvecs"],
-                  "relres": infos[-1]["relres"]},
+        "solve": {k: head[k] for k in ("p50_ms", "p99_ms", "iterations", "matvecs", "refinements", "relres")},
+        "vs_plain_fp32": head["solves_per_s"] / others["plain"]["solves_per_s"],
+        "paths": {name: {k: r[k] for k in ("solves_per_s", "p50_ms", "p99_ms", "iterations", "matvecs", "refinements",
+                                           "relres")} | {"desc": paths[name]["desc"]}
+                  for name, r in others.items()},
         "far_matvecs": far,
         "plan_seconds": plan_s,
-        "gpu_launches": int(launches),
-        "clocks": clk.summary(),
+        "gpu_launches": int(head["launches"]),
+        "clocks": head["clocks"],
         "e2e": e2e,
         "roofline": roofline,
+        "roofline_fp32": roofline_fp32,
     }
     if rank == 0 and world == 1:
-        result["cpu_baseline"] = cpu_baseline(p, infos[-1]["iterations"])
+        result["cpu_baseline"] = cpu_baseline(p, head["matvecs"])
     plan.close()
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def solve_paths(ie) -> dict:
+    """Solve forms measured on the workload; HEADLINE is the value's step."""
+    return {
+        "mixed": dict(opts=dict(tol=1e-5, restart=50, prec=ie.IE_PREC_BF16X3, refine=1,
+                                refine_prec=ie.IE_PREC_FP16X3, inner_tol=1e-3),
+                      dtype="bf16x3 tensor products, f32 GMRES, f64 refinement",
+                      desc="outer FP64 refinement (residual from FP16X3 products) around GMRES(50) on BF16X3 "
+                           "products to 1e-3; stop at 1e-5"),
+        "mixed_bf16x1": dict(opts=dict(tol=1e-5, restart=50, prec=ie.IE_PREC_BF16X1, refine=1,
+                                       refine_prec=ie.IE_PREC_FP16X3, inner_tol=1e-2),
+                             dtype="bf16 tensor products, f32 GMRES, f64 refinement",
+                             desc="refinement (FP16X3 residual) around GMRES(50) on single bf16 products to 1e-2"),
+        "fp16x3": dict(opts=dict(tol=1e-5, restart=50, prec=ie.IE_PREC_FP16X3), dtype="fp16x3",
+                       desc="GMRES(50) on FP16X3 products to 1e-5, no refinement"),
+        "plain": dict(opts=dict(tol=1e-6, restart=50, prec=ie.IE_PREC_FP32), dtype="f32",
+                      desc="plain FP32 path: GMRES(50) on FP32 SIMT products to 1e-6"),
+    }
+
+
+HEADLINE = "mixed"
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return {"bf16": float(d["bf16_tflops"]), "bf16_sustained": float(d["bf16_tflops_sustained"]),
+                "hbm": float(d["hbm_gbs"]), "source": "of measured (MEASURED_PEAKS.json, burst bf16)"}
+    except (OSError, KeyError, ValueError):
+        return {"bf16": 1900.0, "bf16_sustained": 1700.0, "hbm": 6800.0, "source": "of fallback"}
 
 
 def cpu_baseline(p, iters: int) -> dict:

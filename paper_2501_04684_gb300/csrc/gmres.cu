@@ -30,7 +30,11 @@ struct ie_solver_s {
     double2 *partial = nullptr;  // [R][m+1][nblk]
     double *bnorm = nullptr;     // [R]
     double *relres = nullptr;    // [R]
-    int *st = nullptr;           // [2 + 4R]: any_active, any_not_done, done[R], active[R], jend[R], iters[R]
+    int *st = nullptr;           // [4 + 4R]: any_active, any_not_done, done[R], active[R], jend[R], iters[R], j, body runs
+    float2 *Vcur = nullptr;      // [R][n] current Krylov vector (input of the product)
+    cudaGraphConditionalHandle hcond = 0;
+    bool use_while = false;
+    int64_t body_kernels = 0, end_kernels = 0, body_runs_seen = 0;
     const float2 *v = nullptr;
     float2 *x = nullptr;
     const float2 *cap_v = nullptr;   // pointers baked into the captured cycle
@@ -39,7 +43,6 @@ struct ie_solver_s {
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev = nullptr;
     int matvecs_per_cycle = 0;
-    int64_t graph_kernels = 0;
     int cycles_run = 0;
     std::vector<void *> allocs;
     size_t bytes = 0;
@@ -56,6 +59,13 @@ __device__ inline int *st_done(int *st, int R) { return st + 2; }
 __device__ inline int *st_active(int *st, int R) { return st + 2 + R; }
 __device__ inline int *st_jend(int *st, int R) { return st + 2 + 2 * R; }
 __device__ inline int *st_iters(int *st, int R) { return st + 2 + 3 * R; }
+__device__ inline int *st_jdev(int *st, int R) { return st + 2 + 4 * R; }     // Arnoldi index of the cycle
+__device__ inline int *st_body(int *st, int R) { return st + 3 + 4 * R; }     // iterations run by the graph
+
+// j >= 0: index given by the launch; kDevJ: read the cycle's index from device memory
+// (the WHILE-node graph runs one body for every iteration).
+constexpr int kDevJ = -2;
+__device__ inline int resolve_j(int j, int *st, int R) { return j >= 0 ? j : *st_jdev(st, R); }
 
 __device__ inline double2 block_sum2(double2 v) {
     __shared__ double2 red[kDotThreads / 32];
@@ -76,9 +86,10 @@ __device__ inline double2 block_sum2(double2 v) {
 // partial[r][i][blk] = sum over the block's slice of conj(V_i[r]) . W[r], i <= j.
 // j < 0: partial[r][0][blk] = sum |W[r]|^2 (norm pass).  Only rows with active[r]
 // (or not done[r] when use_done) take part.
-__global__ void dots_kernel(const float2 *__restrict__ V, const float2 *__restrict__ Wv, int64_t n, int R, int j,
-                            double2 *__restrict__ partial, int nblk, int m, int *st, int use_done) {
+__global__ void dots_kernel(const float2 *__restrict__ V, const float2 *__restrict__ Wv, int64_t n, int R, int jarg,
+                            double2 *__restrict__ partial, int nblk, int m, int *st, int use_done, int norm) {
     int r = blockIdx.y, blk = blockIdx.x;
+    const int j = norm ? -1 : resolve_j(jarg, st, R);
     bool on = use_done ? !st_done(st, R)[r] : st_active(st, R)[r];
     if (!on) return;
     int64_t base = (int64_t)blk * kChunk;
@@ -115,10 +126,11 @@ __global__ void dots_kernel(const float2 *__restrict__ V, const float2 *__restri
 }
 
 // hbuf[r][i] = sum_blk partial; H[r][j][i] += hbuf (Arnoldi coefficient of pass).
-__global__ void reduce_dots_kernel(const double2 *__restrict__ partial, int nblk, int m, int R, int j,
+__global__ void reduce_dots_kernel(const double2 *__restrict__ partial, int nblk, int m, int R, int jarg,
                                    double2 *__restrict__ hbuf, double2 *__restrict__ H, int *st) {
     int r = blockIdx.x;
     if (!st_active(st, R)[r]) return;
+    const int j = resolve_j(jarg, st, R);
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
         const double2 *p = partial + ((int64_t)r * (m + 1) + i) * nblk;
         double sx = 0, sy = 0;
@@ -131,10 +143,11 @@ __global__ void reduce_dots_kernel(const double2 *__restrict__ partial, int nblk
 }
 
 // W[r] -= sum_{i<=j} V_i[r] hbuf[r][i]
-__global__ void update_kernel(const float2 *__restrict__ V, float2 *__restrict__ Wv, int64_t n, int R, int j, int m,
-                              const double2 *__restrict__ hbuf, int *st) {
+__global__ void update_kernel(const float2 *__restrict__ V, float2 *__restrict__ Wv, int64_t n, int R, int jarg,
+                              int m, const double2 *__restrict__ hbuf, int *st) {
     int r = blockIdx.y;
     if (!st_active(st, R)[r]) return;
+    const int j = resolve_j(jarg, st, R);
     __shared__ float2 h[65];
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
         double2 v = hbuf[(int64_t)r * (m + 1) + i];
@@ -154,10 +167,11 @@ __global__ void update_kernel(const float2 *__restrict__ V, float2 *__restrict__
 }
 
 // ||W[r]|| -> H[r][j][j+1] (and hbuf[r][0] = norm for the scaling kernel).
-__global__ void norm_finish_kernel(const double2 *__restrict__ partial, int nblk, int m, int R, int j,
+__global__ void norm_finish_kernel(const double2 *__restrict__ partial, int nblk, int m, int R, int jarg,
                                    double2 *__restrict__ hbuf, double2 *__restrict__ H, int *st) {
     int r = blockIdx.x;
     if (!st_active(st, R)[r]) return;
+    const int j = resolve_j(jarg, st, R);
     if (threadIdx.x != 0) return;
     const double2 *p = partial + ((int64_t)r * (m + 1)) * nblk;
     double s = 0;
@@ -167,18 +181,22 @@ __global__ void norm_finish_kernel(const double2 *__restrict__ partial, int nblk
     hbuf[(int64_t)r * (m + 1)] = make_double2(hn, 0);
 }
 
-// V_{j+1}[r] = W[r] / hn
-__global__ void scale_kernel(const float2 *__restrict__ Wv, float2 *__restrict__ Vout, int64_t n, int R, int m,
-                             const double2 *__restrict__ hbuf, int *st) {
+// V_{j+1}[r] = W[r] / hn, also written to Vcur (the next product's input)
+__global__ void scale_kernel(const float2 *__restrict__ Wv, float2 *__restrict__ V, float2 *__restrict__ Vcur,
+                             int64_t n, int R, int m, const double2 *__restrict__ hbuf, int *st, int jarg) {
     int r = blockIdx.y;
     if (!st_active(st, R)[r]) return;
+    const int j = resolve_j(jarg, st, R);
     double hn = hbuf[(int64_t)r * (m + 1)].x;
     float s = hn > 0 ? (float)(1.0 / hn) : 0.f;
     const float2 *wr = Wv + (int64_t)r * n;
-    float2 *vr = Vout + (int64_t)r * n;
+    float2 *vr = V + ((int64_t)(j + 1) * R + r) * n;
+    float2 *cr = Vcur + (int64_t)r * n;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         float2 w = wr[e];
-        vr[e] = make_float2(w.x * s, w.y * s);
+        float2 o = make_float2(w.x * s, w.y * s);
+        vr[e] = o;
+        cr[e] = o;
     }
 }
 
@@ -189,8 +207,10 @@ __device__ inline double cabs2(double2 a) { return sqrt(a.x * a.x + a.y * a.y); 
 // Givens update of column j, residual estimate, per-RHS termination; one thread per RHS.
 __global__ void givens_kernel(double2 *__restrict__ H, double *__restrict__ cs, double2 *__restrict__ sn,
                               double2 *__restrict__ g, const double *__restrict__ bnorm, double *__restrict__ relres,
-                              int m, int R, int j, double tol, int max_iters, int *st) {
+                              int m, int R, int jarg, double tol, int max_iters, int *st,
+                              cudaGraphConditionalHandle cond) {
     int r = threadIdx.x;
+    const int j = resolve_j(jarg, st, R);
     __shared__ int any;
     if (threadIdx.x == 0) any = 0;
     __syncthreads();
@@ -238,7 +258,14 @@ __global__ void givens_kernel(double2 *__restrict__ H, double *__restrict__ cs, 
         if (st_active(st, R)[r]) any = 1;
     }
     __syncthreads();
-    if (threadIdx.x == 0) st[0] = any;
+    if (threadIdx.x == 0) {
+        st[0] = any;
+        if (jarg == kDevJ) {
+            *st_jdev(st, R) = j + 1;
+            *st_body(st, R) += 1;
+            cudaGraphSetConditional(cond, any ? 1u : 0u);   // WHILE node: run the next iteration?
+        }
+    }
 }
 
 // Back substitution H[0:jend,0:jend] y = g[0:jend]; y stored in hbuf[r].
@@ -348,20 +375,24 @@ __global__ void begin_cycle_kernel(const double2 *__restrict__ partial, int nblk
     if (threadIdx.x == 0) {
         st[0] = any_active;
         st[1] = any_open;
+        *st_jdev(st, R) = 0;
     }
 }
 
 // V_0[r] /= beta (hbuf[r][0]) for active rows.
-__global__ void scale_v0_kernel(float2 *__restrict__ V0, int64_t n, int R, int m, const double2 *__restrict__ hbuf,
-                                int *st) {
+__global__ void scale_v0_kernel(float2 *__restrict__ V0, float2 *__restrict__ Vcur, int64_t n, int R, int m,
+                                const double2 *__restrict__ hbuf, int *st) {
     int r = blockIdx.y;
     if (!st_active(st, R)[r]) return;
     double b = hbuf[(int64_t)r * (m + 1)].x;
     float s = (float)(1.0 / b);
     float2 *vr = V0 + (int64_t)r * n;
+    float2 *cr = Vcur + (int64_t)r * n;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         float2 a = vr[e];
-        vr[e] = make_float2(a.x * s, a.y * s);
+        float2 o = make_float2(a.x * s, a.y * s);
+        vr[e] = o;
+        cr[e] = o;
     }
 }
 
@@ -460,7 +491,8 @@ size_t solver_bytes(int64_t n, int R, int m) {
     b += (size_t)R * m * (sizeof(double) + sizeof(double2));
     b += (size_t)R * (m + 1) * sizeof(double2) * 2;
     b += (size_t)R * (m + 1) * nblk * sizeof(double2);
-    b += (size_t)R * 2 * sizeof(double) + (2 + 4 * R) * sizeof(int);
+    b += (size_t)R * 2 * sizeof(double) + (4 + 4 * R) * sizeof(int);
+    b += (size_t)R * n * sizeof(float2);
     return b;
 }
 
@@ -475,45 +507,139 @@ void fill_defaults(ie_solve_opts *o) {
     o->max_refine = 20;
 }
 
-// Enqueue `cycles` restart cycles on stream `st`.
-ie_status enqueue_cycle(ie_solver s, cudaStream_t st) {
+// One Arnoldi iteration (product, CGS2, norm, scaling, Givens).  jarg = kDevJ takes
+// the index from device memory (body of the WHILE node).
+ie_status enqueue_iteration(ie_solver s, cudaStream_t st, int jarg) {
     ie_plan p = s->plan;
     int R = s->R, m = s->m;
     int64_t n = s->n;
     dim3 vg(vec_grid(n), R), dg(s->nblk, R);
-    for (int j = 0; j < m; ++j) {
-        float2 *Vj = s->V + (int64_t)j * R * n;
-        IE_TRY(apply(p, IE_FULL, s->prec, Vj, s->W, R, st, s->st));
-        for (int pass = 0; pass < 2; ++pass) {
-            dots_kernel<<<dg, kDotThreads, 0, st>>>(s->V, s->W, n, R, j, s->partial, s->nblk, m, s->st, 0);
-            reduce_dots_kernel<<<R, 64, 0, st>>>(s->partial, s->nblk, m, R, j, s->hbuf, s->H, s->st);
-            update_kernel<<<vg, 256, 0, st>>>(s->V, s->W, n, R, j, m, s->hbuf, s->st);
-        }
-        dots_kernel<<<dg, kDotThreads, 0, st>>>(s->V, s->W, n, R, -1, s->partial, s->nblk, m, s->st, 0);
-        norm_finish_kernel<<<R, 32, 0, st>>>(s->partial, s->nblk, m, R, j, s->hbuf, s->H, s->st);
-        scale_kernel<<<vg, 256, 0, st>>>(s->W, s->V + (int64_t)(j + 1) * R * n, n, R, m, s->hbuf, s->st);
-        givens_kernel<<<1, 64, 0, st>>>(s->H, s->cs, s->sn, s->g, s->bnorm, s->relres, m, R, j, s->tol, s->max_iters,
-                                        s->st);
-        count_launches(9);   // the ten kernels above (IE_CK_LAUNCH adds the last)
-        IE_CK_LAUNCH();
+    IE_TRY(apply(p, IE_FULL, s->prec, s->Vcur, s->W, R, st, s->st));
+    for (int pass = 0; pass < 2; ++pass) {
+        dots_kernel<<<dg, kDotThreads, 0, st>>>(s->V, s->W, n, R, jarg, s->partial, s->nblk, m, s->st, 0, 0);
+        reduce_dots_kernel<<<R, 64, 0, st>>>(s->partial, s->nblk, m, R, jarg, s->hbuf, s->H, s->st);
+        update_kernel<<<vg, 256, 0, st>>>(s->V, s->W, n, R, jarg, m, s->hbuf, s->st);
     }
-    // solution update and restart residual
+    dots_kernel<<<dg, kDotThreads, 0, st>>>(s->V, s->W, n, R, jarg, s->partial, s->nblk, m, s->st, 0, 1);
+    norm_finish_kernel<<<R, 32, 0, st>>>(s->partial, s->nblk, m, R, jarg, s->hbuf, s->H, s->st);
+    scale_kernel<<<vg, 256, 0, st>>>(s->W, s->V, s->Vcur, n, R, m, s->hbuf, s->st, jarg);
+    givens_kernel<<<1, 64, 0, st>>>(s->H, s->cs, s->sn, s->g, s->bnorm, s->relres, m, R, jarg, s->tol, s->max_iters,
+                                    s->st, s->hcond);
+    count_launches(9);   // the ten kernels above (IE_CK_LAUNCH adds the last)
+    IE_CK_LAUNCH();
+    return IE_OK;
+}
+
+// Solution update x += V y and the restart: true residual, its norm, next cycle.
+ie_status enqueue_end(ie_solver s, cudaStream_t st) {
+    ie_plan p = s->plan;
+    int R = s->R, m = s->m;
+    int64_t n = s->n;
+    dim3 vg(vec_grid(n), R), dg(s->nblk, R);
     lsq_kernel<<<1, 64, 0, st>>>(s->H, s->g, s->hbuf, m, R, s->st);
     xupdate_kernel<<<vg, 256, 0, st>>>(s->V, s->x, n, R, m, s->hbuf, s->st);
+    count_launches(2);
     IE_TRY(apply(p, IE_FULL, s->prec, s->x, s->W, R, st, s->st + 1));
     residual_kernel<<<vg, 256, 0, st>>>(s->v, s->W, s->V, n, R, 0, s->st);
-    dots_kernel<<<dg, kDotThreads, 0, st>>>(s->V, s->V, n, R, -1, s->partial, s->nblk, m, s->st, 1);
+    dots_kernel<<<dg, kDotThreads, 0, st>>>(s->V, s->V, n, R, 0, s->partial, s->nblk, m, s->st, 1, 1);
     begin_cycle_kernel<<<1, 256, 0, st>>>(s->partial, s->nblk, m, R, s->tol, s->max_iters, s->bnorm, s->relres, s->g,
                                           s->H, s->hbuf, 0, s->st);
-    scale_v0_kernel<<<vg, 256, 0, st>>>(s->V, n, R, m, s->hbuf, s->st);
-    count_launches(5);       // lsq, xupdate, residual, dots, begin_cycle (+ scale below)
+    scale_v0_kernel<<<vg, 256, 0, st>>>(s->V, s->Vcur, n, R, m, s->hbuf, s->st);
+    count_launches(3);   // residual, dots, begin_cycle (+ scale below)
     IE_CK_LAUNCH();
+    return IE_OK;
+}
+
+int64_t count_kernel_nodes(cudaGraph_t graph) {
+    size_t nn = 0;
+    if (cudaGraphGetNodes(graph, nullptr, &nn) != cudaSuccess) return 0;
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn && cudaGraphGetNodes(graph, nodes.data(), &nn) != cudaSuccess) return 0;
+    int64_t k = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) k++;
+    }
+    return k;
+}
+
+// One restart cycle as a graph: a WHILE node whose body is one Arnoldi iteration
+// (the Givens kernel sets the condition from the per-RHS flags), then the end of
+// the cycle.  Skipped iterations cost nothing and the cycle needs no host sync.
+ie_status build_while_graph(ie_solver s, cudaGraph_t *out) {
+    cudaGraph_t g = nullptr;
+    IE_CK(cudaGraphCreate(&g, 0));
+    auto fail = [&](cudaError_t e, const char *what) {
+        cudaGetLastError();
+        cudaGraphDestroy(g);
+        set_error("%s: %s", what, cudaGetErrorString(e));
+        return IE_ERR_CUDA;
+    };
+    cudaError_t e = cudaGraphConditionalHandleCreate(&s->hcond, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return fail(e, "cudaGraphConditionalHandleCreate");
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = s->hcond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    e = cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) return fail(e, "cudaGraphAddNode(while)");
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(s->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail(e, "capture body");
+    capture_begin();
+    ie_status st1 = enqueue_iteration(s, s->cap, kDevJ);
+    capture_end();
+    cudaGraph_t tmp = nullptr;
+    e = cudaStreamEndCapture(s->cap, &tmp);
+    if (st1 != IE_OK) {
+        cudaGraphDestroy(g);
+        return st1;
+    }
+    if (e != cudaSuccess) return fail(e, "end capture body");
+    s->body_kernels = count_kernel_nodes(body);
+    e = cudaStreamBeginCaptureToGraph(s->cap, g, &wnode, nullptr, 1, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail(e, "capture end");
+    capture_begin();
+    ie_status st2 = enqueue_end(s, s->cap);
+    capture_end();
+    e = cudaStreamEndCapture(s->cap, &tmp);
+    if (st2 != IE_OK) {
+        cudaGraphDestroy(g);
+        return st2;
+    }
+    if (e != cudaSuccess) return fail(e, "end capture end");
+    s->end_kernels = count_kernel_nodes(g);
+    *out = g;
+    return IE_OK;
+}
+
+// Fallback: the m iterations unrolled with explicit indices (every kernel gated).
+ie_status build_unrolled_graph(ie_solver s, cudaGraph_t *out) {
+    s->hcond = 0;
+    IE_CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+    capture_begin();
+    ie_status e = IE_OK;
+    for (int j = 0; j < s->m && e == IE_OK; ++j) e = enqueue_iteration(s, s->cap, j);
+    if (e == IE_OK) e = enqueue_end(s, s->cap);
+    capture_end();
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(s->cap, &graph);
+    if (e != IE_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return e;
+    }
+    IE_CK(ce);
+    s->body_kernels = 0;
+    s->end_kernels = count_kernel_nodes(graph);
+    *out = graph;
     return IE_OK;
 }
 
 ie_status read_info(ie_solver s, ie_solve_info *info, int *done) {
     int R = s->R;
-    std::vector<int> st(2 + 4 * R);
+    std::vector<int> st(4 + 4 * R);
     std::vector<double> rel(R);
     IE_CK(cudaMemcpy(st.data(), s->st, st.size() * sizeof(int), cudaMemcpyDeviceToHost));
     IE_CK(cudaMemcpy(rel.data(), s->relres, R * sizeof(double), cudaMemcpyDeviceToHost));
@@ -530,7 +656,13 @@ ie_status read_info(ie_solver s, ie_solve_info *info, int *done) {
         info->iterations = it;
         info->relres = rr;
         info->converged = conv ? 1 : 0;
-        info->matvecs = s->cycles_run * s->matvecs_per_cycle;
+        // products: one per WHILE-body run (or m per unrolled cycle) plus one restart per cycle
+        int64_t body = st[3 + 4 * R];
+        info->matvecs = (int)(s->use_while ? body + s->cycles_run : (int64_t)s->cycles_run * s->matvecs_per_cycle);
+        if (s->use_while && body > s->body_runs_seen) {
+            count_launches((body - s->body_runs_seen) * s->body_kernels);
+            s->body_runs_seen = body;
+        }
     }
     return IE_OK;
 }
@@ -592,9 +724,10 @@ ie_status ie_solver_create(ie_plan p, int nrhs, const ie_solve_opts *opts, ie_so
     SA(s->partial, (size_t)R * (m + 1) * s->nblk);
     SA(s->bnorm, R);
     SA(s->relres, R);
-    SA(s->st, 2 + 4 * R);
+    SA(s->st, 4 + 4 * R);
+    SA(s->Vcur, (size_t)R * s->n);
 #undef SA
-    if (cudaMemset(s->st, 0, (2 + 4 * R) * sizeof(int)) != cudaSuccess) return fail(IE_ERR_CUDA);
+    if (cudaMemset(s->st, 0, (4 + 4 * R) * sizeof(int)) != cudaSuccess) return fail(IE_ERR_CUDA);
     // work lists must exist before graph capture (they allocate)
     WorkList *wl = nullptr;
     e = work_list(p, o.prec != IE_PREC_FP32, R, &wl);
@@ -628,14 +761,15 @@ ie_status ie_solver_start(ie_solver s, const void *v, void *c, void *stream) {
     s->cycles_run = 0;
     int R = s->R, m = s->m;
     int64_t n = s->n;
-    IE_CK(cudaMemsetAsync(s->st, 0, (2 + 4 * R) * sizeof(int), st));
+    IE_CK(cudaMemsetAsync(s->st, 0, (4 + 4 * R) * sizeof(int), st));
+    s->body_runs_seen = 0;
     IE_CK(cudaMemsetAsync(s->x, 0, (size_t)R * n * sizeof(float2), st));
     dim3 vg(vec_grid(n), R), dg(s->nblk, R);
     residual_kernel<<<vg, 256, 0, st>>>(s->v, nullptr, s->V, n, R, 1, s->st);
-    dots_kernel<<<dg, kDotThreads, 0, st>>>(s->V, s->V, n, R, -1, s->partial, s->nblk, m, s->st, 1);
+    dots_kernel<<<dg, kDotThreads, 0, st>>>(s->V, s->V, n, R, 0, s->partial, s->nblk, m, s->st, 1, 1);
     begin_cycle_kernel<<<1, 256, 0, st>>>(s->partial, s->nblk, m, R, s->tol, s->max_iters, s->bnorm, s->relres, s->g,
                                           s->H, s->hbuf, 1, s->st);
-    scale_v0_kernel<<<vg, 256, 0, st>>>(s->V, n, R, m, s->hbuf, s->st);
+    scale_v0_kernel<<<vg, 256, 0, st>>>(s->V, s->Vcur, n, R, m, s->hbuf, s->st);
     count_launches(3);
     IE_CK_LAUNCH();
     // the captured cycle reads v and x through fixed pointers: recapture if they moved
@@ -651,37 +785,20 @@ ie_status ie_solver_advance(ie_solver s, int cycles, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     for (int c = 0; c < cycles; ++c) {
         if (!s->exec) {
-            // capture one cycle on the private stream, ordered after `st`
+            // build the cycle graph on the private stream, ordered after `st`
             IE_CK(cudaEventRecord(s->ev, st));
             IE_CK(cudaStreamWaitEvent(s->cap, s->ev, 0));
-            IE_CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
-            capture_begin();
-            ie_status e = enqueue_cycle(s, s->cap);
-            capture_end();
             cudaGraph_t graph = nullptr;
-            cudaError_t ce = cudaStreamEndCapture(s->cap, &graph);
-            if (e != IE_OK) {
-                if (graph) cudaGraphDestroy(graph);
-                return e;
-            }
-            IE_CK(ce);
-            size_t nn = 0;
-            IE_CK(cudaGraphGetNodes(graph, nullptr, &nn));
-            std::vector<cudaGraphNode_t> nodes(nn);
-            if (nn) IE_CK(cudaGraphGetNodes(graph, nodes.data(), &nn));
-            s->graph_kernels = 0;
-            for (auto nd : nodes) {
-                cudaGraphNodeType t;
-                IE_CK(cudaGraphNodeGetType(nd, &t));
-                if (t == cudaGraphNodeTypeKernel) s->graph_kernels++;
-            }
-            IE_CK(cudaGraphInstantiate(&s->exec, graph, 0));
+            s->use_while = build_while_graph(s, &graph) == IE_OK;
+            if (!s->use_while) IE_TRY(build_unrolled_graph(s, &graph));
+            cudaError_t ie_ = cudaGraphInstantiate(&s->exec, graph, 0);
             cudaGraphDestroy(graph);
+            IE_CK(ie_);
             s->cap_v = s->v;
             s->cap_x = s->x;
         }
         IE_CK(cudaGraphLaunch(s->exec, st));
-        count_launches(s->graph_kernels);
+        count_launches(s->end_kernels);
         s->cycles_run++;
     }
     IE_CK(cudaEventRecord(s->ev, st));
