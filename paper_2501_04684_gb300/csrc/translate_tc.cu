@@ -11,17 +11,24 @@
 //
 // Work item = (displacement, M-block of 128 real rows, run of <= 128 complex columns).
 // Persistent CTAs walk the size-sorted item list round-robin.  Warp roles:
-//   warps 0-3  producers: per K-chunk of 64, one elected thread bulk-copies the two
-//              pre-swizzled 16 KB A images (TMA engine, mbarrier complete_tx); all 128
-//              threads gather the B rows of the item's columns with 16-byte cp.async
-//              into the SW128 K-major layout (chunk c of row n at c ^ (n mod 8)).
-//   warp 4     MMA issuer: one thread issues tcgen05.mma (M=128, N<=256, K=16) from the
-//              two-stage ring into one of two TMEM accumulators (2 x 256 columns).
-//   warps 5-8  epilogue: tcgen05.ld of their TMEM lane quarter, complex recombination,
-//              power-of-two rescaling (fp16), red.global.add into the slab (d mod 8).
-// Every mbarrier wait is bounded; a wait that gives up sets the device error word,
-// the CTA drains its own copies, frees its TMEM and returns.
+//   warp 0     producer: per K-chunk of 32, lane 0 bulk-copies the pre-swizzled 8 KB
+//              A images (TMA engine); all lanes gather the item's B rows with TMA
+//              tile::gather4 (4 rows per instruction, 64-byte swizzle) from a 2-D tensor
+//              map over the split source vectors.  Both complete on the stage's
+//              mbarrier by transaction bytes, so the producer never waits for data.
+//   warp 1     MMA issuer (one thread): tcgen05.mma M=128, N<=256, K=16 from a 4-stage
+//              ring into one of two TMEM accumulators (2 x 256 columns).
+//   warps 2-5  epilogue: target offsets of the item's columns staged in shared memory
+//              before the accumulator is ready; tcgen05.ld of the warp's TMEM lane
+//              quarter, complex recombination, fp16 rescaling, red.global.add into the
+//              slab (d mod 8).
+// Every wait is bounded and each role decides on a timeout uniformly (lane-0 wait +
+// shuffle, or a named barrier + abort flag), so no lane is ever left at a barrier; a
+// timeout sets the device error word, drains the CTA's bulk copies, frees TMEM, returns.
+#include <cuda.h>
+
 #include <algorithm>
+#include <mutex>
 
 #include "ie_internal.h"
 
@@ -29,14 +36,13 @@ namespace ie {
 namespace {
 
 constexpr int kTcTileCols = 128;                 // complex columns per work item (N <= 256)
-constexpr int kStages = 2;
-constexpr int kProducerThreads = 128;
-constexpr int kEpilogueThreads = 128;
-constexpr int kThreadsTc = kProducerThreads + 32 + kEpilogueThreads;   // 288
-constexpr int kImgBytes = 128 * 64 * 2;          // 16 KB
-constexpr int kBBytes = 256 * 128;               // 32 KB (256 rows x 64 x 16 bit)
-constexpr int kStageBytes = 2 * kImgBytes + 2 * kBBytes;
-constexpr int kSmemBytes = kStages * kStageBytes + 1024 /*barriers*/ + 1024 /*alignment*/;
+constexpr int kStages = 4;
+constexpr int kThreadsTc = 32 + 32 + 128;        // producer, MMA, epilogue
+constexpr int kImgBytes = 128 * kTcK * 2;        // 8 KB A image
+constexpr int kBBytes = 256 * kTcK * 2;          // 16 KB B plane (256 rows x 64 B)
+constexpr int kStageBytes = 2 * kImgBytes + 2 * kBBytes;     // 48 KB
+constexpr int kEpiBytes = 2 * kTcTileCols * (8 + 4);          // column offsets + scales, 2 buffers
+constexpr int kSmemBytes = kStages * kStageBytes + kEpiBytes + 256 /*barriers*/ + 1024 /*alignment*/;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kSpinLimit = 1u << 24;
 
@@ -60,7 +66,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false when the limit is hit or another thread already gave up.
+// Bounded wait by one thread: false when the limit is hit or the CTA already gave up.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
     for (uint32_t i = 0; i < kSpinLimit; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
@@ -70,29 +76,40 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     *abort_flag = 1;
     return false;
 }
+// Whole warp: lane 0 waits, the outcome is broadcast.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    int ok = 0;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag) ? 1 : 0;
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+__device__ __forceinline__ void named_sync_epilogue() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
-__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+// Four rows (y0..y3) of `map`, 32 elements from column x, into 4 x 64 B of shared memory.
+__device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap *map, int x, int y0, int y1, int y2,
+                                            int y3, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+        "l"(map), "r"(x), "r"(y0), "r"(y1), "r"(y2), "r"(y3), "r"(bar)
+        : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFF) >> 4);     // start address
     d |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset
+    d |= (uint64_t)(512 >> 4) << 32;             // stride byte offset
     d |= (uint64_t)1 << 46;                      // descriptor version
-    d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+    d |= (uint64_t)4 << 61;                      // 64-byte swizzle
     return d;
 }
 
@@ -134,11 +151,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
 struct TcArgs {
     const WorkItem *items;
     int64_t n_items;
-    const uint16_t *C;          // [disp][18 images]
+    const uint16_t *C;          // [disp][36 images]
     const int32_t *Cexp;        // [disp] or null
-    const uint16_t *Xtc;        // [hl][col][reim][192]
     const int32_t *Xexp;        // [col]
-    int64_t plane;              // elements per hl plane of Xtc
+    int plane_rows;             // tensor-map rows per hi/lo plane
     const int32_t *src, *dst;
     float *Yslab;               // float view of the complex64 slabs
     size_t slab_stride;         // complex elements between slabs
@@ -148,32 +164,34 @@ struct TcArgs {
 };
 
 template <bool FP16, bool X3>
-__global__ void __launch_bounds__(kThreadsTc, 1) translate_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(kThreadsTc, 1)
+translate_tc_kernel(const __grid_constant__ CUtensorMap xmap, const TcArgs a) {
     if (a.gate && *a.gate == 0) return;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *bars = smem + kStages * kStageBytes;
-    uint64_t *full = reinterpret_cast<uint64_t *>(bars);          // [kStages]
-    uint64_t *empty = full + kStages;                              // [kStages]
-    uint64_t *accfull = empty + kStages;                           // [2]
-    uint64_t *accempty = accfull + 2;                              // [2]
+    int64_t *ep_off = reinterpret_cast<int64_t *>(smem + kStages * kStageBytes);      // [2][128]
+    float *ep_scale = reinterpret_cast<float *>(ep_off + 2 * kTcTileCols);              // [2][128]
+    uint64_t *full = reinterpret_cast<uint64_t *>(ep_scale + 2 * kTcTileCols);          // [kStages]
+    uint64_t *empty = full + kStages;                                                    // [kStages]
+    uint64_t *accfull = empty + kStages;                                                 // [2]
+    uint64_t *accempty = accfull + 2;                                                    // [2]
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accempty + 2);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(smem_u32(&full[s]), kProducerThreads + 1);
+            mbar_init(smem_u32(&full[s]), 1);
             mbar_init(smem_u32(&empty[s]), 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&accfull[b]), 1);
-            mbar_init(smem_u32(&accempty[b]), kEpilogueThreads);
+            mbar_init(smem_u32(&accempty[b]), 128);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 4) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -184,9 +202,8 @@ __global__ void __launch_bounds__(kThreadsTc, 1) translate_tc_kernel(TcArgs a) {
     const uint32_t tmem_base = *tmem_slot;
 
     const int64_t first = blockIdx.x, step = gridDim.x;
-    if (warp < 4) {
-        // ---------------- producers
-        const int tid = threadIdx.x;
+    if (warp == 0) {
+        // ---------------- producer warp
         int64_t il = 0;
         int64_t armed[kStages];
         for (int s = 0; s < kStages; ++s) armed[s] = -1;
@@ -194,122 +211,143 @@ __global__ void __launch_bounds__(kThreadsTc, 1) translate_tc_kernel(TcArgs a) {
         for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
             const WorkItem it = a.items[i];
             const int ncols = it.npairs * a.nrhs;
-            const int nreal = 2 * ncols;
+            const int nmma = (2 * ncols + 15) & ~15;
+            const int ngroups = nmma >> 2;                 // gather4 groups of 4 B rows
+            int rows[2][4];
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int gq = lane + 32 * t;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int n = 4 * gq + q, j = n >> 1, part = n & 1;
+                    int row = part;                        // padding rows read row 0/1 (discarded)
+                    if (gq < ngroups && j < ncols) {
+                        const int p = it.pair0 + j / a.nrhs, r = j % a.nrhs;
+                        row = 2 * (r * a.nbox + a.src[p]) + part;
+                    }
+                    rows[t][q] = row;
+                }
+            }
             const uint16_t *Cd = a.C + (int64_t)it.disp * kTcDispElems;
-            for (int kc = 0; kc < 3 && ok; ++kc) {
-                const int64_t g = il * 3 + kc;
+            const uint32_t bytes = (X3 ? 2u : 1u) * (uint32_t)(kImgBytes + nmma * kTcK * 2);
+            for (int kc = 0; kc < kTcKChunks; ++kc) {
+                const int64_t g = il * kTcKChunks + kc;
                 const int s = (int)(g % kStages);
                 const uint32_t ph = (uint32_t)((g / kStages) & 1);
-                if (!mbar_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag)) {
+                if (!warp_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag)) {
                     ok = false;
                     break;
                 }
                 unsigned char *st = smem + s * kStageBytes;
                 const uint32_t sA = smem_u32(st), sB = smem_u32(st + 2 * kImgBytes);
-                if (tid == 0) {
-                    const uint32_t fb = smem_u32(&full[s]);
-                    mbar_arrive_expect_tx(fb, X3 ? 2 * kImgBytes : kImgBytes);
+                const uint32_t fb = smem_u32(&full[s]);
+                if (lane == 0) {
+                    mbar_arrive_expect_tx(fb, bytes);
                     armed[s] = g;
-                    const uint16_t *img = Cd + (int64_t)((it.mb * 3 + kc) * 2) * kTcImageElems;
-                    bulk_copy_g2s(sA, img, kImgBytes, fb);
-                    if (X3) bulk_copy_g2s(sA + kImgBytes, img + kTcImageElems, kImgBytes, fb);
+                    const uint16_t *img = Cd + (int64_t)((it.mb * kTcKChunks + kc) * 2) * kTcImageElems;
+                    bulk_g2s(sA, img, kImgBytes, fb);
+                    if (X3) bulk_g2s(sA + kImgBytes, img + kTcImageElems, kImgBytes, fb);
                 }
-                for (int n = tid; n < nreal; n += kProducerThreads) {
-                    const int j = n >> 1, part = n & 1;
-                    const int p = it.pair0 + j / a.nrhs, r = j % a.nrhs;
-                    const int64_t row = 2 * ((int64_t)r * a.nbox + a.src[p]) + part;
-                    const uint16_t *gsrc = a.Xtc + row * kNU + kc * 64;
-                    const uint32_t rbase = (uint32_t)((n >> 3) * 1024 + (n & 7) * 128);
+                __syncwarp();
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const uint32_t off = rbase + (uint32_t)((c ^ (n & 7)) * 16);
-                        cp_async16(sB + off, gsrc + c * 8);
-                        if (X3) cp_async16(sB + kBBytes + off, gsrc + a.plane + c * 8);
+                for (int t = 0; t < 2; ++t) {
+                    const int gq = lane + 32 * t;
+                    if (gq < ngroups) {
+                        const uint32_t off = (uint32_t)gq * 4 * (kTcK * 2);
+                        tma_gather4(sB + off, &xmap, kc * kTcK, rows[t][0], rows[t][1], rows[t][2], rows[t][3], fb);
+                        if (X3)
+                            tma_gather4(sB + kBBytes + off, &xmap, kc * kTcK, rows[t][0] + a.plane_rows,
+                                        rows[t][1] + a.plane_rows, rows[t][2] + a.plane_rows,
+                                        rows[t][3] + a.plane_rows, fb);
                     }
                 }
-                cp_async_wait_all();
-                fence_proxy_async();
-                mbar_arrive(smem_u32(&full[s]));
+                __syncwarp();
             }
         }
-        cp_async_wait_all();
         if (!ok) {
-            atomicExch(a.err, 1);
-            // drain: every stage this CTA armed completes once its bulk bytes land
-            if (tid == 0) {
+            if (lane == 0) {
+                atomicExch(a.err, 1);
+                // drain: every stage this CTA armed completes once its bytes land
                 for (int s = 0; s < kStages; ++s) {
                     if (armed[s] < 0) continue;
                     const uint32_t ph = (uint32_t)((armed[s] / kStages) & 1);
                     for (uint32_t w = 0; w < kSpinLimit && !mbar_try_wait(smem_u32(&full[s]), ph); ++w) __nanosleep(64);
                 }
             }
+            __syncwarp();
         }
-    } else if (warp == 4) {
-        // ---------------- MMA issuer
-        int64_t il = 0;
-        bool ok = true;
-        for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
-            const WorkItem it = a.items[i];
-            const int ncols = it.npairs * a.nrhs;
-            const int nmma = (2 * ncols + 15) & ~15;
-            const uint32_t idesc = f16_idesc(nmma, FP16);
-            const int buf = (int)(il & 1);
-            const uint32_t aph = (uint32_t)((il >> 1) & 1);
-            if (!mbar_wait(smem_u32(&accempty[buf]), aph ^ 1, abort_flag)) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
-            const uint32_t dt = tmem_base + (uint32_t)(buf * 256);
-            for (int kc = 0; kc < 3 && ok; ++kc) {
-                const int64_t g = il * 3 + kc;
-                const int s = (int)(g % kStages);
-                const uint32_t ph = (uint32_t)((g / kStages) & 1);
-                if (!mbar_wait(smem_u32(&full[s]), ph, abort_flag)) {
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (lane 0)
+        if (lane == 0) {
+            int64_t il = 0;
+            bool ok = true;
+            for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
+                const WorkItem it = a.items[i];
+                const int ncols = it.npairs * a.nrhs;
+                const int nmma = (2 * ncols + 15) & ~15;
+                const uint32_t idesc = f16_idesc(nmma, FP16);
+                const int buf = (int)(il & 1);
+                const uint32_t aph = (uint32_t)((il >> 1) & 1);
+                if (!mbar_wait(smem_u32(&accempty[buf]), aph ^ 1, abort_flag)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                if (lane == 0) {
+                const uint32_t dt = tmem_base + (uint32_t)(buf * 256);
+                for (int kc = 0; kc < kTcKChunks; ++kc) {
+                    const int64_t g = il * kTcKChunks + kc;
+                    const int s = (int)(g % kStages);
+                    const uint32_t ph = (uint32_t)((g / kStages) & 1);
+                    if (!mbar_wait(smem_u32(&full[s]), ph, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
                     unsigned char *st = smem + s * kStageBytes;
                     const uint32_t sA = smem_u32(st), sB = smem_u32(st + 2 * kImgBytes);
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const uint64_t ah = sw128_desc(sA + k * 32), bh = sw128_desc(sB + k * 32);
+                    for (int k = 0; k < kTcK / 16; ++k) {
+                        const uint64_t ah = sw64_desc(sA + k * 32), bh = sw64_desc(sB + k * 32);
                         umma(dt, ah, bh, idesc, (kc | k) ? 1u : 0u);
                         if (X3) {
-                            const uint64_t al = sw128_desc(sA + kImgBytes + k * 32);
-                            const uint64_t bl = sw128_desc(sB + kBBytes + k * 32);
+                            const uint64_t al = sw64_desc(sA + kImgBytes + k * 32);
+                            const uint64_t bl = sw64_desc(sB + kBBytes + k * 32);
                             umma(dt, ah, bl, idesc, 1u);
                             umma(dt, al, bh, idesc, 1u);
                         }
                     }
                     umma_commit(smem_u32(&empty[s]));
-                    if (kc == 2) umma_commit(smem_u32(&accfull[buf]));
+                    if (kc == kTcKChunks - 1) umma_commit(smem_u32(&accfull[buf]));
                 }
-                __syncwarp();
             }
+            if (!ok) atomicExch(a.err, 1);
         }
-        if (!ok) atomicExch(a.err, 1);
     } else {
-        // ---------------- epilogue
-        const int q = warp & 3;                        // TMEM lane quarter
+        // ---------------- epilogue warps 2-5 (TMEM lane quarter = warp mod 4)
+        const int q = warp & 3;
+        const int te = threadIdx.x - 64;
         const int64_t slab_f = (int64_t)a.slab_stride * 2;
         int64_t il = 0;
-        bool ok = true;
-        for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
+        for (int64_t i = first; i < a.n_items; i += step, ++il) {
             const WorkItem it = a.items[i];
             const int ncols = it.npairs * a.nrhs;
             const int buf = (int)(il & 1);
             const uint32_t aph = (uint32_t)((il >> 1) & 1);
-            if (!mbar_wait(smem_u32(&accfull[buf]), aph, abort_flag)) {
-                ok = false;
-                break;
-            }
-            tc_fence_after();
             const int ed = FP16 ? a.Cexp[it.disp] : 0;
-            const int m0 = 64 * it.mb + 16 * q;        // first complex row of this warp
-            float *Ys = a.Yslab + (int64_t)(it.disp % kSlabs) * slab_f;
+            for (int j = te; j < ncols; j += 128) {
+                const int p = it.pair0 + j / a.nrhs, r = j % a.nrhs;
+                ep_off[buf * kTcTileCols + j] = ((int64_t)r * a.nbox + a.dst[p]) * (2 * kNU);
+                if (FP16) ep_scale[buf * kTcTileCols + j] = ldexpf(1.f, ed + a.Xexp[(int64_t)r * a.nbox + a.src[p]]);
+            }
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(smem_u32(&accfull[buf]), aph, abort_flag);
+            named_sync_epilogue();               // publishes ep_off and makes the abort decision uniform
+            if (*abort_flag) break;
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) break;
+            tc_fence_after();
+            const int m0 = 64 * it.mb + 16 * q;    // first complex row of this warp
+            float *Ys = a.Yslab + (int64_t)(it.disp % kSlabs) * slab_f + 2 * m0 + lane;
             const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256);
             for (int c0 = 0; c0 < 2 * ncols; c0 += 16) {
                 float v[16];
@@ -320,20 +358,17 @@ __global__ void __launch_bounds__(kThreadsTc, 1) translate_tc_kernel(TcArgs a) {
                     if (j >= ncols) break;             // warp-uniform
                     const float ob = __shfl_xor_sync(0xffffffffu, v[2 * jj + 1], 1);
                     float val = (lane & 1) ? v[2 * jj] + ob : v[2 * jj] - ob;
-                    const int p = it.pair0 + j / a.nrhs, r = j % a.nrhs;
-                    const int64_t col = (int64_t)r * a.nbox + a.dst[p];
-                    if (FP16) val = ldexpf(val, ed + a.Xexp[(int64_t)r * a.nbox + a.src[p]]);
-                    atomicAdd(Ys + col * (2 * kNU) + 2 * m0 + lane, val);
+                    if (FP16) val *= ep_scale[buf * kTcTileCols + j];
+                    atomicAdd(Ys + ep_off[buf * kTcTileCols + j], val);
                 }
             }
             tc_fence_before();
             mbar_arrive(smem_u32(&accempty[buf]));
         }
-        if (!ok) atomicExch(a.err, 1);
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 4) {
+    if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols));
     }
@@ -342,6 +377,25 @@ __global__ void __launch_bounds__(kThreadsTc, 1) translate_tc_kernel(TcArgs a) {
 template <bool FP16, bool X3>
 ie_status set_attr() {
     IE_CK(cudaFuncSetAttribute(translate_tc_kernel<FP16, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    return IE_OK;
+}
+
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+std::mutex g_enc_mu;
+EncodeTiled g_encode = nullptr;
+
+ie_status tensor_map_encoder(EncodeTiled *out) {
+    std::lock_guard<std::mutex> lk(g_enc_mu);
+    if (!g_encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        IE_CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !fn) return set_error("cuTensorMapEncodeTiled unavailable"), IE_ERR_CUDA;
+        g_encode = reinterpret_cast<EncodeTiled>(fn);
+    }
+    *out = g_encode;
     return IE_OK;
 }
 
@@ -363,14 +417,26 @@ ie_status launch_translate_tc(ie_plan p, int prec, float2 *Yslab, int nrhs, cuda
     WorkList *wl = nullptr;
     IE_TRY(work_list(p, true, nrhs, &wl));
     if (wl->n == 0) return IE_OK;
+    // 2-D view of the split source vectors: rows (hl, rhs, box, reim) of 192 16-bit values
+    EncodeTiled enc = nullptr;
+    IE_TRY(tensor_map_encoder(&enc));
+    const int plane_rows = nrhs * p->nbox * 2;
+    CUtensorMap map;
+    cuuint64_t dims[2] = {(cuuint64_t)kNU, (cuuint64_t)(2 * plane_rows)};
+    cuuint64_t strides[1] = {(cuuint64_t)kNU * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kTcK, 1};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, p->d_Xtc, dims, strides, box, estr,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return set_error("cuTensorMapEncodeTiled failed (%d)", (int)cr), IE_ERR_CUDA;
     TcArgs a;
     a.items = wl->d_items;
     a.n_items = wl->n;
     a.C = C;
     a.Cexp = fp16 ? p->d_Cexp16 : nullptr;
-    a.Xtc = p->d_Xtc;
     a.Xexp = p->d_Xexp;
-    a.plane = (int64_t)nrhs * p->nbox * 2 * kNU;
+    a.plane_rows = plane_rows;
     a.src = p->d_src;
     a.dst = p->d_dst;
     a.Yslab = reinterpret_cast<float *>(Yslab);
@@ -381,11 +447,11 @@ ie_status launch_translate_tc(ie_plan p, int prec, float2 *Yslab, int nrhs, cuda
     a.gate = gate;
     int grid = (int)std::min<int64_t>(wl->n, p->tc_sms > 0 ? p->tc_sms : 148);
     if (prec == IE_PREC_BF16X3)
-        translate_tc_kernel<false, true><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
+        translate_tc_kernel<false, true><<<grid, kThreadsTc, kSmemBytes, st>>>(map, a);
     else if (prec == IE_PREC_FP16X3)
-        translate_tc_kernel<true, true><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
+        translate_tc_kernel<true, true><<<grid, kThreadsTc, kSmemBytes, st>>>(map, a);
     else if (prec == IE_PREC_BF16X1)
-        translate_tc_kernel<false, false><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
+        translate_tc_kernel<false, false><<<grid, kThreadsTc, kSmemBytes, st>>>(map, a);
     else
         return set_error("not a tensor-core precision: %d", prec), IE_ERR_INVALID;
     IE_CK_LAUNCH();
