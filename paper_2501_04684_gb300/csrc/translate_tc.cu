@@ -11,24 +11,23 @@
 //
 // Work item = (displacement, M-block of 128 real rows, run of <= 128 complex columns).
 // Persistent CTAs walk the size-sorted item list round-robin.  Warp roles:
-//   warp 0     producer: per K-chunk of 32, lane 0 bulk-copies the pre-swizzled 8 KB
-//              A images (TMA engine); all lanes gather the item's B rows with TMA
-//              tile::gather4 (4 rows per instruction, 64-byte swizzle) from a 2-D tensor
-//              map over the split source vectors.  Both complete on the stage's
-//              mbarrier by transaction bytes, so the producer never waits for data.
-//   warp 1     MMA issuer (one thread): tcgen05.mma M=128, N<=256, K=16 from a 4-stage
-//              ring into one of two TMEM accumulators (2 x 256 columns).
-//   warps 2-5  epilogue: target offsets of the item's columns staged in shared memory
+//   warps 0-3  producers: per K-chunk of 64, one thread bulk-copies the two
+//              pre-swizzled 16 KB A images (TMA engine, complete_tx on the stage
+//              mbarrier); the 128 threads gather the item's B rows with 16-byte cp.async
+//              into the SW128 K-major layout (chunk c of row n at c ^ (n mod 8)), row
+//              addresses computed once per item, and signal the same mbarrier with
+//              cp.async.mbarrier.arrive.noinc — nobody waits for its own copies.
+//   warp 4     MMA issuer (one thread): after the stage completes, a proxy fence makes
+//              the gathered rows visible to the tensor core; tcgen05.mma M=128, N<=256,
+//              K=16 from a 2-stage ring into one of two TMEM accumulators (2 x 256 cols).
+//   warps 5-8  epilogue: target offsets of the item's columns staged in shared memory
 //              before the accumulator is ready; tcgen05.ld of the warp's TMEM lane
 //              quarter, complex recombination, fp16 rescaling, red.global.add into the
 //              slab (d mod 8).
 // Every wait is bounded and each role decides on a timeout uniformly (lane-0 wait +
 // shuffle, or a named barrier + abort flag), so no lane is ever left at a barrier; a
-// timeout sets the device error word, drains the CTA's bulk copies, frees TMEM, returns.
-#include <cuda.h>
-
+// timeout sets the device error word, drains the CTA's copies, frees TMEM, returns.
 #include <algorithm>
-#include <mutex>
 
 #include "ie_internal.h"
 
@@ -36,11 +35,13 @@ namespace ie {
 namespace {
 
 constexpr int kTcTileCols = 128;                 // complex columns per work item (N <= 256)
-constexpr int kStages = 4;
-constexpr int kThreadsTc = 32 + 32 + 128;        // producer, MMA, epilogue
-constexpr int kImgBytes = 128 * kTcK * 2;        // 8 KB A image
-constexpr int kBBytes = 256 * kTcK * 2;          // 16 KB B plane (256 rows x 64 B)
-constexpr int kStageBytes = 2 * kImgBytes + 2 * kBBytes;     // 48 KB
+constexpr int kStages = 2;
+constexpr int kProducers = 128;
+constexpr int kThreadsTc = kProducers + 32 + 128;             // producers, MMA, epilogue
+constexpr int kEpiFirst = kProducers + 32;                    // first epilogue thread
+constexpr int kImgBytes = 128 * kTcK * 2;        // 16 KB A image
+constexpr int kBBytes = 256 * kTcK * 2;          // 32 KB B plane (256 rows x 128 B)
+constexpr int kStageBytes = 2 * kImgBytes + 2 * kBBytes;     // 96 KB
 constexpr int kEpiBytes = 2 * kTcTileCols * (8 + 4);          // column offsets + scales, 2 buffers
 constexpr int kSmemBytes = kStages * kStageBytes + kEpiBytes + 256 /*barriers*/ + 1024 /*alignment*/;
 constexpr uint32_t kTmemCols = 512;
@@ -89,27 +90,27 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
                  "l"(src), "r"(bytes), "r"(bar)
                  : "memory");
 }
-// Four rows (y0..y3) of `map`, 32 elements from column x, into 4 x 64 B of shared memory.
-__device__ __forceinline__ void tma_gather4(uint32_t dst, const CUtensorMap *map, int x, int y0, int y1, int y2,
-                                            int y3, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
-        "l"(map), "r"(x), "r"(y0), "r"(y1), "r"(y2), "r"(y3), "r"(bar)
-        : "memory");
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
+// Arrive on `bar` once every earlier cp.async of this thread has landed (no pending-count increment).
+__device__ __forceinline__ void cp_async_arrive_noinc(uint32_t bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 B apart.
-__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFF) >> 4);     // start address
     d |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(512 >> 4) << 32;             // stride byte offset
+    d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset
     d |= (uint64_t)1 << 46;                      // descriptor version
-    d |= (uint64_t)4 << 61;                      // 64-byte swizzle
+    d |= (uint64_t)2 << 61;                      // 128-byte swizzle
     return d;
 }
 
@@ -154,7 +155,8 @@ struct TcArgs {
     const uint16_t *C;          // [disp][36 images]
     const int32_t *Cexp;        // [disp] or null
     const int32_t *Xexp;        // [col]
-    int plane_rows;             // tensor-map rows per hi/lo plane
+    const uint16_t *Xtc;        // [hl][col][reim][192]
+    int64_t plane;              // elements per hl plane of Xtc
     const int32_t *src, *dst;
     float *Yslab;               // float view of the complex64 slabs
     size_t slab_stride;         // complex elements between slabs
@@ -165,7 +167,7 @@ struct TcArgs {
 
 template <bool FP16, bool X3>
 __global__ void __launch_bounds__(kThreadsTc, 1)
-translate_tc_kernel(const __grid_constant__ CUtensorMap xmap, const TcArgs a) {
+translate_tc_kernel(const TcArgs a) {
     if (a.gate && *a.gate == 0) return;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -181,7 +183,7 @@ translate_tc_kernel(const __grid_constant__ CUtensorMap xmap, const TcArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&full[s]), kProducers + 1);
             mbar_init(smem_u32(&empty[s]), 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -191,7 +193,7 @@ translate_tc_kernel(const __grid_constant__ CUtensorMap xmap, const TcArgs a) {
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {
+    if (warp == 4) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -202,8 +204,9 @@ translate_tc_kernel(const __grid_constant__ CUtensorMap xmap, const TcArgs a) {
     const uint32_t tmem_base = *tmem_slot;
 
     const int64_t first = blockIdx.x, step = gridDim.x;
-    if (warp == 0) {
-        // ---------------- producer warp
+    if (warp < 4) {
+        // ---------------- producers (warps 0-3)
+        const int tid = threadIdx.x;
         int64_t il = 0;
         int64_t armed[kStages];
         for (int s = 0; s < kStages; ++s) armed[s] = -1;
@@ -211,25 +214,20 @@ translate_tc_kernel(const __grid_constant__ CUtensorMap xmap, const TcArgs a) {
         for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
             const WorkItem it = a.items[i];
             const int ncols = it.npairs * a.nrhs;
-            const int nmma = (2 * ncols + 15) & ~15;
-            const int ngroups = nmma >> 2;                 // gather4 groups of 4 B rows
-            int rows[2][4];
+            const int nreal = 2 * ncols;
+            // this thread's B rows (n = tid, tid + 128) and their source rows in Xtc
+            const uint16_t *grow[2];
 #pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                const int gq = lane + 32 * t;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int n = 4 * gq + q, j = n >> 1, part = n & 1;
-                    int row = part;                        // padding rows read row 0/1 (discarded)
-                    if (gq < ngroups && j < ncols) {
-                        const int p = it.pair0 + j / a.nrhs, r = j % a.nrhs;
-                        row = 2 * (r * a.nbox + a.src[p]) + part;
-                    }
-                    rows[t][q] = row;
+            for (int t2 = 0; t2 < 2; ++t2) {
+                const int n = tid + kProducers * t2;
+                grow[t2] = nullptr;
+                if (n < nreal) {
+                    const int j = n >> 1, part = n & 1;
+                    const int p = it.pair0 + j / a.nrhs, r = j % a.nrhs;
+                    grow[t2] = a.Xtc + (2 * ((int64_t)r * a.nbox + a.src[p]) + part) * kNU;
                 }
             }
             const uint16_t *Cd = a.C + (int64_t)it.disp * kTcDispElems;
-            const uint32_t bytes = (X3 ? 2u : 1u) * (uint32_t)(kImgBytes + nmma * kTcK * 2);
             for (int kc = 0; kc < kTcKChunks; ++kc) {
                 const int64_t g = il * kTcKChunks + kc;
                 const int s = (int)(g % kStages);
@@ -241,42 +239,42 @@ translate_tc_kernel(const __grid_constant__ CUtensorMap xmap, const TcArgs a) {
                 unsigned char *st = smem + s * kStageBytes;
                 const uint32_t sA = smem_u32(st), sB = smem_u32(st + 2 * kImgBytes);
                 const uint32_t fb = smem_u32(&full[s]);
-                if (lane == 0) {
-                    mbar_arrive_expect_tx(fb, bytes);
+                if (tid == 0) {
+                    mbar_arrive_expect_tx(fb, X3 ? 2 * kImgBytes : kImgBytes);
                     armed[s] = g;
                     const uint16_t *img = Cd + (int64_t)((it.mb * kTcKChunks + kc) * 2) * kTcImageElems;
                     bulk_g2s(sA, img, kImgBytes, fb);
                     if (X3) bulk_g2s(sA + kImgBytes, img + kTcImageElems, kImgBytes, fb);
                 }
-                __syncwarp();
 #pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                    const int gq = lane + 32 * t;
-                    if (gq < ngroups) {
-                        const uint32_t off = (uint32_t)gq * 4 * (kTcK * 2);
-                        tma_gather4(sB + off, &xmap, kc * kTcK, rows[t][0], rows[t][1], rows[t][2], rows[t][3], fb);
-                        if (X3)
-                            tma_gather4(sB + kBBytes + off, &xmap, kc * kTcK, rows[t][0] + a.plane_rows,
-                                        rows[t][1] + a.plane_rows, rows[t][2] + a.plane_rows,
-                                        rows[t][3] + a.plane_rows, fb);
+                for (int t2 = 0; t2 < 2; ++t2) {
+                    if (!grow[t2]) continue;
+                    const int n = tid + kProducers * t2;
+                    const uint32_t rbase = (uint32_t)((n >> 3) * 1024 + (n & 7) * 128);
+                    const uint16_t *gs = grow[t2] + kc * kTcK;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const uint32_t off = rbase + (uint32_t)((c ^ (n & 7)) * 16);
+                        cp_async16(sB + off, gs + c * 8);
+                        if (X3) cp_async16(sB + kBBytes + off, gs + a.plane + c * 8);
                     }
                 }
-                __syncwarp();
+                cp_async_arrive_noinc(fb);
             }
         }
+        cp_async_wait_all();
         if (!ok) {
-            if (lane == 0) {
+            if (tid == 0) {
                 atomicExch(a.err, 1);
-                // drain: every stage this CTA armed completes once its bytes land
+                // drain: every stage this CTA armed completes once its bulk bytes land
                 for (int s = 0; s < kStages; ++s) {
                     if (armed[s] < 0) continue;
                     const uint32_t ph = (uint32_t)((armed[s] / kStages) & 1);
                     for (uint32_t w = 0; w < kSpinLimit && !mbar_try_wait(smem_u32(&full[s]), ph); ++w) __nanosleep(64);
                 }
             }
-            __syncwarp();
         }
-    } else if (warp == 1) {
+    } else if (warp == 4) {
         // ---------------- MMA issuer (lane 0)
         if (lane == 0) {
             int64_t il = 0;
@@ -302,16 +300,17 @@ translate_tc_kernel(const __grid_constant__ CUtensorMap xmap, const TcArgs a) {
                         ok = false;
                         break;
                     }
+                    fence_proxy_async();     // gathered rows (generic proxy) -> tensor core (async proxy)
                     tc_fence_after();
                     unsigned char *st = smem + s * kStageBytes;
                     const uint32_t sA = smem_u32(st), sB = smem_u32(st + 2 * kImgBytes);
 #pragma unroll
                     for (int k = 0; k < kTcK / 16; ++k) {
-                        const uint64_t ah = sw64_desc(sA + k * 32), bh = sw64_desc(sB + k * 32);
+                        const uint64_t ah = sw128_desc(sA + k * 32), bh = sw128_desc(sB + k * 32);
                         umma(dt, ah, bh, idesc, (kc | k) ? 1u : 0u);
                         if (X3) {
-                            const uint64_t al = sw64_desc(sA + kImgBytes + k * 32);
-                            const uint64_t bl = sw64_desc(sB + kBBytes + k * 32);
+                            const uint64_t al = sw128_desc(sA + kImgBytes + k * 32);
+                            const uint64_t bl = sw128_desc(sB + kBBytes + k * 32);
                             umma(dt, ah, bl, idesc, 1u);
                             umma(dt, al, bh, idesc, 1u);
                         }
@@ -323,9 +322,9 @@ translate_tc_kernel(const __grid_constant__ CUtensorMap xmap, const TcArgs a) {
             if (!ok) atomicExch(a.err, 1);
         }
     } else {
-        // ---------------- epilogue warps 2-5 (TMEM lane quarter = warp mod 4)
+        // ---------------- epilogue warps 5-8 (TMEM lane quarter = warp mod 4)
         const int q = warp & 3;
-        const int te = threadIdx.x - 64;
+        const int te = threadIdx.x - kEpiFirst;
         const int64_t slab_f = (int64_t)a.slab_stride * 2;
         int64_t il = 0;
         for (int64_t i = first; i < a.n_items; i += step, ++il) {
@@ -368,7 +367,7 @@ translate_tc_kernel(const __grid_constant__ CUtensorMap xmap, const TcArgs a) {
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 1) {
+    if (warp == 4) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols));
     }
@@ -377,25 +376,6 @@ translate_tc_kernel(const __grid_constant__ CUtensorMap xmap, const TcArgs a) {
 template <bool FP16, bool X3>
 ie_status set_attr() {
     IE_CK(cudaFuncSetAttribute(translate_tc_kernel<FP16, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
-    return IE_OK;
-}
-
-using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-std::mutex g_enc_mu;
-EncodeTiled g_encode = nullptr;
-
-ie_status tensor_map_encoder(EncodeTiled *out) {
-    std::lock_guard<std::mutex> lk(g_enc_mu);
-    if (!g_encode) {
-        void *fn = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        IE_CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
-        if (q != cudaDriverEntryPointSuccess || !fn) return set_error("cuTensorMapEncodeTiled unavailable"), IE_ERR_CUDA;
-        g_encode = reinterpret_cast<EncodeTiled>(fn);
-    }
-    *out = g_encode;
     return IE_OK;
 }
 
@@ -417,26 +397,14 @@ ie_status launch_translate_tc(ie_plan p, int prec, float2 *Yslab, int nrhs, cuda
     WorkList *wl = nullptr;
     IE_TRY(work_list(p, true, nrhs, &wl));
     if (wl->n == 0) return IE_OK;
-    // 2-D view of the split source vectors: rows (hl, rhs, box, reim) of 192 16-bit values
-    EncodeTiled enc = nullptr;
-    IE_TRY(tensor_map_encoder(&enc));
-    const int plane_rows = nrhs * p->nbox * 2;
-    CUtensorMap map;
-    cuuint64_t dims[2] = {(cuuint64_t)kNU, (cuuint64_t)(2 * plane_rows)};
-    cuuint64_t strides[1] = {(cuuint64_t)kNU * 2};
-    cuuint32_t box[2] = {(cuuint32_t)kTcK, 1};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, p->d_Xtc, dims, strides, box, estr,
-                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) return set_error("cuTensorMapEncodeTiled failed (%d)", (int)cr), IE_ERR_CUDA;
     TcArgs a;
     a.items = wl->d_items;
     a.n_items = wl->n;
     a.C = C;
     a.Cexp = fp16 ? p->d_Cexp16 : nullptr;
     a.Xexp = p->d_Xexp;
-    a.plane_rows = plane_rows;
+    a.Xtc = p->d_Xtc;
+    a.plane = (int64_t)nrhs * p->nbox * 2 * kNU;
     a.src = p->d_src;
     a.dst = p->d_dst;
     a.Yslab = reinterpret_cast<float *>(Yslab);
@@ -447,11 +415,11 @@ ie_status launch_translate_tc(ie_plan p, int prec, float2 *Yslab, int nrhs, cuda
     a.gate = gate;
     int grid = (int)std::min<int64_t>(wl->n, p->tc_sms > 0 ? p->tc_sms : 148);
     if (prec == IE_PREC_BF16X3)
-        translate_tc_kernel<false, true><<<grid, kThreadsTc, kSmemBytes, st>>>(map, a);
+        translate_tc_kernel<false, true><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
     else if (prec == IE_PREC_FP16X3)
-        translate_tc_kernel<true, true><<<grid, kThreadsTc, kSmemBytes, st>>>(map, a);
+        translate_tc_kernel<true, true><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
     else if (prec == IE_PREC_BF16X1)
-        translate_tc_kernel<false, false><<<grid, kThreadsTc, kSmemBytes, st>>>(map, a);
+        translate_tc_kernel<false, false><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
     else
         return set_error("not a tensor-core precision: %d", prec), IE_ERR_INVALID;
     IE_CK_LAUNCH();
