@@ -72,9 +72,9 @@ __global__ void coupling_fp32_kernel(double k, double eta, double h, const int32
 // Real embedding of y = G x with G = Gr + j Gi, split operands x = [xr; xi]:
 // real row 2m holds Gr[m][:], row 2m+1 holds Gi[m][:]; the GEMM against the
 // columns xr and xi gives Gr xr, Gr xi, Gi xr, Gi xi, combined in the epilogue.
-// Image (mb, kc, hl): rows 128 mb .. +127, source unknowns 64 kc .. +63, hi or lo
-// 16-bit part, in the 128-byte-swizzled K-major layout of tcgen05.mma: row r is 128 B,
-// its 16-byte chunk c lands at chunk c ^ (r mod 8).  One CTA per displacement.
+// Image (mb, kc, hl): rows 128 mb .. +127, source unknowns 32 kc .. +31, hi or lo
+// 16-bit part, in the 64-byte-swizzled K-major layout of tcgen05.mma: row r is 64 B,
+// its 16-byte chunk c lands at chunk c ^ ((r / 2) mod 4).  One CTA per displacement.
 // fp16: scaled by 2^-e (e stored) so that |entries| <= 2^14.
 template <bool FP16>
 __global__ void coupling_tc_kernel(const float2 *__restrict__ Cs, int64_t nd, uint16_t *__restrict__ out,
@@ -109,11 +109,11 @@ __global__ void coupling_tc_kernel(const float2 *__restrict__ Cs, int64_t nd, ui
         scale = s_scale;
     }
     uint16_t *img0 = out + di * (int64_t)kTcDispElems;
-    // 18 images x 128 rows x 8 chunks of 16 bytes
-    for (int w = threadIdx.x; w < kTcImagesPerDisp * 128 * 8; w += blockDim.x) {
-        int c = w & 7;
-        int r = (w >> 3) & 127;
-        int img = w >> 10;              // (mb * 3 + kc) * 2 + hl
+    // 36 images x 128 rows x 4 chunks of 16 bytes
+    for (int w = threadIdx.x; w < kTcImagesPerDisp * 128 * 4; w += blockDim.x) {
+        int c = w & 3;
+        int r = (w >> 2) & 127;
+        int img = w >> 9;               // (mb * 6 + kc) * 2 + hl
         int hl = img & 1;
         int kc = (img >> 1) % kTcKChunks;
         int mb = (img >> 1) / kTcKChunks;
@@ -140,7 +140,8 @@ __global__ void coupling_tc_kernel(const float2 *__restrict__ Cs, int64_t nd, ui
         pk.y = vals[2] | ((uint32_t)vals[3] << 16);
         pk.z = vals[4] | ((uint32_t)vals[5] << 16);
         pk.w = vals[6] | ((uint32_t)vals[7] << 16);
-        uint4 *dst = reinterpret_cast<uint4 *>(img0 + (int64_t)img * kTcImageElems + r * kTcK + 8 * (c ^ (r & 7)));
+        uint4 *dst = reinterpret_cast<uint4 *>(img0 + (int64_t)img * kTcImageElems + r * kTcK +
+                                               8 * (c ^ ((r >> 1) & 3)));
         *dst = pk;
     }
 }

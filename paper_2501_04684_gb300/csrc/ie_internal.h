@@ -20,12 +20,12 @@ constexpr int kNU = 192;            // 3 unknowns per site
 constexpr int kSlabs = 8;           // FP32 partial-sum slabs of the far field (see translate_simt.cu)
 
 // Tensor-core store of one coupling block: 3 M-blocks (128 real-embedded rows) x
-// 3 K-chunks (64 source unknowns) x {hi, lo}, each a 128 x 64 16-bit image laid out
-// exactly as the 128-byte-swizzled K-major shared-memory operand of tcgen05.mma (16 KB).
-constexpr int kTcK = 64;
-constexpr int kTcKChunks = kNU / kTcK;                          // 3
+// 6 K-chunks (32 source unknowns) x {hi, lo}, each a 128 x 32 16-bit image laid out
+// exactly as the 64-byte-swizzled K-major shared-memory operand of tcgen05.mma (8 KB).
+constexpr int kTcK = 32;
+constexpr int kTcKChunks = kNU / kTcK;                          // 6
 constexpr int kTcImageElems = 128 * kTcK;
-constexpr int kTcImagesPerDisp = 3 * kTcKChunks * 2;            // 18
+constexpr int kTcImagesPerDisp = 3 * kTcKChunks * 2;            // 36
 constexpr size_t kTcDispElems = (size_t)kTcImageElems * kTcImagesPerDisp;   // 147,456
 
 void set_error(const char *fmt, ...);

@@ -11,19 +11,23 @@
 //
 // Work item = (displacement, M-block of 128 real rows, run of <= 128 complex columns).
 // Persistent CTAs walk the size-sorted item list round-robin.  Warp roles:
-//   warps 0-3  producers: per K-chunk of 64, one thread bulk-copies the two
-//              pre-swizzled 16 KB A images (TMA engine, complete_tx on the stage
-//              mbarrier); the 128 threads gather the item's B rows with 16-byte cp.async
-//              into the SW128 K-major layout (chunk c of row n at c ^ (n mod 8)), row
-//              addresses computed once per item, and signal the same mbarrier with
-//              cp.async.mbarrier.arrive.noinc — nobody waits for its own copies.
-//   warp 4     MMA issuer (one thread): after the stage completes, a proxy fence makes
-//              the gathered rows visible to the tensor core; tcgen05.mma M=128, N<=256,
-//              K=16 from a 2-stage ring into one of two TMEM accumulators (2 x 256 cols).
-//   warps 5-8  epilogue: target offsets of the item's columns staged in shared memory
-//              before the accumulator is ready; tcgen05.ld of the warp's TMEM lane
-//              quarter, complex recombination, fp16 rescaling, red.global.add into the
-//              slab (d mod 8).
+//   warps 0-3  producers: per K-chunk of 32, one thread bulk-copies the two
+//              pre-swizzled 8 KB A images (TMA engine, complete_tx on the stage's `full`
+//              mbarrier); the 128 threads gather the item's B rows (<= 2 each) with
+//              16-byte cp.async into the 64-byte-swizzled K-major layout (chunk c of row n
+//              at c ^ ((n / 2) mod 4)), addresses prefetched one item ahead, and arrive on
+//              the stage's `landed` mbarrier when their copies complete
+//              (cp.async.mbarrier.arrive.noinc) — nobody waits for its own copies.
+//   warp 5     signaller (one thread): per stage, waits for `landed`, issues the proxy
+//              fence that makes the gathered rows visible to the tensor core, arrives on
+//              `full`.  48 KB stages, 4-deep ring.
+//   warp 4     MMA issuer (one thread): tcgen05.mma M=128, N<=256, K=16 with
+//              descriptors derived from one base, into one of two TMEM accumulators
+//              (2 x 256 columns).
+//   warps 6-13 epilogue (two warps per TMEM lane quarter, alternating 8-column chunks):
+//              target offsets of the item's columns staged in shared memory before the
+//              accumulator is ready; tcgen05.ld, complex recombination, fp16 rescaling,
+//              red.global.add into the slab (d mod 8).
 // Every wait is bounded and each role decides on a timeout uniformly (lane-0 wait +
 // shuffle, or a named barrier + abort flag), so no lane is ever left at a barrier; a
 // timeout sets the device error word, drains the CTA's copies, frees TMEM, returns.
@@ -35,14 +39,16 @@ namespace ie {
 namespace {
 
 constexpr int kTcTileCols = 128;                 // complex columns per work item (N <= 256)
-constexpr int kStages = 2;
+constexpr int kStages = 4;
+constexpr int kAcc = 2;                          // TMEM accumulators of 256 columns
 constexpr int kProducers = 128;
-constexpr int kThreadsTc = kProducers + 32 + 128;             // producers, MMA, epilogue
-constexpr int kEpiFirst = kProducers + 32;                    // first epilogue thread
-constexpr int kImgBytes = 128 * kTcK * 2;        // 16 KB A image
-constexpr int kBBytes = 256 * kTcK * 2;          // 32 KB B plane (256 rows x 128 B)
-constexpr int kStageBytes = 2 * kImgBytes + 2 * kBBytes;     // 96 KB
-constexpr int kEpiBytes = 2 * kTcTileCols * (8 + 4);          // column offsets + scales, 2 buffers
+constexpr int kEpilogue = 256;
+constexpr int kThreadsTc = kProducers + 32 + 32 + kEpilogue;  // producers, MMA, signaller, epilogue
+constexpr int kEpiFirst = kProducers + 64;                    // first epilogue thread
+constexpr int kImgBytes = 128 * kTcK * 2;        // 8 KB A image
+constexpr int kBBytes = 256 * kTcK * 2;          // 16 KB B plane (256 rows x 64 B)
+constexpr int kStageBytes = 2 * kImgBytes + 2 * kBBytes;     // 48 KB
+constexpr int kEpiBytes = kAcc * kTcTileCols * (8 + 4);       // column offsets + scales per accumulator
 constexpr int kSmemBytes = kStages * kStageBytes + kEpiBytes + 256 /*barriers*/ + 1024 /*alignment*/;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kSpinLimit = 1u << 24;
@@ -83,7 +89,7 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatil
     if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag) ? 1 : 0;
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
-__device__ __forceinline__ void named_sync_epilogue() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void named_sync_epilogue() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -103,14 +109,14 @@ __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFF) >> 4);     // start address
     d |= (uint64_t)1 << 16;                      // leading byte offset (unused for swizzled K-major)
-    d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset
+    d |= (uint64_t)(512 >> 4) << 32;             // stride byte offset
     d |= (uint64_t)1 << 46;                      // descriptor version
-    d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+    d |= (uint64_t)4 << 61;                      // 64-byte swizzle
     return d;
 }
 
@@ -171,24 +177,26 @@ translate_tc_kernel(const TcArgs a) {
     if (a.gate && *a.gate == 0) return;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    int64_t *ep_off = reinterpret_cast<int64_t *>(smem + kStages * kStageBytes);      // [2][128]
-    float *ep_scale = reinterpret_cast<float *>(ep_off + 2 * kTcTileCols);              // [2][128]
-    uint64_t *full = reinterpret_cast<uint64_t *>(ep_scale + 2 * kTcTileCols);          // [kStages]
+    int64_t *ep_off = reinterpret_cast<int64_t *>(smem + kStages * kStageBytes);      // [kAcc][64]
+    float *ep_scale = reinterpret_cast<float *>(ep_off + kAcc * kTcTileCols);           // [kAcc][64]
+    uint64_t *full = reinterpret_cast<uint64_t *>(ep_scale + kAcc * kTcTileCols);       // [kStages]
     uint64_t *empty = full + kStages;                                                    // [kStages]
-    uint64_t *accfull = empty + kStages;                                                 // [2]
-    uint64_t *accempty = accfull + 2;                                                    // [2]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accempty + 2);
+    uint64_t *landed = empty + kStages;                                                  // [kStages]
+    uint64_t *accfull = landed + kStages;                                                // [kAcc]
+    uint64_t *accempty = accfull + kAcc;                                                 // [kAcc]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accempty + kAcc);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(smem_u32(&full[s]), kProducers + 1);
+            mbar_init(smem_u32(&full[s]), 2);               // signaller + the A copies' expect_tx arrive
             mbar_init(smem_u32(&empty[s]), 1);
+            mbar_init(smem_u32(&landed[s]), kProducers);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kAcc; ++b) {
             mbar_init(smem_u32(&accfull[b]), 1);
-            mbar_init(smem_u32(&accempty[b]), 128);
+            mbar_init(smem_u32(&accempty[b]), kEpilogue);
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -207,29 +215,32 @@ translate_tc_kernel(const TcArgs a) {
     if (warp < 4) {
         // ---------------- producers (warps 0-3)
         const int tid = threadIdx.x;
-        int64_t il = 0;
         int64_t armed[kStages];
         for (int s = 0; s < kStages; ++s) armed[s] = -1;
         bool ok = true;
-        for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
+        // source rows of this thread's B rows n = tid, tid + 128 for item i (null = padding)
+        auto rows_of = [&](int64_t i, const uint16_t *r[2]) {
+            r[0] = r[1] = nullptr;
+            if (i >= a.n_items) return;
             const WorkItem it = a.items[i];
-            const int ncols = it.npairs * a.nrhs;
-            const int nreal = 2 * ncols;
-            // this thread's B rows (n = tid, tid + 128) and their source rows in Xtc
-            const uint16_t *grow[2];
+            const int nreal = 2 * it.npairs * a.nrhs;
 #pragma unroll
             for (int t2 = 0; t2 < 2; ++t2) {
                 const int n = tid + kProducers * t2;
-                grow[t2] = nullptr;
-                if (n < nreal) {
-                    const int j = n >> 1, part = n & 1;
-                    const int p = it.pair0 + j / a.nrhs, r = j % a.nrhs;
-                    grow[t2] = a.Xtc + (2 * ((int64_t)r * a.nbox + a.src[p]) + part) * kNU;
-                }
+                if (n >= nreal) continue;
+                const int j = n >> 1, part = n & 1;
+                const int p = it.pair0 + j / a.nrhs, rr = j % a.nrhs;
+                r[t2] = a.Xtc + (2 * ((int64_t)rr * a.nbox + a.src[p]) + part) * kNU;
             }
+        };
+        const uint16_t *grow[2], *gnext[2];
+        rows_of(first, grow);
+        int64_t g = 0;                 // stages issued by this CTA
+        for (int64_t i = first; i < a.n_items && ok; i += step) {
+            const WorkItem it = a.items[i];
+            rows_of(i + step, gnext);   // prefetch: loads in flight during this item
             const uint16_t *Cd = a.C + (int64_t)it.disp * kTcDispElems;
-            for (int kc = 0; kc < kTcKChunks; ++kc) {
-                const int64_t g = il * kTcKChunks + kc;
+            for (int kc = 0; kc < kTcKChunks; ++kc, ++g) {
                 const int s = (int)(g % kStages);
                 const uint32_t ph = (uint32_t)((g / kStages) & 1);
                 if (!warp_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag)) {
@@ -250,17 +261,19 @@ translate_tc_kernel(const TcArgs a) {
                 for (int t2 = 0; t2 < 2; ++t2) {
                     if (!grow[t2]) continue;
                     const int n = tid + kProducers * t2;
-                    const uint32_t rbase = (uint32_t)((n >> 3) * 1024 + (n & 7) * 128);
+                    const uint32_t rbase = (uint32_t)((n >> 3) * 512 + (n & 7) * 64);
                     const uint16_t *gs = grow[t2] + kc * kTcK;
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const uint32_t off = rbase + (uint32_t)((c ^ (n & 7)) * 16);
+                    for (int c = 0; c < 4; ++c) {
+                        const uint32_t off = rbase + (uint32_t)((c ^ ((n >> 1) & 3)) * 16);
                         cp_async16(sB + off, gs + c * 8);
                         if (X3) cp_async16(sB + kBBytes + off, gs + a.plane + c * 8);
                     }
                 }
-                cp_async_arrive_noinc(fb);
+                cp_async_arrive_noinc(smem_u32(&landed[s]));
             }
+            grow[0] = gnext[0];
+            grow[1] = gnext[1];
         }
         cp_async_wait_all();
         if (!ok) {
@@ -277,6 +290,7 @@ translate_tc_kernel(const TcArgs a) {
     } else if (warp == 4) {
         // ---------------- MMA issuer (lane 0)
         if (lane == 0) {
+            const uint64_t d0 = sw64_desc(smem_u32(smem));   // stage s: + s * kStageBytes / 16
             int64_t il = 0;
             bool ok = true;
             for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
@@ -284,8 +298,8 @@ translate_tc_kernel(const TcArgs a) {
                 const int ncols = it.npairs * a.nrhs;
                 const int nmma = (2 * ncols + 15) & ~15;
                 const uint32_t idesc = f16_idesc(nmma, FP16);
-                const int buf = (int)(il & 1);
-                const uint32_t aph = (uint32_t)((il >> 1) & 1);
+                const int buf = (int)(il % kAcc);
+                const uint32_t aph = (uint32_t)((il / kAcc) & 1);
                 if (!mbar_wait(smem_u32(&accempty[buf]), aph ^ 1, abort_flag)) {
                     ok = false;
                     break;
@@ -300,20 +314,20 @@ translate_tc_kernel(const TcArgs a) {
                         ok = false;
                         break;
                     }
-                    fence_proxy_async();     // gathered rows (generic proxy) -> tensor core (async proxy)
                     tc_fence_after();
-                    unsigned char *st = smem + s * kStageBytes;
-                    const uint32_t sA = smem_u32(st), sB = smem_u32(st + 2 * kImgBytes);
-#pragma unroll
-                    for (int k = 0; k < kTcK / 16; ++k) {
-                        const uint64_t ah = sw128_desc(sA + k * 32), bh = sw128_desc(sB + k * 32);
-                        umma(dt, ah, bh, idesc, (kc | k) ? 1u : 0u);
-                        if (X3) {
-                            const uint64_t al = sw128_desc(sA + kImgBytes + k * 32);
-                            const uint64_t bl = sw128_desc(sB + kBBytes + k * 32);
-                            umma(dt, ah, bl, idesc, 1u);
-                            umma(dt, al, bh, idesc, 1u);
-                        }
+                    // descriptors of this stage; +2 advances the start address by 32 B (K = 16)
+                    const uint64_t ah = d0 + (uint64_t)(s * (kStageBytes >> 4));
+                    const uint64_t bh = ah + (uint64_t)((2 * kImgBytes) >> 4);
+                    const uint64_t al = ah + (uint64_t)(kImgBytes >> 4), bl = bh + (uint64_t)(kBBytes >> 4);
+                    umma(dt, ah, bh, idesc, kc ? 1u : 0u);
+                    if (X3) {
+                        umma(dt, ah, bl, idesc, 1u);
+                        umma(dt, al, bh, idesc, 1u);
+                    }
+                    umma(dt, ah + 2, bh + 2, idesc, 1u);
+                    if (X3) {
+                        umma(dt, ah + 2, bl + 2, idesc, 1u);
+                        umma(dt, al + 2, bh + 2, idesc, 1u);
                     }
                     umma_commit(smem_u32(&empty[s]));
                     if (kc == kTcKChunks - 1) umma_commit(smem_u32(&accfull[buf]));
@@ -321,19 +335,42 @@ translate_tc_kernel(const TcArgs a) {
             }
             if (!ok) atomicExch(a.err, 1);
         }
+    } else if (warp == 5) {
+        // ---------------- signaller (lane 0)
+        if (lane == 0) {
+            int64_t g = 0;
+            for (int64_t i = first; i < a.n_items; i += step) {
+                bool ok = true;
+                for (int kc = 0; kc < kTcKChunks; ++kc, ++g) {
+                    const int s = (int)(g % kStages);
+                    const uint32_t ph = (uint32_t)((g / kStages) & 1);
+                    if (!mbar_wait(smem_u32(&landed[s]), ph, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_proxy_async();     // gathered rows (generic proxy) -> tensor core (async proxy)
+                    mbar_arrive(smem_u32(&full[s]));
+                }
+                if (!ok) {
+                    atomicExch(a.err, 1);
+                    break;
+                }
+            }
+        }
     } else {
-        // ---------------- epilogue warps 5-8 (TMEM lane quarter = warp mod 4)
+        // ---------------- epilogue warps 6-13 (TMEM lane quarter = warp mod 4)
         const int q = warp & 3;
+        const int half = (warp - kEpiFirst / 32) >> 2;     // which alternate 8-column chunks
         const int te = threadIdx.x - kEpiFirst;
         const int64_t slab_f = (int64_t)a.slab_stride * 2;
         int64_t il = 0;
         for (int64_t i = first; i < a.n_items; i += step, ++il) {
             const WorkItem it = a.items[i];
             const int ncols = it.npairs * a.nrhs;
-            const int buf = (int)(il & 1);
-            const uint32_t aph = (uint32_t)((il >> 1) & 1);
+            const int buf = (int)(il % kAcc);
+            const uint32_t aph = (uint32_t)((il / kAcc) & 1);
             const int ed = FP16 ? a.Cexp[it.disp] : 0;
-            for (int j = te; j < ncols; j += 128) {
+            for (int j = te; j < ncols; j += kEpilogue) {
                 const int p = it.pair0 + j / a.nrhs, r = j % a.nrhs;
                 ep_off[buf * kTcTileCols + j] = ((int64_t)r * a.nbox + a.dst[p]) * (2 * kNU);
                 if (FP16) ep_scale[buf * kTcTileCols + j] = ldexpf(1.f, ed + a.Xexp[(int64_t)r * a.nbox + a.src[p]]);
@@ -348,7 +385,7 @@ translate_tc_kernel(const TcArgs a) {
             const int m0 = 64 * it.mb + 16 * q;    // first complex row of this warp
             float *Ys = a.Yslab + (int64_t)(it.disp % kSlabs) * slab_f + 2 * m0 + lane;
             const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256);
-            for (int c0 = 0; c0 < 2 * ncols; c0 += 16) {
+            for (int c0 = 16 * half; c0 < 2 * ncols; c0 += 32) {
                 float v[16];
                 tmem_ld16(tbase + (uint32_t)c0, v);
 #pragma unroll
