@@ -286,11 +286,17 @@ def main():
     tc_ms = far["bf16x3"]["translate_kernel_ms"]
     tc_ach = tc_flops / (tc_ms / 1e3) / 1e12
     roofline = {"bound": "tensor", "achieved": tc_ach, "peak": peaks["bf16"], "unit": "TFLOP/s",
-                "frac": tc_ach / peaks["bf16"], "traffic": None, "kernel": "translate_tc_kernel<bf16,x3>",
-                "peak_source": peaks["source"]}
+                "frac": tc_ach / peaks["bf16"],
+                "traffic": profiled_traffic("translate_tc_bf16x3_shell16.md", "translate_tc.cu"),
+                "kernel": "translate_tc_kernel<bf16,x3>", "peak_source": peaks["source"],
+                "algorithmic_flops_per_launch": tc_flops,
+                "dram_gbs": None}
+    if roofline["traffic"]:
+        roofline["dram_gbs"] = roofline["traffic"] / (tc_ms / 1e3) / 1e9
     simt_ach = pairs * 8 * 192 * 192 / (far["fp32"]["translate_kernel_ms"] / 1e3) / 1e12
     roofline_fp32 = {"bound": "alu", "achieved": simt_ach, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": simt_ach / FP32_SIMT_PEAK_TFLOPS, "kernel": "translate_simt_kernel",
+                     "traffic": profiled_traffic("translate_simt_fp32_shell16.md", "translate_simt.cu"),
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
 
     hp = paths[HEADLINE]
@@ -344,6 +350,24 @@ def solve_paths(ie) -> dict:
 
 
 HEADLINE = "mixed"
+
+
+def profiled_traffic(summary: str, source: str):
+    """DRAM bytes per launch from a committed ncu summary, or None once the kernel source
+    has changed since the counters were taken (the summary records the source hash)."""
+    import hashlib
+    try:
+        text = open(os.path.join(ROOT, "profiles", summary)).read()
+        src = open(os.path.join(ROOT, "paper_2501_04684_gb300", "csrc", source), "rb").read()
+    except OSError:
+        return None
+    fields = dict(line.split(": ", 1) for line in text.splitlines() if ": " in line and not line.startswith(("|", " ")))
+    if fields.get("kernel_source_sha256_16", "").strip() != hashlib.sha256(src).hexdigest()[:16]:
+        return None
+    try:
+        return int(fields["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def measured_peaks() -> dict:
