@@ -86,6 +86,14 @@ typedef struct {
                               dipoles; 1: the box itself is left out                   */
     unsigned prec_mask;    /* IE_PRECMASK(...) of every precision the plan must serve  */
     int max_rhs;           /* largest nrhs any later call will pass (>= 1)             */
+    /* Batches of independent scatterers (optional; n_groups = 0: one scatterer).
+     * Boxes carry a scatterer id, ids non-decreasing in box order (each scatterer's
+     * boxes, hence its unknowns, are contiguous); boxes of different scatterers never
+     * interact, and two scatterers may occupy the same grid cells.  All scatterers
+     * share k, eta, box_edge and grid_n, hence one coupling-block store.           */
+    int n_groups;              /* >= 1 when box_group is given                      */
+    const int32_t *box_group;  /* HOST, n_boxes ids in [0, n_groups), non-decreasing */
+    const double *group_alpha; /* HOST, n_groups self terms (replaces alpha)        */
 } ie_problem;
 
 typedef struct {
@@ -101,11 +109,15 @@ typedef struct {
     double translate_ms;       /* with profiling on: summed device time of the
                                   translation kernel (CUDA events on its stream)      */
     int64_t translate_launches;/* with profiling on: launches timed                   */
+    int n_groups;              /* scatterers in the plan (1 without box_group)        */
+    int max_rhs;               /* the plan's max_rhs                                  */
 } ie_plan_stats;
 
 /* Build a plan: validate the geometry, group far box pairs by displacement, generate
  * every far coupling block G_d (eq. 13) and the near blocks P_a G_{b-a} P_b^T on the
- * device in FP64 arithmetic, stored in the layouts of the requested precisions.
+ * device in FP64 arithmetic, stored in the layouts of the requested precisions
+ * (the FP32 block store is kept only when IE_PREC_FP32 is requested; otherwise the
+ * 16-bit images are cut from a bounded FP32 staging buffer, chunk by chunk).
  * Host inputs are copied; they may be freed on return.  Synchronises `stream`.
  * Errors: IE_ERR_INVALID (lattice != 4, n_boxes < 1, duplicate boxes, nb outside
  * [1,192], P/nb mismatch, max_rhs < 1, empty prec_mask), IE_ERR_OOM, IE_ERR_CUDA. */
@@ -155,7 +167,8 @@ ie_status ie_disaggregate(ie_plan plan, const void *Y, void *r, int nrhs, void *
  * ie_last_error().  The first call on a device looks the area up and sets the kernel
  * up on that device (make it before any stream capture).  Every call reuses the same
  * area, so calls that overlap in time on the GPU (any streams, any plans) race; the
- * partial sums are cleared by each call.  X, Y: device complex64 [nrhs][n_boxes][192]. */
+ * partial sums are cleared by each call.  X, Y: device complex64 [nrhs][n_boxes][192].
+ * A plan built without IE_PREC_FP32 returns IE_ERR_UNSUPPORTED. */
 ie_status ie_translate_noalloc(ie_plan plan, const void *X, void *Y, int nrhs, void *stream);
 
 /* Near product (eq. 2, stored Z^N) plus the self term: y = alpha c + Z^N c. */
@@ -168,7 +181,10 @@ ie_status ie_near(ie_plan plan, const void *c, void *y, int nrhs, void *stream);
 ie_status ie_coupling_blocks(ie_plan plan, const int32_t *d, int nd, void *out, void *stream);
 
 /* Plane-wave excitation tested with the basis functions (§5): v = P e with
- * e[r][b][3s+a] = pol_r[a] exp(-j k khat_r . r_s).  khat, pol: HOST double nrhs x 3;
+ * e[r][b][3s+a] = pol_r[a] exp(-j k khat_r . r_s).  khat, pol: HOST double nrhs x 3
+ * (batched plans: n_groups x nrhs x 3, scatterer-major, so each scatterer has its own
+ * incidences; a zero polarisation leaves that scatterer's column at zero);
+ * nrhs in [1, max_rhs] counts the columns of v, not n_groups x nrhs;
  * v: device complex64 [nrhs][n]. */
 ie_status ie_rhs_plane_wave(ie_plan plan, const double *khat, const double *pol, int nrhs, void *v,
                             void *stream);
@@ -200,7 +216,9 @@ typedef struct {
 /* Fill `o` with the defaults above. */
 void ie_solve_opts_default(ie_solve_opts *o);
 
-/* Solve Z c = v for nrhs independent right-hand sides with restarted GMRES (§5):
+/* Solve Z c = v for nrhs independent right-hand sides with restarted GMRES (§5);
+ * in a batched plan every (scatterer, right-hand side) pair is its own GMRES system
+ * over its scatterer's unknowns, with its own convergence test:
  * x0 = 0, Arnoldi by classical Gram-Schmidt applied twice with FP64 dot products,
  * Givens rotations and the small least-squares solve in FP64, Krylov vectors in
  * FP32 on the device.  With refine = 1, c is kept in FP64, each outer step forms

@@ -22,6 +22,7 @@ IE_OK, IE_ERR_INVALID, IE_ERR_OOM, IE_ERR_CUDA, IE_ERR_NOT_CONVERGED, IE_ERR_TIM
 IE_PREC_FP32, IE_PREC_BF16X3, IE_PREC_FP16X3, IE_PREC_BF16X1 = 1, 2, 3, 4
 IE_FAR, IE_NEAR, IE_FULL = 1, 2, 3
 PREC_NAMES = {IE_PREC_FP32: "fp32", IE_PREC_BF16X3: "bf16x3", IE_PREC_FP16X3: "fp16x3", IE_PREC_BF16X1: "bf16x1"}
+NU = 192                      # dipole unknowns per box (4^3 lattice x 3 orientations)
 
 EXPORTED = [
     "ie_plan_create", "ie_plan_footprint", "ie_plan_stats_get", "ie_plan_destroy", "ie_matvec",
@@ -44,14 +45,16 @@ class ie_problem(ctypes.Structure):
                 ("lattice", ctypes.c_int), ("grid_n", ctypes.c_int), ("n_boxes", ctypes.c_int),
                 ("box_ijk", ctypes.c_void_p), ("nb", ctypes.c_void_p), ("P", ctypes.c_void_p),
                 ("alpha", ctypes.c_double), ("self_box_mode", ctypes.c_int), ("prec_mask", ctypes.c_uint),
-                ("max_rhs", ctypes.c_int)]
+                ("max_rhs", ctypes.c_int), ("n_groups", ctypes.c_int), ("box_group", ctypes.c_void_p),
+                ("group_alpha", ctypes.c_void_p)]
 
 
 class ie_plan_stats(ctypes.Structure):
     _fields_ = [("n_boxes", ctypes.c_int), ("n", ctypes.c_int64), ("n_far_pairs", ctypes.c_int64),
                 ("n_far_disp", ctypes.c_int64), ("n_near_pairs", ctypes.c_int64), ("n_work_simt", ctypes.c_int64),
                 ("n_work_tc", ctypes.c_int64), ("device_bytes", ctypes.c_size_t), ("plan_seconds", ctypes.c_double),
-                ("translate_ms", ctypes.c_double), ("translate_launches", ctypes.c_int64)]
+                ("translate_ms", ctypes.c_double), ("translate_launches", ctypes.c_int64),
+                ("n_groups", ctypes.c_int), ("max_rhs", ctypes.c_int)]
 
 
 class ie_solve_opts(ctypes.Structure):
@@ -134,6 +137,27 @@ def _ptr(t) -> int:
     return t.data_ptr()
 
 
+def _need(t, count: int, what: str):
+    """Marshalling check of a device buffer: a CUDA complex64 contiguous tensor of at
+    least `count` elements (raw integer pointers are passed through unchecked)."""
+    if t is None or isinstance(t, int):
+        return
+    if isinstance(t, np.ndarray):
+        raise TypeError(f"{what}: device buffer expected, got a numpy array")
+    import torch
+    if not t.is_cuda or t.dtype != torch.complex64 or not t.is_contiguous():
+        raise TypeError(f"{what}: contiguous CUDA complex64 tensor expected")
+    if t.numel() < count:
+        raise ValueError(f"{what}: {t.numel()} elements, at least {count} needed")
+
+
+def _dims(plan) -> tuple[int, int, int]:
+    """(n basis unknowns, n_boxes, n_groups) of a plan handle."""
+    s = ie_plan_stats()
+    _check(lib().ie_plan_stats_get(plan, ctypes.byref(s)), "ie_plan_stats_get")
+    return int(s.n), int(s.n_boxes), int(s.n_groups)
+
+
 def _stream(stream) -> int | None:
     if stream is None:
         import torch
@@ -144,16 +168,21 @@ def _stream(stream) -> int | None:
 
 
 def make_problem(k, eta, box_edge, grid_n, box_ijk, nb, P, alpha, prec_mask, max_rhs=1, self_box_mode=0,
-                 lattice=4):
-    """Build an ie_problem struct; keeps the host arrays alive on the returned object."""
+                 lattice=4, box_group=None, group_alpha=None):
+    """Build an ie_problem struct; keeps the host arrays alive on the returned object.
+    box_group / group_alpha: batch of independent scatterers (ids non-decreasing)."""
     ijk = np.ascontiguousarray(box_ijk, dtype=np.int32)
     nb_a = None if nb is None else np.ascontiguousarray(nb, dtype=np.int32)
     P_a = None if P is None else np.ascontiguousarray(np.asarray(P, dtype=np.complex128))
+    bg = None if box_group is None else np.ascontiguousarray(box_group, dtype=np.int32)
+    ga = None if group_alpha is None else np.ascontiguousarray(group_alpha, dtype=np.float64)
     pr = ie_problem(k=k, eta=eta, box_edge=box_edge, lattice=lattice, grid_n=grid_n, n_boxes=ijk.shape[0],
                     box_ijk=ijk.ctypes.data, nb=None if nb_a is None else nb_a.ctypes.data,
                     P=None if P_a is None else P_a.ctypes.data, alpha=alpha, self_box_mode=self_box_mode,
-                    prec_mask=prec_mask, max_rhs=max_rhs)
-    pr._keep = (ijk, nb_a, P_a)
+                    prec_mask=prec_mask, max_rhs=max_rhs, n_groups=0 if ga is None else len(ga),
+                    box_group=None if bg is None else bg.ctypes.data,
+                    group_alpha=None if ga is None else ga.ctypes.data)
+    pr._keep = (ijk, nb_a, P_a, bg, ga)
     return pr
 
 
@@ -161,6 +190,15 @@ def problem_from(p, prec_mask: int, max_rhs: int = 1):
     """ie_problem from a workloads.Problem-like object."""
     return make_problem(p.k, p.eta, p.a, p.G, p.box_ijk, None if p.P is None else p.nb, p.P, p.alpha, prec_mask,
                         max_rhs, getattr(p, "self_box_mode", 0), p.lattice)
+
+
+def problem_from_batch(b, prec_mask: int, max_rhs: int | None = None):
+    """ie_problem of a batch of scatterers (workloads.Batch-like: members in order,
+    box_group ids, one self term per member)."""
+    m0 = b.members[0]
+    return make_problem(m0.k, m0.eta, m0.a, b.G, b.box_ijk, b.nb, b.P, m0.alpha, prec_mask,
+                        b.max_rhs if max_rhs is None else max_rhs, getattr(m0, "self_box_mode", 0), m0.lattice,
+                        box_group=b.box_group, group_alpha=b.group_alpha)
 
 
 # ---------------------------------------------------------------- C ABI, same names
@@ -191,39 +229,64 @@ def ie_plan_destroy(plan: int) -> None:
 
 
 def ie_matvec(plan, which, prec, c, y, nrhs, stream=None):
+    n, _, _ = _dims(plan)
+    _need(c, nrhs * n, "c")
+    _need(y, nrhs * n, "y")
     return _check(lib().ie_matvec(plan, which, prec, _ptr(c), _ptr(y), nrhs, _stream(stream)), "ie_matvec")
 
 
 def ie_aggregate(plan, c, X, nrhs, stream=None):
+    n, nbox, _ = _dims(plan)
+    _need(c, nrhs * n, "c")
+    _need(X, nrhs * nbox * NU, "X")
     return _check(lib().ie_aggregate(plan, _ptr(c), _ptr(X), nrhs, _stream(stream)), "ie_aggregate")
 
 
 def ie_translate(plan, prec, X, Y, nrhs, stream=None):
+    _, nbox, _ = _dims(plan)
+    _need(X, nrhs * nbox * NU, "X")
+    _need(Y, nrhs * nbox * NU, "Y")
     return _check(lib().ie_translate(plan, prec, _ptr(X), _ptr(Y), nrhs, _stream(stream)), "ie_translate")
 
 
 def ie_translate_noalloc(plan, X, Y, nrhs, stream=None):
+    _, nbox, _ = _dims(plan)
+    _need(X, nrhs * nbox * NU, "X")
+    _need(Y, nrhs * nbox * NU, "Y")
     return _check(lib().ie_translate_noalloc(plan, _ptr(X), _ptr(Y), nrhs, _stream(stream)), "ie_translate_noalloc")
 
 
 def ie_disaggregate(plan, Y, r, nrhs, stream=None):
+    n, nbox, _ = _dims(plan)
+    _need(Y, nrhs * nbox * NU, "Y")
+    _need(r, nrhs * n, "r")
     return _check(lib().ie_disaggregate(plan, _ptr(Y), _ptr(r), nrhs, _stream(stream)), "ie_disaggregate")
 
 
 def ie_near(plan, c, y, nrhs, stream=None):
+    n, _, _ = _dims(plan)
+    _need(c, nrhs * n, "c")
+    _need(y, nrhs * n, "y")
     return _check(lib().ie_near(plan, _ptr(c), _ptr(y), nrhs, _stream(stream)), "ie_near")
 
 
 def ie_coupling_blocks(plan, d, out, stream=None):
     d = np.ascontiguousarray(d, dtype=np.int32).reshape(-1, 3)
+    _need(out, d.shape[0] * NU * NU, "out")
     return _check(lib().ie_coupling_blocks(plan, d.ctypes.data, d.shape[0], _ptr(out), _stream(stream)),
                   "ie_coupling_blocks")
 
 
 def ie_rhs_plane_wave(plan, khat, pol, v, stream=None):
-    khat = np.ascontiguousarray(khat, dtype=np.float64).reshape(-1, 3)
-    pol = np.ascontiguousarray(pol, dtype=np.float64).reshape(-1, 3)
-    return _check(lib().ie_rhs_plane_wave(plan, khat.ctypes.data, pol.ctypes.data, khat.shape[0], _ptr(v),
+    """khat, pol: (nrhs, 3), or (n_groups, nrhs, 3) for a batched plan; v: [nrhs][n]."""
+    n, _, groups = _dims(plan)
+    khat = np.ascontiguousarray(khat, dtype=np.float64)
+    pol = np.ascontiguousarray(pol, dtype=np.float64)
+    nrhs = khat.shape[-2] if khat.ndim >= 2 else 1
+    if khat.size != groups * nrhs * 3 or pol.shape != khat.shape:
+        raise ValueError(f"khat/pol must be ({groups}, nrhs, 3) for this plan, got {khat.shape} / {pol.shape}")
+    _need(v, nrhs * n, "v")
+    return _check(lib().ie_rhs_plane_wave(plan, khat.ctypes.data, pol.ctypes.data, nrhs, _ptr(v),
                                           _stream(stream)), "ie_rhs_plane_wave")
 
 
@@ -239,15 +302,22 @@ def ie_solve(plan, v, c, nrhs, opts: ie_solve_opts | None = None, stream=None):
     """Returns (status, info dict); IE_ERR_NOT_CONVERGED is returned, not raised."""
     info = ie_solve_info()
     o = opts or solve_opts()
+    n, _, _ = _dims(plan)
+    _need(v, nrhs * n, "v")
+    _need(c, nrhs * n, "c")
     st = lib().ie_solve(plan, _ptr(v), _ptr(c), nrhs, ctypes.byref(o), ctypes.byref(info), _stream(stream))
     _check(st, "ie_solve", allow=(IE_OK, IE_ERR_NOT_CONVERGED))
     return st, {f: getattr(info, f) for f, _ in info._fields_}
+
+
+_solver_sizes: dict = {}     # solver handle -> elements of its v and c
 
 
 def ie_solver_create(plan, nrhs, opts: ie_solve_opts | None = None) -> int:
     h = ctypes.c_void_p()
     o = opts or solve_opts()
     _check(lib().ie_solver_create(plan, nrhs, ctypes.byref(o), ctypes.byref(h)), "ie_solver_create")
+    _solver_sizes[h.value] = nrhs * _dims(plan)[0]
     return h.value
 
 
@@ -259,6 +329,8 @@ def ie_solver_footprint(plan, nrhs, opts: ie_solve_opts | None = None) -> int:
 
 
 def ie_solver_start(solver, v, c, stream=None):
+    _need(v, _solver_sizes.get(solver, 0), "v")
+    _need(c, _solver_sizes.get(solver, 0), "c")
     return _check(lib().ie_solver_start(solver, _ptr(v), _ptr(c), _stream(stream)), "ie_solver_start")
 
 
@@ -274,6 +346,7 @@ def ie_solver_poll(solver):
 
 
 def ie_solver_destroy(solver):
+    _solver_sizes.pop(solver, None)
     return _check(lib().ie_solver_destroy(solver), "ie_solver_destroy")
 
 

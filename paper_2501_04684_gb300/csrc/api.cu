@@ -86,17 +86,32 @@ ie_status validate(const ie_problem *pr) {
             int v = pr->box_ijk[3 * b + c];
             if (v < -(1 << 20) || v > (1 << 20)) return set_error("box index out of range"), IE_ERR_INVALID;
         }
+    if (pr->box_group) {
+        if (pr->n_groups < 1 || !pr->group_alpha)
+            return set_error("box_group needs n_groups >= 1 and group_alpha"), IE_ERR_INVALID;
+        for (int b = 0; b < pr->n_boxes; ++b) {
+            int g = pr->box_group[b];
+            if (g < 0 || g >= pr->n_groups) return set_error("box_group[%d] = %d out of range", b, g), IE_ERR_INVALID;
+            if (b > 0 && g < pr->box_group[b - 1]) return set_error("box_group must be non-decreasing"), IE_ERR_INVALID;
+        }
+    } else if (pr->n_groups > 1) {
+        return set_error("n_groups > 1 needs box_group"), IE_ERR_INVALID;
+    }
     return IE_OK;
 }
 
-// Dense lookup of the occupied boxes over their bounding box.
+int group_of(const ie_problem *pr, int b) { return pr->box_group ? pr->box_group[b] : 0; }
+int n_groups_of(const ie_problem *pr) { return pr->box_group ? pr->n_groups : 1; }
+
+// Dense lookup of the occupied boxes over their bounding box, one layer per scatterer.
 struct BoxGrid {
     int lo[3], ext[3];
+    size_t cells = 0;
     std::vector<int32_t> slot;
-    int at(int x, int y, int z) const {
+    int at(int g, int x, int y, int z) const {
         x -= lo[0], y -= lo[1], z -= lo[2];
         if (x < 0 || y < 0 || z < 0 || x >= ext[0] || y >= ext[1] || z >= ext[2]) return -1;
-        return slot[((size_t)x * ext[1] + y) * ext[2] + z];
+        return slot[(size_t)g * cells + ((size_t)x * ext[1] + y) * ext[2] + z];
     }
 };
 
@@ -110,12 +125,14 @@ ie_status build_grid(const ie_problem *pr, BoxGrid &g) {
         g.lo[c] = lo;
         g.ext[c] = hi - lo + 1;
     }
-    size_t cells = (size_t)g.ext[0] * g.ext[1] * g.ext[2];
-    if (cells > ((size_t)1 << 28)) return set_error("box bounding grid too large"), IE_ERR_INVALID;
-    g.slot.assign(cells, -1);
+    g.cells = (size_t)g.ext[0] * g.ext[1] * g.ext[2];
+    size_t ng = (size_t)n_groups_of(pr);
+    if (g.cells * ng > ((size_t)1 << 28)) return set_error("box bounding grid too large"), IE_ERR_INVALID;
+    g.slot.assign(g.cells * ng, -1);
     for (int b = 0; b < pr->n_boxes; ++b) {
         const int32_t *q = pr->box_ijk + 3 * b;
-        size_t i = ((size_t)(q[0] - g.lo[0]) * g.ext[1] + (q[1] - g.lo[1])) * g.ext[2] + (q[2] - g.lo[2]);
+        size_t i = (size_t)group_of(pr, b) * g.cells +
+                   ((size_t)(q[0] - g.lo[0]) * g.ext[1] + (q[1] - g.lo[1])) * g.ext[2] + (q[2] - g.lo[2]);
         if (g.slot[i] != -1) return set_error("duplicate box (%d,%d,%d)", q[0], q[1], q[2]), IE_ERR_INVALID;
         g.slot[i] = b;
     }
@@ -135,11 +152,16 @@ void far_groups(const ie_problem *pr, const BoxGrid &g, bool fill, FarGroups &ou
     std::vector<int64_t> count(nkeys + 1, 0);
     const int32_t *ijk = pr->box_ijk;
     int n = pr->n_boxes;
+    // box range of each scatterer (ids are non-decreasing)
+    std::vector<int> gend(n);
+    for (int b = n - 1; b >= 0; --b) gend[b] = (b + 1 < n && group_of(pr, b + 1) == group_of(pr, b)) ? gend[b + 1] : b + 1;
+    std::vector<int> gbeg(n);
+    for (int b = 0; b < n; ++b) gbeg[b] = (b > 0 && group_of(pr, b - 1) == group_of(pr, b)) ? gbeg[b - 1] : b;
     auto key = [&](int dx, int dy, int dz) {
         return ((size_t)(dx + g.ext[0] - 1) * span[1] + (dy + g.ext[1] - 1)) * span[2] + (dz + g.ext[2] - 1);
     };
     for (int b = 0; b < n; ++b)
-        for (int t = 0; t < n; ++t) {
+        for (int t = gbeg[b]; t < gend[b]; ++t) {
             int dx = ijk[3 * t] - ijk[3 * b], dy = ijk[3 * t + 1] - ijk[3 * b + 1], dz = ijk[3 * t + 2] - ijk[3 * b + 2];
             int ch = std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz)));
             if (ch >= 2) count[key(dx, dy, dz)]++;
@@ -173,7 +195,7 @@ void far_groups(const ie_problem *pr, const BoxGrid &g, bool fill, FarGroups &ou
     out.src.resize(npairs);
     out.dst.resize(npairs);
     for (int b = 0; b < n; ++b)
-        for (int t = 0; t < n; ++t) {
+        for (int t = gbeg[b]; t < gend[b]; ++t) {
             int dx = ijk[3 * t] - ijk[3 * b], dy = ijk[3 * t + 1] - ijk[3 * b + 1], dz = ijk[3 * t + 2] - ijk[3 * b + 2];
             int ch = std::max(std::abs(dx), std::max(std::abs(dy), std::abs(dz)));
             if (ch >= 2) {
@@ -200,7 +222,7 @@ void near_lists(const ie_problem *pr, const BoxGrid &g, const std::vector<int32_
             for (int ey = -1; ey <= 1; ++ey)
                 for (int ez = -1; ez <= 1; ++ez) {
                     if (pr->self_box_mode == 1 && ex == 0 && ey == 0 && ez == 0) continue;
-                    int b = g.at(q[0] - ex, q[1] - ey, q[2] - ez);
+                    int b = g.at(group_of(pr, a), q[0] - ex, q[1] - ey, q[2] - ez);
                     if (b < 0) continue;
                     src.push_back(b);
                     boff.push_back(elems);
@@ -221,7 +243,10 @@ size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, i
     add(nd * 3 * sizeof(int32_t));
     add(npairs * sizeof(int32_t));
     add(npairs * sizeof(int32_t));
-    add((size_t)nd * kNU * kNU * sizeof(float2));
+    if (pr->prec_mask & IE_PRECMASK(IE_PREC_FP32))
+        add((size_t)nd * kNU * kNU * sizeof(float2));
+    else   // staging of the 16-bit images, freed before the plan returns
+        add((size_t)std::min<int64_t>(nd, kCouplingChunk) * kNU * kNU * sizeof(float2));
     if (wants_bf16(pr->prec_mask)) add((size_t)nd * kTcDispElems * sizeof(uint16_t));
     if (wants_fp16(pr->prec_mask)) {
         add((size_t)nd * kTcDispElems * sizeof(uint16_t));
@@ -423,6 +448,15 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
         p->off[b + 1] = p->off[b] + p->nb[b];
     }
     p->n = p->off[p->nbox];
+    p->ngroups = n_groups_of(pr);
+    p->gbox.assign(p->ngroups + 1, 0);
+    p->galpha.assign(p->ngroups, pr->alpha);
+    for (int b = 0; b < p->nbox; ++b) p->gbox[group_of(pr, b) + 1] = b + 1;
+    for (int gi = 1; gi <= p->ngroups; ++gi) p->gbox[gi] = std::max(p->gbox[gi], p->gbox[gi - 1]);
+    p->goff.resize(p->ngroups + 1);
+    for (int gi = 0; gi <= p->ngroups; ++gi) p->goff[gi] = p->off[p->gbox[gi]];
+    if (pr->box_group)
+        for (int gi = 0; gi < p->ngroups; ++gi) p->galpha[gi] = pr->group_alpha[gi];
 
     FarGroups fg;
     far_groups(pr, g, true, fg, p->n_far_pairs, p->n_far_disp);
@@ -455,6 +489,18 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
     PC(cudaMemcpyAsync(p->d_nb, p->nb.data(), p->nbox * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     PC(cudaMemcpyAsync(p->d_off, p->off.data(), (p->nbox + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     PC(cudaMemcpyAsync(p->d_ijk, p->ijk.data(), 3 * p->nbox * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    {
+        std::vector<int32_t> bg(p->nbox);
+        std::vector<double> ab(p->nbox);
+        for (int b = 0; b < p->nbox; ++b) {
+            bg[b] = group_of(pr, b);
+            ab[b] = p->galpha[bg[b]];
+        }
+        PT(dalloc_t(p, &p->d_box_group, p->nbox));
+        PT(dalloc_t(p, &p->d_alpha_box, p->nbox));
+        PC(cudaMemcpy(p->d_box_group, bg.data(), p->nbox * sizeof(int32_t), cudaMemcpyHostToDevice));
+        PC(cudaMemcpy(p->d_alpha_box, ab.data(), p->nbox * sizeof(double), cudaMemcpyHostToDevice));
+    }
     if (!p->identity) {
         std::vector<float2> P32((size_t)p->n * kNU);
         for (size_t i = 0; i < P32.size(); ++i) P32[i] = make_float2((float)pr->P[2 * i], (float)pr->P[2 * i + 1]);
@@ -471,17 +517,35 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
         PC(cudaMemcpyAsync(p->d_disp, fg.disp.data(), fg.disp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         PC(cudaMemcpyAsync(p->d_src, fg.src.data(), fg.src.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         PC(cudaMemcpyAsync(p->d_dst, fg.dst.data(), fg.dst.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        PT(dalloc_t(p, &p->d_Csimt, (size_t)p->n_far_disp * kNU * kNU));
-        PT(launch_coupling_simt(p, p->d_disp, p->n_far_disp, p->d_Csimt, false, st));
-        if (wants_bf16(p->prec_mask)) {
-            PT(dalloc_t(p, &p->d_Cbf16, (size_t)p->n_far_disp * kTcDispElems));
-            PT(launch_coupling_tc(p, p->d_Cbf16, nullptr, false, st));
-        }
+        const int64_t nd = p->n_far_disp;
+        if (wants_bf16(p->prec_mask)) PT(dalloc_t(p, &p->d_Cbf16, (size_t)nd * kTcDispElems));
         if (wants_fp16(p->prec_mask)) {
-            PT(dalloc_t(p, &p->d_Cfp16, (size_t)p->n_far_disp * kTcDispElems));
-            PT(dalloc_t(p, &p->d_Cexp16, (size_t)p->n_far_disp));
-            PT(launch_coupling_tc(p, p->d_Cfp16, p->d_Cexp16, true, st));
+            PT(dalloc_t(p, &p->d_Cfp16, (size_t)nd * kTcDispElems));
+            PT(dalloc_t(p, &p->d_Cexp16, (size_t)nd));
         }
+        // FP32 blocks: the FP32 store itself, or (FP32 not requested) a bounded
+        // staging buffer from which the 16-bit images are cut chunk by chunk
+        const bool keep32 = (p->prec_mask & IE_PRECMASK(IE_PREC_FP32)) != 0;
+        const int64_t chunk = keep32 ? nd : std::min<int64_t>(nd, kCouplingChunk);
+        float2 *C32 = nullptr;
+        if (keep32) {
+            PT(dalloc_t(p, &p->d_Csimt, (size_t)nd * kNU * kNU));
+            C32 = p->d_Csimt;
+        } else {
+            PC(cudaMallocAsync(&C32, (size_t)chunk * kNU * kNU * sizeof(float2), st));
+        }
+        ie_status cst = IE_OK;
+        for (int64_t d0 = 0; d0 < nd && cst == IE_OK; d0 += chunk) {
+            const int64_t m = std::min(chunk, nd - d0);
+            float2 *blk = keep32 ? C32 + d0 * kNU * kNU : C32;
+            cst = launch_coupling_simt(p, p->d_disp + 3 * d0, m, blk, false, st);
+            if (cst == IE_OK && wants_bf16(p->prec_mask))
+                cst = launch_coupling_tc(blk, m, p->d_Cbf16 + d0 * kTcDispElems, nullptr, false, st);
+            if (cst == IE_OK && wants_fp16(p->prec_mask))
+                cst = launch_coupling_tc(blk, m, p->d_Cfp16 + d0 * kTcDispElems, p->d_Cexp16 + d0, true, st);
+        }
+        if (!keep32) cudaFreeAsync(C32, st);
+        PT(cst);
     }
 
     // near blocks
@@ -532,6 +596,8 @@ ie_status ie_plan_stats_get(ie_plan p, ie_plan_stats *o) {
     o->plan_seconds = p->plan_seconds;
     o->translate_ms = p->translate_ms;
     o->translate_launches = p->translate_launches;
+    o->n_groups = p->ngroups;
+    o->max_rhs = p->max_rhs;
     return IE_OK;
 }
 
@@ -614,13 +680,14 @@ ie_status ie_coupling_blocks(ie_plan p, const int32_t *d, int nd, void *outp, vo
 
 ie_status ie_rhs_plane_wave(ie_plan p, const double *khat, const double *pol, int nrhs, void *v, void *stream) {
     if (!p || !khat || !pol || !v) return set_error("null argument"), IE_ERR_INVALID;
-    if (nrhs < 1) return set_error("nrhs must be >= 1"), IE_ERR_INVALID;
+    if (nrhs < 1 || nrhs > p->max_rhs) return set_error("nrhs %d outside [1, %d]", nrhs, p->max_rhs), IE_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     double *dk = nullptr;
-    IE_CK(cudaMallocAsync(&dk, (size_t)nrhs * 6 * sizeof(double), st));
-    IE_CK(cudaMemcpyAsync(dk, khat, (size_t)nrhs * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
-    IE_CK(cudaMemcpyAsync(dk + 3 * nrhs, pol, (size_t)nrhs * 3 * sizeof(double), cudaMemcpyHostToDevice, st));
-    IE_TRY(launch_plane_wave(p, dk, dk + 3 * nrhs, nrhs, (float2 *)v, st));
+    size_t cnt = (size_t)p->ngroups * nrhs * 3;       // [group][rhs][3]
+    IE_CK(cudaMallocAsync(&dk, cnt * 2 * sizeof(double), st));
+    IE_CK(cudaMemcpyAsync(dk, khat, cnt * sizeof(double), cudaMemcpyHostToDevice, st));
+    IE_CK(cudaMemcpyAsync(dk + cnt, pol, cnt * sizeof(double), cudaMemcpyHostToDevice, st));
+    IE_TRY(launch_plane_wave(p, dk, dk + cnt, nrhs, (float2 *)v, st));
     IE_CK(cudaFreeAsync(dk, st));
     return IE_OK;
 }

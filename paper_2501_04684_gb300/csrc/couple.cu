@@ -241,12 +241,12 @@ ie_status launch_coupling_simt(const ie_plan p, const int32_t *d_disp, int64_t n
     return IE_OK;
 }
 
-ie_status launch_coupling_tc(const ie_plan p, uint16_t *out, int32_t *exps, bool fp16, cudaStream_t st) {
-    if (p->n_far_disp <= 0) return IE_OK;
+ie_status launch_coupling_tc(const float2 *Cs, int64_t nd, uint16_t *out, int32_t *exps, bool fp16, cudaStream_t st) {
+    if (nd <= 0) return IE_OK;
     if (fp16)
-        coupling_tc_kernel<true><<<(unsigned)p->n_far_disp, 256, 0, st>>>(p->d_Csimt, p->n_far_disp, out, exps);
+        coupling_tc_kernel<true><<<(unsigned)nd, 256, 0, st>>>(Cs, nd, out, exps);
     else
-        coupling_tc_kernel<false><<<(unsigned)p->n_far_disp, 256, 0, st>>>(p->d_Csimt, p->n_far_disp, out, exps);
+        coupling_tc_kernel<false><<<(unsigned)nd, 256, 0, st>>>(Cs, nd, out, exps);
     IE_CK_LAUNCH();
     return IE_OK;
 }

@@ -18,6 +18,7 @@ constexpr int kLattice = 4;
 constexpr int kSites = 64;          // 4^3 dipole sites per box
 constexpr int kNU = 192;            // 3 unknowns per site
 constexpr int kSlabs = 8;           // FP32 partial-sum slabs of the far field (see translate_simt.cu)
+constexpr int64_t kCouplingChunk = 4096;   // displacements per staging chunk of the 16-bit coupling images
 
 // Tensor-core store of one coupling block: 3 M-blocks (128 real-embedded rows) x
 // 6 K-chunks (32 source unknowns) x {hi, lo}, each a 128 x 32 16-bit image laid out
@@ -84,6 +85,12 @@ struct ie_plan_s {
     unsigned prec_mask = 0;
     bool identity = false;
     int64_t n = 0;                     // basis unknowns
+    // scatterers of a batched plan (one group otherwise): box and unknown ranges
+    int ngroups = 1;
+    std::vector<int64_t> gbox, goff;   // ngroups + 1 each
+    std::vector<double> galpha;        // ngroups
+    int32_t *d_box_group = nullptr;    // [nbox]
+    double *d_alpha_box = nullptr;     // [nbox] self term of each box's scatterer
     std::vector<int32_t> ijk, nb;
     std::vector<int64_t> off;          // nbox + 1
 
@@ -148,7 +155,8 @@ ie_status dalloc_t(ie_plan p, T **ptr, size_t count) {
 ie_status prepare_kernels();
 ie_status launch_coupling_simt(const ie_plan p, const int32_t *d_disp, int64_t nd, float2 *out, bool row_major,
                                cudaStream_t st);
-ie_status launch_coupling_tc(const ie_plan p, uint16_t *out, int32_t *exps, bool fp16, cudaStream_t st);
+// 16-bit split images (and, fp16, the per-block exponents) of nd FP32 blocks [k][m].
+ie_status launch_coupling_tc(const float2 *Cs, int64_t nd, uint16_t *out, int32_t *exps, bool fp16, cudaStream_t st);
 ie_status launch_near_blocks(ie_plan p, cudaStream_t st);
 ie_status launch_aggregate(const ie_plan p, const float2 *c, float2 *X, int nrhs, cudaStream_t st,
                            const int *gate = nullptr);

@@ -191,20 +191,22 @@ __global__ void plane_wave_kernel(double k, double a, int G, const int32_t *__re
                                   const float2 *__restrict__ P, const int32_t *__restrict__ nb,
                                   const int64_t *__restrict__ off, int64_t n,
                                   const double *__restrict__ khat, const double *__restrict__ pol,
+                                  const int32_t *__restrict__ box_group, int nrhs,
                                   float2 *__restrict__ v, int identity) {
     __shared__ float2 es[kNU];
     int b = blockIdx.x, r = blockIdx.y;
+    const int w = box_group[b] * nrhs + r;        // incidence of this scatterer's column r
     double h = a / kLattice;
     for (int s = threadIdx.x; s < kSites; s += blockDim.x) {
         int ii[3] = {s & 3, (s >> 2) & 3, s >> 4};
         double ph = 0;
         for (int c = 0; c < 3; ++c) {
             double pos = a * ((double)ijk[3 * b + c] + 0.5 - 0.5 * G) + h * (ii[c] + 0.5) - 0.5 * a;
-            ph += khat[3 * r + c] * pos;
+            ph += khat[3 * w + c] * pos;
         }
         double sn, cs;
         sincos(-k * ph, &sn, &cs);
-        for (int c = 0; c < 3; ++c) es[3 * s + c] = make_float2((float)(pol[3 * r + c] * cs), (float)(pol[3 * r + c] * sn));
+        for (int c = 0; c < 3; ++c) es[3 * s + c] = make_float2((float)(pol[3 * w + c] * cs), (float)(pol[3 * w + c] * sn));
     }
     __syncthreads();
     float2 *vb = v + (int64_t)r * n + off[b];
@@ -288,7 +290,8 @@ ie_status launch_sum_slabs(const ie_plan p, const float2 *Yslab, int nslab, size
 ie_status launch_plane_wave(const ie_plan p, const double *d_khat, const double *d_pol, int nrhs, float2 *v,
                             cudaStream_t st) {
     plane_wave_kernel<<<dim3(p->nbox, nrhs), 256, 0, st>>>(p->k, p->a, p->G, p->d_ijk, p->d_P, p->d_nb, p->d_off,
-                                                           p->n, d_khat, d_pol, v, p->identity ? 1 : 0);
+                                                           p->n, d_khat, d_pol, p->d_box_group, nrhs, v,
+                                                           p->identity ? 1 : 0);
     IE_CK_LAUNCH();
     return IE_OK;
 }

@@ -1,5 +1,5 @@
 // K5: near-zone product with the stored blocks plus the self term (eq. 2):
-//   y_a = alpha c_a + sum over stored pairs (a, b) of N_ab c_b,
+//   y_a = alpha_a c_a + sum over stored pairs (a, b) of N_ab c_b   (alpha of a's scatterer),
 // N_ab = P_a G_{a-b} P_b^T for boxes within Chebyshev distance 1 (the self block
 // without coincident dipoles).  Blocks are nb_a x nb_b column-major, so the threads
 // of a CTA (one per test row i) read a column contiguously.  HBM-bound on the blocks.
@@ -10,12 +10,14 @@ namespace {
 
 __global__ void near_kernel(const int32_t *__restrict__ nb, const int64_t *__restrict__ off, int64_t n,
                             const int32_t *__restrict__ start, const int32_t *__restrict__ src,
-                            const int64_t *__restrict__ boff, const float2 *__restrict__ Nblk, double alpha,
+                            const int64_t *__restrict__ boff, const float2 *__restrict__ Nblk,
+                            const double *__restrict__ alpha_box,
                             const float2 *__restrict__ c, float2 *__restrict__ y, const int *__restrict__ gate) {
     if (gate && *gate == 0) return;
     __shared__ float2 cs[kNU];
     int a = blockIdx.x, r = blockIdx.y;
     int na = nb[a];
+    const double alpha = alpha_box[a];
     const float2 *cr = c + (int64_t)r * n;
     // threads own rows i = threadIdx.x + k*blockDim.x (at most 2 per thread for 192 rows)
     double accr[2] = {0, 0}, acci[2] = {0, 0};
@@ -59,7 +61,7 @@ ie_status launch_near(const ie_plan p, const float2 *c, float2 *y, int nrhs, cud
     int threads = maxnb <= 32 ? 32 : (maxnb <= 64 ? 64 : (maxnb <= 128 ? 128 : 96));
     if (maxnb > 128) threads = 96;   // 2 rows per thread up to 192
     near_kernel<<<dim3(p->nbox, nrhs), threads, 0, st>>>(p->d_nb, p->d_off, p->n, p->d_near_start, p->d_near_src,
-                                                         p->d_near_boff, p->d_Nblk, p->alpha, c, y, gate);
+                                                         p->d_near_boff, p->d_Nblk, p->d_alpha_box, c, y, gate);
     IE_CK_LAUNCH();
     return IE_OK;
 }

@@ -232,6 +232,9 @@ extern "C" ie_status ie_translate_noalloc(ie_plan p, const void *X, void *Y, int
     if (!p || !X || !Y) return set_error("null argument"), IE_ERR_INVALID;
     if (nrhs < 1 || nrhs > p->max_rhs || nrhs > kTileN)
         return set_error("nrhs %d outside [1, %d]", nrhs, p->max_rhs < kTileN ? p->max_rhs : kTileN), IE_ERR_INVALID;
+    if (!(p->prec_mask & IE_PRECMASK(IE_PREC_FP32)))
+        return set_error("ie_translate_noalloc runs the FP32 translation; the plan holds no FP32 store"),
+               IE_ERR_UNSUPPORTED;
     size_t off_bytes = ((size_t)(p->n_far_disp + 1) * sizeof(int64_t) + 255) / 256 * 256;
     size_t stride = (size_t)nrhs * p->nbox * kNU;                 // float2 per slab
     size_t need = off_bytes + (size_t)kSlabs * stride * sizeof(float2);

@@ -70,6 +70,9 @@ def test_footprint_is_host_only_and_counts_pairs(built):
     dict(nb=np.full(64, 193, dtype=np.int32)),
     dict(box_ijk=np.zeros((64, 3), dtype=np.int32)),          # duplicates
     dict(nb=None),                                           # P given without nb
+    dict(box_group=np.r_[np.ones(32), np.zeros(32)], group_alpha=[1.0, 1.0]),   # ids decreasing
+    dict(box_group=np.full(64, 2), group_alpha=[1.0, 1.0]),                     # id out of range
+    dict(box_group=np.zeros(64)),                                               # no self terms
 ])
 def test_validation_rejects(built, bad):
     pr = _tiny_problem(**bad)
@@ -79,3 +82,17 @@ def test_validation_rejects(built, bad):
     h = ctypes.c_void_p()
     assert ie.lib().ie_plan_create(ctypes.byref(pr), None, ctypes.byref(h)) == ie.IE_ERR_INVALID
     assert h.value is None
+
+
+def test_batch_of_two_copies_is_valid(built):
+    """Two scatterers may occupy the same cells; duplicates inside one stay invalid."""
+    p = W.tiny()
+    two = dict(box_ijk=np.concatenate([p.box_ijk, p.box_ijk]), nb=np.concatenate([p.nb, p.nb]),
+               P=np.concatenate([p.P, p.P]), box_group=np.repeat([0, 1], 64), group_alpha=[1.0, 2.0])
+    b1 = ie.ie_plan_footprint(_tiny_problem())
+    b2 = ie.ie_plan_footprint(_tiny_problem(**two))
+    assert b2 > b1
+    bad = dict(two, box_group=np.zeros(128))
+    bad["group_alpha"] = [1.0]
+    with pytest.raises(ie.IEError):
+        ie.ie_plan_footprint(_tiny_problem(**bad))

@@ -131,3 +131,29 @@ def test_mixed_solve_shell16_true_residual():
     Zx = oracle.operator(p, xs, "full", targets=targets)
     res = np.linalg.norm(Zx - vref[:, rows]) / np.linalg.norm(vref[:, rows])
     assert res <= 1e-5, res
+
+
+def test_tc_plan_without_fp32_store():
+    """A plan of 16-bit precisions only cuts its images from a staging buffer in
+    chunks (shell16: 16,540 displacements, several chunks) and keeps no FP32 store."""
+    p = W.shell16()
+    c = W.coefficients(p, 1, W.SEED_C["shell16"])
+    targets = W.subsample_boxes(p, 12, W.SEED_SUBSAMPLE["shell16"])
+    ref = oracle.far_matvec(p, c, targets=targets)
+    rows = oracle.basis_rows(p, targets)
+    mask16 = ie.precmask(ie.IE_PREC_BF16X3, ie.IE_PREC_FP16X3)
+    mask_all = ie.precmask(ie.IE_PREC_FP32, ie.IE_PREC_BF16X3, ie.IE_PREC_FP16X3)
+    assert ie.ie_plan_footprint(ie.problem_from(p, mask16)) < ie.ie_plan_footprint(ie.problem_from(p, mask_all))
+    with plan_for(p, precs=[ie.IE_PREC_BF16X3, ie.IE_PREC_FP16X3]) as plan:
+        for prec in (ie.IE_PREC_BF16X3, ie.IE_PREC_FP16X3):
+            y = empty((1, p.n))
+            ie.ie_matvec(plan.handle, ie.IE_FAR, prec, dev(c), y, 1)
+            assert rel_l2(host(y)[:, rows], ref) <= BOUND[prec], _name(prec)
+        y = empty((1, p.n))
+        with pytest.raises(ie.IEError) as e:
+            ie.ie_matvec(plan.handle, ie.IE_FAR, ie.IE_PREC_FP32, dev(c), y, 1)
+        assert e.value.status == ie.IE_ERR_UNSUPPORTED
+        X = empty((1, p.n_boxes * 192))
+        with pytest.raises(ie.IEError) as e:
+            ie.ie_translate_noalloc(plan.handle, X, empty((1, p.n_boxes * 192)), 1)
+        assert e.value.status == ie.IE_ERR_UNSUPPORTED

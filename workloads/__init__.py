@@ -281,3 +281,104 @@ def serve_requests(count: int = 256, seed: int = 51, rate_hz: float = 10.0,
                         nb=np.full(boxes.shape[0], nb, dtype=np.int32),
                         seed_P=int(seed * 1000 + i), nrhs=nrhs, khat=khat, pol=pol))
     return out
+
+
+# ---------------------------------------------------------------- batches of scatterers
+@dataclass
+class Batch:
+    """Independent scatterers on one grid.  Each member is a Problem (what the oracle
+    sees, one at a time); their concatenation in member order (boxes, basis unknowns)
+    is what one batched plan takes.  Member g has nrhs[g] plane waves khat[g], pol[g]."""
+    name: str
+    G: int
+    members: list
+    nrhs: list
+    khat: list
+    pol: list
+
+    @property
+    def n_groups(self) -> int:
+        return len(self.members)
+
+    @property
+    def box_ijk(self) -> np.ndarray:
+        return np.concatenate([m.box_ijk for m in self.members]).astype(np.int32)
+
+    @property
+    def nb(self) -> np.ndarray:
+        return np.concatenate([m.nb for m in self.members]).astype(np.int32)
+
+    @property
+    def P(self) -> np.ndarray:
+        return np.concatenate([m.P for m in self.members])
+
+    @property
+    def box_group(self) -> np.ndarray:
+        return np.concatenate([np.full(m.n_boxes, g, dtype=np.int32) for g, m in enumerate(self.members)])
+
+    @property
+    def group_alpha(self) -> np.ndarray:
+        return np.array([m.alpha for m in self.members], dtype=np.float64)
+
+    @property
+    def unknown_offsets(self) -> np.ndarray:
+        o = np.zeros(self.n_groups + 1, dtype=np.int64)
+        np.cumsum([m.n for m in self.members], out=o[1:])
+        return o
+
+    @property
+    def n(self) -> int:
+        return int(self.unknown_offsets[-1])
+
+    @property
+    def max_rhs(self) -> int:
+        return max(self.nrhs)
+
+    def padded_waves(self, R: int | None = None):
+        """(khat, pol) as (n_groups, R, 3); columns beyond a member's own waves get a
+        zero polarisation (a zero right-hand side)."""
+        R = self.max_rhs if R is None else R
+        kh = np.zeros((self.n_groups, R, 3))
+        kh[:, :, 2] = 1.0
+        po = np.zeros((self.n_groups, R, 3))
+        for g in range(self.n_groups):
+            q = self.nrhs[g]
+            kh[g, :q] = self.khat[g]
+            po[g, :q] = self.pol[g]
+        return kh, po
+
+    def split(self, packed: np.ndarray) -> list:
+        """Member slices of a packed [rhs][n] array."""
+        o = self.unknown_offsets
+        return [packed[..., o[g]:o[g + 1]] for g in range(self.n_groups)]
+
+
+def batch_alpha(nb: np.ndarray) -> float:
+    """Self term of a batched scatterer: the shell16 value rescaled by the square of
+    the usual random-matrix estimate sqrt(nb) + sqrt(192) of ||P_b||_2 at the
+    member's largest nb (the members are too large for the oracle's power iteration)."""
+    ref = alpha_for("shell16")
+    s = (math.sqrt(float(np.max(nb))) + math.sqrt(NU)) / (math.sqrt(32.0) + math.sqrt(NU))
+    return float(ref * s * s)
+
+
+def as_batch(items: list, name: str) -> Batch:
+    """Batch from the dicts of batch_scatterers()."""
+    members = []
+    for i, it in enumerate(items):
+        nb = np.asarray(it["nb"], dtype=np.int32)
+        members.append(Problem(name=f"{name}[{i}]", G=it["G"], box_ijk=np.asarray(it["box_ijk"], dtype=np.int32),
+                               nb=nb, P=it["P"], alpha=batch_alpha(nb)))
+    return Batch(name=name, G=items[0]["G"], members=members, nrhs=[it["nrhs"] for it in items],
+                 khat=[it["khat"] for it in items], pol=[it["pol"] for it in items])
+
+
+def batch64() -> Batch:
+    """64 scatterers on a 32^3 grid: sphere, cube and ellipsoid shells of radius 3..14,
+    nb 16..64 per box, 1..8 plane waves each (seed 41)."""
+    return as_batch(batch_scatterers(), "batch64")
+
+
+def small_batch(count: int = 4, seed: int = 45) -> Batch:
+    """A few small scatterers on an 8^3 grid (radius 1..2, nb 16..64, 1..3 waves)."""
+    return as_batch(batch_scatterers(count=count, G=8, seed=seed, rmin=1, rmax=2, rhs_max=3), "small_batch")
