@@ -58,8 +58,10 @@ typedef enum {
  *  BF16X3  tcgen05 tensor cores, each FP32 operand split into bf16 hi + lo and the
  *          three products hi*hi + hi*lo + lo*hi accumulated in FP32.
  *  FP16X3  as BF16X3 with fp16 halves.
- *  BF16X1  tcgen05, one bf16 product (hi*hi) — the cheapest, least accurate form. */
-typedef enum { IE_PREC_FP32 = 1, IE_PREC_BF16X3 = 2, IE_PREC_FP16X3 = 3, IE_PREC_BF16X1 = 4 } ie_prec;
+ *  BF16X1  tcgen05, one bf16 product (hi*hi) — the cheapest, least accurate form.
+ *  FP16X1  tcgen05, one fp16 product (hi*hi) from the FP16X3 store: three more bits
+ *          than BF16X1; with FP16X3 it makes a mixed pair that shares one store. */
+typedef enum { IE_PREC_FP32 = 1, IE_PREC_BF16X3 = 2, IE_PREC_FP16X3 = 3, IE_PREC_BF16X1 = 4, IE_PREC_FP16X1 = 5 } ie_prec;
 #define IE_PRECMASK(p) (1u << (unsigned)(p))
 
 /* Which part of Z a product applies. */

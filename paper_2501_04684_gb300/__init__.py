@@ -19,9 +19,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libie.so")
 
 IE_OK, IE_ERR_INVALID, IE_ERR_OOM, IE_ERR_CUDA, IE_ERR_NOT_CONVERGED, IE_ERR_TIMEOUT, IE_ERR_UNSUPPORTED = range(7)
-IE_PREC_FP32, IE_PREC_BF16X3, IE_PREC_FP16X3, IE_PREC_BF16X1 = 1, 2, 3, 4
+IE_PREC_FP32, IE_PREC_BF16X3, IE_PREC_FP16X3, IE_PREC_BF16X1, IE_PREC_FP16X1 = 1, 2, 3, 4, 5
 IE_FAR, IE_NEAR, IE_FULL = 1, 2, 3
-PREC_NAMES = {IE_PREC_FP32: "fp32", IE_PREC_BF16X3: "bf16x3", IE_PREC_FP16X3: "fp16x3", IE_PREC_BF16X1: "bf16x1"}
+PREC_NAMES = {IE_PREC_FP32: "fp32", IE_PREC_BF16X3: "bf16x3", IE_PREC_FP16X3: "fp16x3", IE_PREC_BF16X1: "bf16x1",
+              IE_PREC_FP16X1: "fp16x1"}
 NU = 192                      # dipole unknowns per box (4^3 lattice x 3 orientations)
 
 EXPORTED = [

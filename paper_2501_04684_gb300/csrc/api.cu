@@ -56,12 +56,13 @@ ie_status prepare_kernels() {
 namespace {
 
 bool wants_tc(unsigned mask) {
-    return mask & (IE_PRECMASK(IE_PREC_BF16X3) | IE_PRECMASK(IE_PREC_FP16X3) | IE_PRECMASK(IE_PREC_BF16X1));
+    return mask & (IE_PRECMASK(IE_PREC_BF16X3) | IE_PRECMASK(IE_PREC_FP16X3) | IE_PRECMASK(IE_PREC_BF16X1) |
+                   IE_PRECMASK(IE_PREC_FP16X1));
 }
 bool wants_bf16(unsigned mask) {
     return mask & (IE_PRECMASK(IE_PREC_BF16X3) | IE_PRECMASK(IE_PREC_BF16X1));
 }
-bool wants_fp16(unsigned mask) { return mask & IE_PRECMASK(IE_PREC_FP16X3); }
+bool wants_fp16(unsigned mask) { return mask & (IE_PRECMASK(IE_PREC_FP16X3) | IE_PRECMASK(IE_PREC_FP16X1)); }
 
 ie_status validate(const ie_problem *pr) {
     if (!pr) return set_error("null problem"), IE_ERR_INVALID;
@@ -74,7 +75,7 @@ ie_status validate(const ie_problem *pr) {
     if (!(pr->k > 0) || !(pr->box_edge > 0) || !(pr->eta > 0))
         return set_error("k, eta and box_edge must be positive"), IE_ERR_INVALID;
     unsigned known = IE_PRECMASK(IE_PREC_FP32) | IE_PRECMASK(IE_PREC_BF16X3) | IE_PRECMASK(IE_PREC_FP16X3) |
-                     IE_PRECMASK(IE_PREC_BF16X1);
+                     IE_PRECMASK(IE_PREC_BF16X1) | IE_PRECMASK(IE_PREC_FP16X1);
     if (pr->prec_mask == 0 || (pr->prec_mask & ~known)) return set_error("bad prec_mask"), IE_ERR_INVALID;
     if (pr->self_box_mode != 0 && pr->self_box_mode != 1) return set_error("self_box_mode must be 0 or 1"), IE_ERR_INVALID;
     if (pr->nb)
@@ -346,7 +347,7 @@ ie_status far_product(ie_plan p, int prec, const float2 *c, float2 *y, int nrhs,
     IE_TRY(launch_aggregate(p, c, p->d_X, nrhs, st, gate));
     for (int s = 0; s < kSlabs; ++s)
         IE_TRY(launch_zero(p->d_Yslab + s * stride, (size_t)nrhs * p->nbox * kNU * sizeof(float2), st, gate));
-    if (prec != IE_PREC_FP32) IE_TRY(launch_split_tc(p, p->d_X, nrhs, prec == IE_PREC_FP16X3, st, gate));
+    if (prec != IE_PREC_FP32) IE_TRY(launch_split_tc(p, p->d_X, nrhs, is_fp16(prec), st, gate));
     IE_TRY(translate_timed(p, prec, p->d_X, p->d_Yslab, nrhs, st, gate));
     IE_TRY(launch_disaggregate(p, p->d_Yslab, kSlabs, stride, y, nrhs, accumulate, st, gate));
     return IE_OK;
@@ -365,7 +366,7 @@ ie_status apply(ie_plan p, int which, int prec, const float2 *c, float2 *y, int 
 using namespace ie;
 
 static ie_status check_prec(ie_plan p, int prec) {
-    if (prec < IE_PREC_FP32 || prec > IE_PREC_BF16X1) return set_error("unknown precision %d", prec), IE_ERR_INVALID;
+    if (prec < IE_PREC_FP32 || prec > IE_PREC_FP16X1) return set_error("unknown precision %d", prec), IE_ERR_INVALID;
     if (!(p->prec_mask & IE_PRECMASK(prec)))
         return set_error("precision %d not prepared by this plan", prec), IE_ERR_UNSUPPORTED;
     return IE_OK;
@@ -649,7 +650,7 @@ ie_status ie_translate(ie_plan p, int prec, const void *X, void *Y, int nrhs, vo
     size_t stride = slab_stride(p);
     for (int s = 0; s < kSlabs; ++s)
         IE_TRY(launch_zero(p->d_Yslab + s * stride, (size_t)nrhs * p->nbox * kNU * sizeof(float2), st));
-    if (prec != IE_PREC_FP32) IE_TRY(launch_split_tc(p, (const float2 *)X, nrhs, prec == IE_PREC_FP16X3, st));
+    if (prec != IE_PREC_FP32) IE_TRY(launch_split_tc(p, (const float2 *)X, nrhs, is_fp16(prec), st));
     IE_TRY(translate_timed(p, prec, (const float2 *)X, p->d_Yslab, nrhs, st, nullptr));
     return launch_sum_slabs(p, p->d_Yslab, kSlabs, stride, (float2 *)Y, nrhs, st);
 }

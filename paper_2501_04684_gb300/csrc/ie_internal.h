@@ -18,6 +18,8 @@ constexpr int kLattice = 4;
 constexpr int kSites = 64;          // 4^3 dipole sites per box
 constexpr int kNU = 192;            // 3 unknowns per site
 constexpr int kSlabs = 8;           // FP32 partial-sum slabs of the far field (see translate_simt.cu)
+// Precisions whose products use the fp16 split store (per-block power-of-two scaling).
+inline bool is_fp16(int prec) { return prec == IE_PREC_FP16X3 || prec == IE_PREC_FP16X1; }
 constexpr int64_t kCouplingChunk = 4096;   // displacements per staging chunk of the 16-bit coupling images
 
 // Tensor-core store of one coupling block: 3 M-blocks (128 real-embedded rows) x

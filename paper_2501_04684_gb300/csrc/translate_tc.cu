@@ -424,11 +424,12 @@ ie_status prepare_translate_tc() {
     IE_TRY((set_attr<false, true>()));
     IE_TRY((set_attr<true, true>()));
     IE_TRY((set_attr<false, false>()));
+    IE_TRY((set_attr<true, false>()));
     return IE_OK;
 }
 
 ie_status launch_translate_tc(ie_plan p, int prec, float2 *Yslab, int nrhs, cudaStream_t st, const int *gate) {
-    const bool fp16 = prec == IE_PREC_FP16X3;
+    const bool fp16 = is_fp16(prec);
     const uint16_t *C = fp16 ? p->d_Cfp16 : p->d_Cbf16;
     if (!C) return set_error("tensor-core coupling store for precision %d not built", prec), IE_ERR_UNSUPPORTED;
     WorkList *wl = nullptr;
@@ -457,6 +458,8 @@ ie_status launch_translate_tc(ie_plan p, int prec, float2 *Yslab, int nrhs, cuda
         translate_tc_kernel<true, true><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
     else if (prec == IE_PREC_BF16X1)
         translate_tc_kernel<false, false><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
+    else if (prec == IE_PREC_FP16X1)
+        translate_tc_kernel<true, false><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
     else
         return set_error("not a tensor-core precision: %d", prec), IE_ERR_INVALID;
     IE_CK_LAUNCH();

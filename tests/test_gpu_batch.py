@@ -11,7 +11,8 @@ from gpu_util import dev, empty, host, rel_l2
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-6
-BOUND = {ie.IE_PREC_FP32: TOL, ie.IE_PREC_BF16X3: 5e-5, ie.IE_PREC_FP16X3: 2e-6, ie.IE_PREC_BF16X1: 1e-2}
+BOUND = {ie.IE_PREC_FP32: TOL, ie.IE_PREC_BF16X3: 5e-5, ie.IE_PREC_FP16X3: 2e-6, ie.IE_PREC_BF16X1: 1e-2,
+         ie.IE_PREC_FP16X1: 2e-3}
 ALL = list(BOUND)
 
 

@@ -4,7 +4,7 @@ FP64 oracle, through the C ABI.
 Stated bounds (relative L2), from the split arithmetic: bf16 hi + lo keeps ~16
 significant bits and the dropped lo*lo term is ~2^-16 of each product, so BF16X3
 <= 5e-5; fp16 hi + lo keeps ~22 bits, FP16X3 <= 2e-6; one bf16 product (8 bits)
-BF16X1 <= 1e-2.  The mixed solve (inner GMRES on BF16X3 products, FP64 refinement
+BF16X1 <= 1e-2; one fp16 product (11 bits, 2^3 finer) FP16X1 <= 2e-3.  The mixed solve (inner GMRES on BF16X3 products, FP64 refinement
 residual from FP32 products) must reach a true residual <= 1e-5.
 """
 import numpy as np
@@ -17,8 +17,8 @@ from gpu_util import dev, empty, host, plan_for, rel_l2
 from test_gpu_parity import ragged_problem
 
 pytestmark = pytest.mark.gpu
-BOUND = {ie.IE_PREC_BF16X3: 5e-5, ie.IE_PREC_FP16X3: 2e-6, ie.IE_PREC_BF16X1: 1e-2}
-TC = [ie.IE_PREC_BF16X3, ie.IE_PREC_FP16X3, ie.IE_PREC_BF16X1]
+BOUND = {ie.IE_PREC_BF16X3: 5e-5, ie.IE_PREC_FP16X3: 2e-6, ie.IE_PREC_BF16X1: 1e-2, ie.IE_PREC_FP16X1: 2e-3}
+TC = [ie.IE_PREC_BF16X3, ie.IE_PREC_FP16X3, ie.IE_PREC_BF16X1, ie.IE_PREC_FP16X1]
 ALL = [ie.IE_PREC_FP32] + TC
 
 
@@ -95,7 +95,7 @@ def test_tc_full_size_shell16_sampled(prec):
     assert rel_l2(got, ref) <= BOUND[prec]
 
 
-@pytest.mark.parametrize("inner", [ie.IE_PREC_BF16X3, ie.IE_PREC_BF16X1], ids=_name)
+@pytest.mark.parametrize("inner", [ie.IE_PREC_BF16X3, ie.IE_PREC_BF16X1, ie.IE_PREC_FP16X1], ids=_name)
 def test_mixed_solve_with_refinement_tiny(inner, tiny):
     Z = oracle.dense_operator(tiny)
     kh, pol = W.plane_wave_spec(2, seed=404)
@@ -104,7 +104,7 @@ def test_mixed_solve_with_refinement_tiny(inner, tiny):
         x = empty((2, tiny.n))
         st, info = ie.ie_solve(plan.handle, dev(v), x, 2,
                                ie.solve_opts(tol=1e-5, prec=inner, refine=1, refine_prec=ie.IE_PREC_FP32,
-                                             inner_tol=1e-3 if inner == ie.IE_PREC_BF16X3 else 1e-2))
+                                             inner_tol=1e-2 if inner == ie.IE_PREC_BF16X1 else 1e-3))
         assert st == ie.IE_OK, info
         xs = host(x)
     for r in range(2):
@@ -157,3 +157,46 @@ def test_tc_plan_without_fp32_store():
         with pytest.raises(ie.IEError) as e:
             ie.ie_translate_noalloc(plan.handle, X, empty((1, p.n_boxes * 192)), 1)
         assert e.value.status == ie.IE_ERR_UNSUPPORTED
+
+
+def test_mixed_solve_one_fp16_store_shell16():
+    """Inner GMRES on FP16X1 products, refinement residual from FP16X3: one store."""
+    p = W.shell16()
+    p.alpha = W.alpha_for("shell16")
+    kh, pol = W.plane_wave_spec(1)
+    targets = W.subsample_boxes(p, 12, W.SEED_SUBSAMPLE["shell16"])
+    with plan_for(p, precs=[ie.IE_PREC_FP16X1, ie.IE_PREC_FP16X3]) as plan:
+        v = empty((1, p.n))
+        ie.ie_rhs_plane_wave(plan.handle, kh, pol, v)
+        x = empty((1, p.n))
+        st, info = ie.ie_solve(plan.handle, v, x, 1,
+                               ie.solve_opts(tol=1e-5, prec=ie.IE_PREC_FP16X1, refine=1,
+                                             refine_prec=ie.IE_PREC_FP16X3, inner_tol=1e-3))
+        assert st == ie.IE_OK, info
+        xs = host(x)
+    vref = oracle.plane_wave_rhs(p, kh, pol)
+    rows = oracle.basis_rows(p, targets)
+    Zx = oracle.operator(p, xs, "full", targets=targets)
+    res = np.linalg.norm(Zx - vref[:, rows]) / np.linalg.norm(vref[:, rows])
+    assert res <= 1e-5, res
+
+
+def test_fp16x3_solve_shell16_true_residual():
+    """GMRES(50) directly on FP16X3 products to 1e-5, no refinement: the true residual
+    against the FP64 operator stays within 1e-5."""
+    p = W.shell16()
+    p.alpha = W.alpha_for("shell16")
+    kh, pol = W.plane_wave_spec(1)
+    targets = W.subsample_boxes(p, 12, W.SEED_SUBSAMPLE["shell16"])
+    with plan_for(p, precs=[ie.IE_PREC_FP16X3]) as plan:
+        v = empty((1, p.n))
+        ie.ie_rhs_plane_wave(plan.handle, kh, pol, v)
+        x = empty((1, p.n))
+        st, info = ie.ie_solve(plan.handle, v, x, 1, ie.solve_opts(tol=1e-5, prec=ie.IE_PREC_FP16X3))
+        assert st == ie.IE_OK, info
+        xs = host(x)
+    vref = oracle.plane_wave_rhs(p, kh, pol)
+    rows = oracle.basis_rows(p, targets)
+    Zx = oracle.operator(p, xs, "full", targets=targets)
+    res = np.linalg.norm(Zx - vref[:, rows]) / np.linalg.norm(vref[:, rows])
+    assert res <= 1e-5, res
