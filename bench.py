@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--workload", default="shell16", choices=["shell16", "shell32", "batch64", "serve"],
                     help="shell16 is the headline line; the others measure the precision, batching and "
                          "serving workloads")
+    ap.add_argument("--symmetry", type=int, default=0, choices=[0, 1],
+                    help="1: symmetry-compressed coupling store (one block per sorted |d|)")
     ap.add_argument("--requests", type=int, default=24, help="serve: requests per run")
     ap.add_argument("--serve-load", type=float, nargs="+", default=[0.7], help="serve: loads x capacity")
     ap.add_argument("--serve-batch", type=int, default=4, help="serve: most requests merged into one plan")
@@ -297,7 +299,7 @@ def run_shell16(ctx):
     p.alpha = W.alpha_for("shell16")
     precs = [ie.IE_PREC_FP32, ie.IE_PREC_BF16X3, ie.IE_PREC_FP16X3, ie.IE_PREC_BF16X1, ie.IE_PREC_FP16X1]
     t0 = time.perf_counter()
-    plan = ie.Plan(ie.problem_from(p, ie.precmask(*precs)), stream)
+    plan = ie.Plan(ie.problem_from(p, ie.precmask(*precs), symmetry=args.symmetry), stream)
     plan_s = time.perf_counter() - t0
     st = plan.stats
     kh, pol = W.plane_wave_spec(1)
@@ -351,7 +353,10 @@ def run_shell16(ctx):
         "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": hp["dtype"], "data": "synthetic",
         "config": {"workload": WORKLOAD, "path": HEADLINE, "path_desc": hp["desc"], "tol": hp["opts"].tol,
-                   "nrhs": 1, "l2": "no flush needed: each product streams >= 4.9 GB of coupling blocks (> 129 MB L2)",
+                   "nrhs": 1, "symmetry": args.symmetry,
+                   "l2": ("no flush needed: each product streams >= 4.9 GB of coupling blocks (> 129 MB L2)"
+                          if not args.symmetry else
+                          "symmetry-compressed store (473 blocks, 139 MB); inputs and slabs are rewritten each product"),
                    "parallelism": "replicas" if world > 1 else "single"},
         "solve": {k: head[k] for k in ("p50_ms", "p99_ms", "iterations", "matvecs", "refinements", "relres")},
         "vs_plain_fp32": head["solves_per_s"] / others["plain"]["solves_per_s"],
@@ -380,7 +385,7 @@ def run_shell32(ctx):
     p.alpha = W.alpha_for("shell32")
     precs = [ie.IE_PREC_FP32, ie.IE_PREC_BF16X3, ie.IE_PREC_FP16X3, ie.IE_PREC_FP16X1]
     t0 = time.perf_counter()
-    plan = ie.Plan(ie.problem_from(p, ie.precmask(*precs)), ctx.stream)
+    plan = ie.Plan(ie.problem_from(p, ie.precmask(*precs), symmetry=args.symmetry), ctx.stream)
     plan_s = time.perf_counter() - t0
     st = plan.stats
     kh, pol = W.plane_wave_spec(1)
@@ -431,7 +436,7 @@ def run_batch64(ctx):
     pair_rhs = sum(m.n_boxes ** 2 * q for m, q in zip(b.members, b.nrhs))   # upper bound (near pairs included)
     precs = [ie.IE_PREC_FP16X1, ie.IE_PREC_FP16X3]
     t0 = time.perf_counter()
-    plan = ie.Plan(ie.problem_from_batch(b, ie.precmask(*precs)), ctx.stream)
+    plan = ie.Plan(ie.problem_from_batch(b, ie.precmask(*precs), symmetry=args.symmetry), ctx.stream)
     plan_s = time.perf_counter() - t0
     st = plan.stats
     kh, pol = b.padded_waves()
@@ -449,7 +454,7 @@ def run_batch64(ctx):
     torch.cuda.empty_cache()
     # the plain FP32 product on its own plan (one FP32 store)
     t0 = time.perf_counter()
-    plan32 = ie.Plan(ie.problem_from_batch(b, ie.precmask(ie.IE_PREC_FP32)), ctx.stream)
+    plan32 = ie.Plan(ie.problem_from_batch(b, ie.precmask(ie.IE_PREC_FP32), symmetry=args.symmetry), ctx.stream)
     plan32_s = time.perf_counter() - t0
     far |= time_far(ctx, plan32, c, R, [ie.IE_PREC_FP32], 1, warmup=1)
     plan32.close()
@@ -497,7 +502,7 @@ def run_serve(ctx):
 
     def run(form, rate, batch):
         precs, opts = forms[form]
-        srv = S.Server(precs, opts, budget, workers=args.serve_workers, batch=batch)
+        srv = S.Server(precs, opts, budget, workers=args.serve_workers, batch=batch, symmetry=args.symmetry)
         gaps = np.diff([0.0] + [q["t_arrival"] for q in reqs])      # seeded arrival process at 1 Hz
         todo = [S.Request(rid=i, problem=pr, khat=q["khat"], pol=q["pol"]) for i, (q, pr) in
                 enumerate(zip(reqs, problems))]

@@ -96,6 +96,14 @@ typedef struct {
     int n_groups;              /* >= 1 when box_group is given                      */
     const int32_t *box_group;  /* HOST, n_boxes ids in [0, n_groups), non-decreasing */
     const double *group_alpha; /* HOST, n_groups self terms (replaces alpha)        */
+    /* Symmetry-compressed coupling store (optional; 0 = one block per displacement).
+     * The cell-centred lattice is invariant under the 48 signed axis permutations Q,
+     * and D(QR) = Q D(R) Q^T, so G_{Qc} = S_Q G_c S_Q^T with S_Q a signed permutation
+     * of the 192 unknowns (§2.2: displacements with the same sorted |d| share one
+     * matrix up to such a map).  With symmetry = 1 the plan stores G_c for the
+     * canonical c = sorted |d| only, keeps 48 signed-permuted copies of the
+     * translation input, and applies the output map in the translation epilogue.   */
+    int symmetry;
 } ie_problem;
 
 typedef struct {
@@ -113,6 +121,8 @@ typedef struct {
     int64_t translate_launches;/* with profiling on: launches timed                   */
     int n_groups;              /* scatterers in the plan (1 without box_group)        */
     int max_rhs;               /* the plan's max_rhs                                  */
+    int64_t n_coupling_blocks; /* stored far blocks: n_far_disp, or the canonical
+                                  displacements with symmetry = 1                     */
 } ie_plan_stats;
 
 /* Build a plan: validate the geometry, group far box pairs by displacement, generate
@@ -170,7 +180,7 @@ ie_status ie_disaggregate(ie_plan plan, const void *Y, void *r, int nrhs, void *
  * up on that device (make it before any stream capture).  Every call reuses the same
  * area, so calls that overlap in time on the GPU (any streams, any plans) race; the
  * partial sums are cleared by each call.  X, Y: device complex64 [nrhs][n_boxes][192].
- * A plan built without IE_PREC_FP32 returns IE_ERR_UNSUPPORTED. */
+ * A plan built without IE_PREC_FP32 or with symmetry = 1 returns IE_ERR_UNSUPPORTED. */
 ie_status ie_translate_noalloc(ie_plan plan, const void *X, void *Y, int nrhs, void *stream);
 
 /* Near product (eq. 2, stored Z^N) plus the self term: y = alpha c + Z^N c. */

@@ -47,7 +47,7 @@ class ie_problem(ctypes.Structure):
                 ("box_ijk", ctypes.c_void_p), ("nb", ctypes.c_void_p), ("P", ctypes.c_void_p),
                 ("alpha", ctypes.c_double), ("self_box_mode", ctypes.c_int), ("prec_mask", ctypes.c_uint),
                 ("max_rhs", ctypes.c_int), ("n_groups", ctypes.c_int), ("box_group", ctypes.c_void_p),
-                ("group_alpha", ctypes.c_void_p)]
+                ("group_alpha", ctypes.c_void_p), ("symmetry", ctypes.c_int)]
 
 
 class ie_plan_stats(ctypes.Structure):
@@ -55,7 +55,7 @@ class ie_plan_stats(ctypes.Structure):
                 ("n_far_disp", ctypes.c_int64), ("n_near_pairs", ctypes.c_int64), ("n_work_simt", ctypes.c_int64),
                 ("n_work_tc", ctypes.c_int64), ("device_bytes", ctypes.c_size_t), ("plan_seconds", ctypes.c_double),
                 ("translate_ms", ctypes.c_double), ("translate_launches", ctypes.c_int64),
-                ("n_groups", ctypes.c_int), ("max_rhs", ctypes.c_int)]
+                ("n_groups", ctypes.c_int), ("max_rhs", ctypes.c_int), ("n_coupling_blocks", ctypes.c_int64)]
 
 
 class ie_solve_opts(ctypes.Structure):
@@ -169,7 +169,7 @@ def _stream(stream) -> int | None:
 
 
 def make_problem(k, eta, box_edge, grid_n, box_ijk, nb, P, alpha, prec_mask, max_rhs=1, self_box_mode=0,
-                 lattice=4, box_group=None, group_alpha=None):
+                 lattice=4, box_group=None, group_alpha=None, symmetry=0):
     """Build an ie_problem struct; keeps the host arrays alive on the returned object.
     box_group / group_alpha: batch of independent scatterers (ids non-decreasing)."""
     ijk = np.ascontiguousarray(box_ijk, dtype=np.int32)
@@ -182,24 +182,24 @@ def make_problem(k, eta, box_edge, grid_n, box_ijk, nb, P, alpha, prec_mask, max
                     P=None if P_a is None else P_a.ctypes.data, alpha=alpha, self_box_mode=self_box_mode,
                     prec_mask=prec_mask, max_rhs=max_rhs, n_groups=0 if ga is None else len(ga),
                     box_group=None if bg is None else bg.ctypes.data,
-                    group_alpha=None if ga is None else ga.ctypes.data)
+                    group_alpha=None if ga is None else ga.ctypes.data, symmetry=int(symmetry))
     pr._keep = (ijk, nb_a, P_a, bg, ga)
     return pr
 
 
-def problem_from(p, prec_mask: int, max_rhs: int = 1):
+def problem_from(p, prec_mask: int, max_rhs: int = 1, symmetry: int = 0):
     """ie_problem from a workloads.Problem-like object."""
     return make_problem(p.k, p.eta, p.a, p.G, p.box_ijk, None if p.P is None else p.nb, p.P, p.alpha, prec_mask,
-                        max_rhs, getattr(p, "self_box_mode", 0), p.lattice)
+                        max_rhs, getattr(p, "self_box_mode", 0), p.lattice, symmetry=symmetry)
 
 
-def problem_from_batch(b, prec_mask: int, max_rhs: int | None = None):
+def problem_from_batch(b, prec_mask: int, max_rhs: int | None = None, symmetry: int = 0):
     """ie_problem of a batch of scatterers (workloads.Batch-like: members in order,
     box_group ids, one self term per member)."""
     m0 = b.members[0]
     return make_problem(m0.k, m0.eta, m0.a, b.G, b.box_ijk, b.nb, b.P, m0.alpha, prec_mask,
                         b.max_rhs if max_rhs is None else max_rhs, getattr(m0, "self_box_mode", 0), m0.lattice,
-                        box_group=b.box_group, group_alpha=b.group_alpha)
+                        box_group=b.box_group, group_alpha=b.group_alpha, symmetry=symmetry)
 
 
 # ---------------------------------------------------------------- C ABI, same names

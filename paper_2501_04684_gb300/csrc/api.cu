@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <unordered_set>
 
@@ -78,6 +79,7 @@ ie_status validate(const ie_problem *pr) {
                      IE_PRECMASK(IE_PREC_BF16X1) | IE_PRECMASK(IE_PREC_FP16X1);
     if (pr->prec_mask == 0 || (pr->prec_mask & ~known)) return set_error("bad prec_mask"), IE_ERR_INVALID;
     if (pr->self_box_mode != 0 && pr->self_box_mode != 1) return set_error("self_box_mode must be 0 or 1"), IE_ERR_INVALID;
+    if (pr->symmetry != 0 && pr->symmetry != 1) return set_error("symmetry must be 0 or 1"), IE_ERR_INVALID;
     if (pr->nb)
         for (int b = 0; b < pr->n_boxes; ++b)
             if (pr->nb[b] < 1 || pr->nb[b] > kNU)
@@ -141,13 +143,60 @@ ie_status build_grid(const ie_problem *pr, BoxGrid &g) {
 }
 
 // Far pairs (Chebyshev distance >= 2) by counting sort on the displacement.
+// ---- symmetry of the cell-centred lattice (§2.2: blocks of displacements with the
+// same sorted |d| are one matrix up to a signed permutation of the unknowns)
+// Q = 8 * p + s: (Q c)_i = (-1)^{bit i of s} c_{kPerm[p][i]}.
+const int kPerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+// Canonical c = |d| sorted ascending and the Q with Q c = d.
+int canon_of(const int32_t d[3], int32_t c[3]) {
+    const int ad[3] = {std::abs(d[0]), std::abs(d[1]), std::abs(d[2])};
+    int ord[3] = {0, 1, 2};
+    std::stable_sort(ord, ord + 3, [&](int x, int y) { return ad[x] < ad[y]; });
+    int pi[3];
+    for (int k = 0; k < 3; ++k) {
+        c[k] = ad[ord[k]];
+        pi[ord[k]] = k;
+    }
+    int pidx = 0;
+    while (pidx < 5 && !(kPerm[pidx][0] == pi[0] && kPerm[pidx][1] == pi[1] && kPerm[pidx][2] == pi[2])) ++pidx;
+    return 8 * pidx + (d[0] < 0 ? 1 : 0) + (d[1] < 0 ? 2 : 0) + (d[2] < 0 ? 4 : 0);
+}
+
+// map[Q][u], u = 3 site + a in the frame of c: U_Q(u) | 0x100 when negated, so that
+// G_{Qc}[U(u)][U(v)] = sign(u) sign(v) G_c[u][v].  Site l maps to l' with
+// l'_i = l_{p(i)} (s_i = +1) or 3 - l_{p(i)} (s_i = -1); component a to the axis i
+// with p(i) = a, with sign s_i.
+void symmetry_map(std::vector<uint16_t> &map) {
+    map.assign((size_t)kSym * kNU, 0);
+    for (int q = 0; q < kSym; ++q) {
+        const int *pi = kPerm[q / 8];
+        int sg[3], inv[3];
+        for (int i = 0; i < 3; ++i) {
+            sg[i] = ((q >> i) & 1) ? -1 : 1;
+            inv[pi[i]] = i;
+        }
+        for (int site = 0; site < kSites; ++site) {
+            const int l[3] = {site & 3, (site >> 2) & 3, site >> 4};
+            int lp[3];
+            for (int i = 0; i < 3; ++i) lp[i] = sg[i] > 0 ? l[pi[i]] : 3 - l[pi[i]];
+            const int sp = lp[0] + 4 * lp[1] + 16 * lp[2];
+            for (int a = 0; a < 3; ++a) {
+                const int ap = inv[a];
+                map[(size_t)q * kNU + 3 * site + a] = (uint16_t)((3 * sp + ap) | (sg[ap] < 0 ? 0x100 : 0));
+            }
+        }
+    }
+}
+
 struct FarGroups {
     std::vector<int32_t> disp;       // n_d x 3
     std::vector<int64_t> start;      // n_d + 1
     std::vector<int32_t> src, dst;   // sorted by displacement, then source
 };
 
-void far_groups(const ie_problem *pr, const BoxGrid &g, bool fill, FarGroups &out, int64_t &npairs, int64_t &nd) {
+void far_groups(const ie_problem *pr, const BoxGrid &g, bool fill, FarGroups &out, int64_t &npairs, int64_t &nd,
+                int64_t *ncanon = nullptr) {
     int span[3] = {2 * g.ext[0] - 1, 2 * g.ext[1] - 1, 2 * g.ext[2] - 1};
     size_t nkeys = (size_t)span[0] * span[1] * span[2];
     std::vector<int64_t> count(nkeys + 1, 0);
@@ -174,6 +223,21 @@ void far_groups(const ie_problem *pr, const BoxGrid &g, bool fill, FarGroups &ou
             npairs += count[k];
             nd++;
         }
+    if (ncanon) {   // distinct sorted |d| among the displacements present
+        const int E = std::max(g.ext[0], std::max(g.ext[1], g.ext[2]));
+        std::vector<char> seen((size_t)E * E * E, 0);
+        *ncanon = 0;
+        for (size_t k = 0; k < nkeys; ++k)
+            if (count[k]) {
+                const int32_t d[3] = {(int32_t)(k / ((size_t)span[2] * span[1])) - (g.ext[0] - 1),
+                                      (int32_t)((k / span[2]) % span[1]) - (g.ext[1] - 1),
+                                      (int32_t)(k % span[2]) - (g.ext[2] - 1)};
+                int32_t c[3];
+                canon_of(d, c);
+                char &f = seen[((size_t)c[0] * E + c[1]) * E + c[2]];
+                if (!f) f = 1, ++*ncanon;
+            }
+    }
     if (!fill) return;
     out.disp.resize(3 * nd);
     out.start.resize(nd + 1);
@@ -233,7 +297,8 @@ void near_lists(const ie_problem *pr, const BoxGrid &g, const std::vector<int32_
     start[n] = (int32_t)src.size();
 }
 
-size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, int64_t nnear, int64_t near_elems) {
+size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, int64_t nnear, int64_t near_elems,
+                  int64_t nblk) {
     size_t b = 0;
     auto add = [&](size_t x) { b += (x + 255) / 256 * 256; };
     int64_t nbox = pr->n_boxes;
@@ -244,14 +309,23 @@ size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, i
     add(nd * 3 * sizeof(int32_t));
     add(npairs * sizeof(int32_t));
     add(npairs * sizeof(int32_t));
+    const bool sym = pr->symmetry == 1;
+    if (!sym) nblk = nd;
+    if (sym) {
+        add(nd * 2 * sizeof(int32_t));                       // block and Q of each group
+        add((size_t)kSym * kNU * sizeof(uint16_t));
+        add(nblk * 3 * sizeof(int32_t));
+        if (pr->prec_mask & IE_PRECMASK(IE_PREC_FP32))       // permuted FP32 inputs
+            add((size_t)kSym * pr->max_rhs * nbox * kNU * sizeof(float2));
+    }
     if (pr->prec_mask & IE_PRECMASK(IE_PREC_FP32))
-        add((size_t)nd * kNU * kNU * sizeof(float2));
+        add((size_t)nblk * kNU * kNU * sizeof(float2));
     else   // staging of the 16-bit images, freed before the plan returns
-        add((size_t)std::min<int64_t>(nd, kCouplingChunk) * kNU * kNU * sizeof(float2));
-    if (wants_bf16(pr->prec_mask)) add((size_t)nd * kTcDispElems * sizeof(uint16_t));
+        add((size_t)std::min<int64_t>(nblk, kCouplingChunk) * kNU * kNU * sizeof(float2));
+    if (wants_bf16(pr->prec_mask)) add((size_t)nblk * kTcDispElems * sizeof(uint16_t));
     if (wants_fp16(pr->prec_mask)) {
-        add((size_t)nd * kTcDispElems * sizeof(uint16_t));
-        add(nd * sizeof(int32_t));
+        add((size_t)nblk * kTcDispElems * sizeof(uint16_t));
+        add(nblk * sizeof(int32_t));
     }
     add((nbox + 1) * sizeof(int32_t));
     add(nnear * sizeof(int32_t));
@@ -261,7 +335,7 @@ size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, i
     add(col * kNU * sizeof(float2));                       // X
     add((size_t)kSlabs * col * kNU * sizeof(float2));      // slabs
     if (wants_tc(pr->prec_mask)) {
-        add(2 * col * 2 * kNU * sizeof(uint16_t));
+        add((sym ? kSym : 1) * 2 * col * 2 * kNU * sizeof(uint16_t));
         add(col * sizeof(int32_t));
     }
     add(sizeof(int) * 4);
@@ -405,13 +479,13 @@ ie_status ie_plan_footprint(const ie_problem *pr, size_t *bytes) {
     int64_t n = 0;
     for (int b = 0; b < pr->n_boxes; ++b) n += (nb[b] = pr->nb ? pr->nb[b] : kNU);
     FarGroups fg;
-    int64_t npairs = 0, nd = 0;
-    far_groups(pr, g, false, fg, npairs, nd);
+    int64_t npairs = 0, nd = 0, ncanon = 0;
+    far_groups(pr, g, false, fg, npairs, nd, pr->symmetry ? &ncanon : nullptr);
     std::vector<int32_t> st, src;
     std::vector<int64_t> boff;
     int64_t elems = 0;
     near_lists(pr, g, nb, st, src, boff, elems);
-    *bytes = plan_bytes(pr, n, npairs, nd, (int64_t)src.size(), elems);
+    *bytes = plan_bytes(pr, n, npairs, nd, (int64_t)src.size(), elems, ncanon);
     return IE_OK;
 }
 
@@ -463,6 +537,24 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
     far_groups(pr, g, true, fg, p->n_far_pairs, p->n_far_disp);
     p->h_disp = fg.disp;
     p->h_gstart = fg.start;
+    // stored blocks: one per displacement, or one per canonical displacement
+    p->sym = pr->symmetry == 1;
+    std::vector<int32_t> gcanon, gsigma, canon_disp;
+    if (p->sym) {
+        std::map<std::array<int32_t, 3>, int32_t> index;
+        gcanon.resize(p->n_far_disp);
+        gsigma.resize(p->n_far_disp);
+        for (int64_t d = 0; d < p->n_far_disp; ++d) {
+            int32_t c[3];
+            gsigma[d] = canon_of(&fg.disp[3 * d], c);
+            auto ins = index.emplace(std::array<int32_t, 3>{c[0], c[1], c[2]}, (int32_t)index.size());
+            if (ins.second) canon_disp.insert(canon_disp.end(), c, c + 3);
+            gcanon[d] = ins.first->second;
+        }
+        p->n_blocks = (int64_t)index.size();
+    } else {
+        p->n_blocks = p->n_far_disp;
+    }
     std::vector<int32_t> nstart, nsrc;
     std::vector<int64_t> nboff;
     near_lists(pr, g, p->nb, nstart, nsrc, nboff, p->near_elems);
@@ -518,7 +610,22 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
         PC(cudaMemcpyAsync(p->d_disp, fg.disp.data(), fg.disp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         PC(cudaMemcpyAsync(p->d_src, fg.src.data(), fg.src.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         PC(cudaMemcpyAsync(p->d_dst, fg.dst.data(), fg.dst.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        const int64_t nd = p->n_far_disp;
+        const int32_t *gen_disp = p->d_disp;
+        if (p->sym) {
+            std::vector<uint16_t> map;
+            symmetry_map(map);
+            PT(dalloc_t(p, &p->d_gcanon, gcanon.size()));
+            PT(dalloc_t(p, &p->d_gsigma, gsigma.size()));
+            PT(dalloc_t(p, &p->d_symmap, map.size()));
+            PT(dalloc_t(p, &p->d_canon_disp, canon_disp.size()));
+            PC(cudaMemcpy(p->d_gcanon, gcanon.data(), gcanon.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+            PC(cudaMemcpy(p->d_gsigma, gsigma.data(), gsigma.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+            PC(cudaMemcpy(p->d_symmap, map.data(), map.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+            PC(cudaMemcpy(p->d_canon_disp, canon_disp.data(), canon_disp.size() * sizeof(int32_t),
+                          cudaMemcpyHostToDevice));
+            gen_disp = p->d_canon_disp;
+        }
+        const int64_t nd = p->n_blocks;
         if (wants_bf16(p->prec_mask)) PT(dalloc_t(p, &p->d_Cbf16, (size_t)nd * kTcDispElems));
         if (wants_fp16(p->prec_mask)) {
             PT(dalloc_t(p, &p->d_Cfp16, (size_t)nd * kTcDispElems));
@@ -539,7 +646,7 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
         for (int64_t d0 = 0; d0 < nd && cst == IE_OK; d0 += chunk) {
             const int64_t m = std::min(chunk, nd - d0);
             float2 *blk = keep32 ? C32 + d0 * kNU * kNU : C32;
-            cst = launch_coupling_simt(p, p->d_disp + 3 * d0, m, blk, false, st);
+            cst = launch_coupling_simt(p, gen_disp + 3 * d0, m, blk, false, st);
             if (cst == IE_OK && wants_bf16(p->prec_mask))
                 cst = launch_coupling_tc(blk, m, p->d_Cbf16 + d0 * kTcDispElems, nullptr, false, st);
             if (cst == IE_OK && wants_fp16(p->prec_mask))
@@ -566,9 +673,10 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
     PT(dalloc_t(p, &p->d_X, col * kNU));
     PT(dalloc_t(p, &p->d_Yslab, (size_t)kSlabs * col * kNU));
     if (wants_tc(p->prec_mask)) {
-        PT(dalloc_t(p, &p->d_Xtc, 2 * col * 2 * kNU));
+        PT(dalloc_t(p, &p->d_Xtc, (size_t)(p->sym ? kSym : 1) * 2 * col * 2 * kNU));
         PT(dalloc_t(p, &p->d_Xexp, col));
     }
+    if (p->sym && (p->prec_mask & IE_PRECMASK(IE_PREC_FP32))) PT(dalloc_t(p, &p->d_Xsym, (size_t)kSym * col * kNU));
     PT(dalloc_t(p, &p->d_err, 4));
     PC(cudaMemsetAsync(p->d_err, 0, 4 * sizeof(int), st));
     PT(dalloc_t(p, &p->d_tmp, (size_t)p->max_rhs * p->n));
@@ -599,6 +707,7 @@ ie_status ie_plan_stats_get(ie_plan p, ie_plan_stats *o) {
     o->translate_launches = p->translate_launches;
     o->n_groups = p->ngroups;
     o->max_rhs = p->max_rhs;
+    o->n_coupling_blocks = p->n_blocks;
     return IE_OK;
 }
 

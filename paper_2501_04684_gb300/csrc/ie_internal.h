@@ -20,6 +20,7 @@ constexpr int kNU = 192;            // 3 unknowns per site
 constexpr int kSlabs = 8;           // FP32 partial-sum slabs of the far field (see translate_simt.cu)
 // Precisions whose products use the fp16 split store (per-block power-of-two scaling).
 inline bool is_fp16(int prec) { return prec == IE_PREC_FP16X3 || prec == IE_PREC_FP16X1; }
+constexpr int kSym = 48;             // signed permutations of the three axes
 constexpr int64_t kCouplingChunk = 4096;   // displacements per staging chunk of the 16-bit coupling images
 
 // Tensor-core store of one coupling block: 3 M-blocks (128 real-embedded rows) x
@@ -112,6 +113,15 @@ struct ie_plan_s {
     uint16_t *d_Cbf16 = nullptr;       // [n_far_disp][kTcDispElems] bf16 images
     uint16_t *d_Cfp16 = nullptr;       // [n_far_disp][kTcDispElems] fp16 images
     int32_t *d_Cexp16 = nullptr;       // [n_far_disp] power-of-two scale of the fp16 images
+    // symmetry-compressed store (symmetry = 1): the block stores above then hold one
+    // block per canonical displacement c = sorted |d| (n_blocks of them)
+    bool sym = false;
+    int64_t n_blocks = 0;              // stored far blocks (n_far_disp without symmetry)
+    int32_t *d_gcanon = nullptr;       // [n_far_disp] stored block of each displacement group
+    int32_t *d_gsigma = nullptr;       // [n_far_disp] signed permutation Q (0..47) with Q c = d
+    uint16_t *d_symmap = nullptr;      // [48][192] u -> U(u) | 0x100 when negated (G_d[U(u)][U(v)] = +-G_c[u][v])
+    int32_t *d_canon_disp = nullptr;   // [n_blocks x 3]
+    float2 *d_Xsym = nullptr;          // [48][max_rhs][nbox][192] signed-permuted FP32 translation inputs
 
     // near zone: per target box a run of (source box, block offset)
     int64_t n_near_pairs = 0;
@@ -124,7 +134,7 @@ struct ie_plan_s {
     // scratch (sized for max_rhs)
     float2 *d_X = nullptr;             // [max_rhs][nbox][192]
     float2 *d_Yslab = nullptr;         // [kSlabs][max_rhs][nbox][192]
-    uint16_t *d_Xtc = nullptr;         // [2 hl][max_rhs][nbox][2 reim][192] 16-bit
+    uint16_t *d_Xtc = nullptr;         // [48 with symmetry][2 hl][max_rhs][nbox][2 reim][192] 16-bit
     int32_t *d_Xexp = nullptr;         // [max_rhs][nbox] power-of-two scale of d_Xtc columns
     int *d_err = nullptr;              // device error word of bounded waits
     float2 *d_tmp = nullptr;           // [max_rhs][n] scratch of products
@@ -162,6 +172,8 @@ ie_status launch_coupling_tc(const float2 *Cs, int64_t nd, uint16_t *out, int32_
 ie_status launch_near_blocks(ie_plan p, cudaStream_t st);
 ie_status launch_aggregate(const ie_plan p, const float2 *c, float2 *X, int nrhs, cudaStream_t st,
                            const int *gate = nullptr);
+// symmetry = 1: the 48 signed-permuted FP32 copies of X into p->d_Xsym
+ie_status launch_permute_sym(const ie_plan p, const float2 *X, int nrhs, cudaStream_t st, const int *gate = nullptr);
 ie_status launch_split_tc(const ie_plan p, const float2 *X, int nrhs, bool fp16, cudaStream_t st,
                           const int *gate = nullptr);
 ie_status launch_disaggregate(const ie_plan p, const float2 *Yslab, int nslab, size_t slab_stride, float2 *r,

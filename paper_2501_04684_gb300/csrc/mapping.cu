@@ -49,13 +49,25 @@ __global__ void copy_kernel(const float4 *__restrict__ a, float4 *__restrict__ b
 // 16-bit hi/lo split of X for the tensor-core path.  Layout [hl][rhs][nbox][reim][192]:
 // row (rhs, box, reim) of 192 contiguous 16-bit values = one operand row (K-major).
 // FP16: the column is scaled by 2^-e so that max |x| < 2^14; e is stored.
+// With a symmetry map, block z writes copy z of the signed-permuted input
+// x^Q[u] = +-x[U_Q(u)] at Xtc + z * (2 planes); the scale is the same for every copy.
 template <bool FP16>
 __global__ void split_kernel(const float2 *__restrict__ X, int nbox, int nrhs, uint16_t *__restrict__ Xtc,
-                             int32_t *__restrict__ Xexp, const int *__restrict__ gate) {
+                             int32_t *__restrict__ Xexp, const uint16_t *__restrict__ symmap,
+                             const int *__restrict__ gate) {
     if (gate && *gate == 0) return;
     int b = blockIdx.x, r = blockIdx.y, u = threadIdx.x;
+    const int sg = blockIdx.z;
     int64_t col = (int64_t)r * nbox + b;
-    float2 x = X[col * kNU + u];
+    float2 x;
+    if (symmap) {
+        const uint16_t e = symmap[sg * kNU + u];
+        x = X[col * kNU + (e & 0xFF)];
+        if (e & 0x100) x = make_float2(-x.x, -x.y);
+    } else {
+        x = X[col * kNU + u];
+    }
+    const bool write_exp = sg == 0;
     float scale = 1.f;
     if (FP16) {
         __shared__ float red[8];
@@ -72,16 +84,16 @@ __global__ void split_kernel(const float2 *__restrict__ X, int nbox, int nrhs, u
                 frexpf(mm, &e);
                 e -= 14;
             }
-            Xexp[col] = e;
+            if (write_exp) Xexp[col] = e;
             s_scale = ldexpf(1.f, -e);
         }
         __syncthreads();
         scale = s_scale;
-    } else if (u == 0) {
+    } else if (u == 0 && write_exp) {
         Xexp[col] = 0;
     }
     int64_t plane = (int64_t)nrhs * nbox * 2 * kNU;
-    uint16_t *row_re = Xtc + (col * 2) * kNU;
+    uint16_t *row_re = Xtc + 2 * plane * sg + (col * 2) * kNU;
     uint16_t *row_im = row_re + kNU;
     float v[2] = {x.x * scale, x.y * scale};
     uint16_t hi[2], lo[2];
@@ -249,10 +261,31 @@ ie_status launch_aggregate(const ie_plan p, const float2 *c, float2 *X, int nrhs
 }
 
 ie_status launch_split_tc(const ie_plan p, const float2 *X, int nrhs, bool fp16, cudaStream_t st, const int *gate) {
+    const dim3 grid(p->nbox, nrhs, p->sym ? kSym : 1);
+    const uint16_t *map = p->sym ? p->d_symmap : nullptr;
     if (fp16)
-        split_kernel<true><<<dim3(p->nbox, nrhs), kNU, 0, st>>>(X, p->nbox, nrhs, p->d_Xtc, p->d_Xexp, gate);
+        split_kernel<true><<<grid, kNU, 0, st>>>(X, p->nbox, nrhs, p->d_Xtc, p->d_Xexp, map, gate);
     else
-        split_kernel<false><<<dim3(p->nbox, nrhs), kNU, 0, st>>>(X, p->nbox, nrhs, p->d_Xtc, p->d_Xexp, gate);
+        split_kernel<false><<<grid, kNU, 0, st>>>(X, p->nbox, nrhs, p->d_Xtc, p->d_Xexp, map, gate);
+    IE_CK_LAUNCH();
+    return IE_OK;
+}
+
+// The 48 signed-permuted copies x^Q[u] = +-x[U_Q(u)] of the FP32 translation input,
+// layout [Q][rhs][nbox][192].
+__global__ void permute_sym_kernel(const float2 *__restrict__ X, int nbox, int nrhs, const uint16_t *__restrict__ symmap,
+                                   float2 *__restrict__ Xsym, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    const int b = blockIdx.x, r = blockIdx.y, sg = blockIdx.z, u = threadIdx.x;
+    const int64_t col = (int64_t)r * nbox + b;
+    const uint16_t e = symmap[sg * kNU + u];
+    float2 x = X[col * kNU + (e & 0xFF)];
+    if (e & 0x100) x = make_float2(-x.x, -x.y);
+    Xsym[((int64_t)sg * nrhs * nbox + col) * kNU + u] = x;
+}
+
+ie_status launch_permute_sym(const ie_plan p, const float2 *X, int nrhs, cudaStream_t st, const int *gate) {
+    permute_sym_kernel<<<dim3(p->nbox, nrhs, kSym), kNU, 0, st>>>(X, p->nbox, nrhs, p->d_symmap, p->d_Xsym, gate);
     IE_CK_LAUNCH();
     return IE_OK;
 }

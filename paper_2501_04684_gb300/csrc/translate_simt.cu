@@ -42,17 +42,29 @@ struct SmemSimt {
 
 namespace {
 
+// Symmetry-compressed store: the block of displacement d is G_c (c canonical) and
+// G_d = S G_c S^T, so the tile reads G_c, takes its input from the signed-permuted
+// copy Q of X, and adds output row u at U_Q(u) with the map's sign.
+struct SymArgs {
+    const int32_t *gcanon = nullptr;     // [disp] stored block (null: no symmetry)
+    const int32_t *gsigma = nullptr;     // [disp] copy Q of the input
+    const uint16_t *map = nullptr;       // [48][192]
+    size_t stride = 0;                   // complex elements between input copies
+};
+
 // One work item: the 192 x (npairs * nrhs) output tile of displacement it.disp,
 // scatter-added into slab (disp mod kSlabs).
 __device__ __forceinline__ void simt_tile(const WorkItem it, const float2 *__restrict__ C,
                                           const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
                                           const float2 *__restrict__ X, float2 *__restrict__ Yslab,
-                                          size_t slab_stride, int nbox, int nrhs) {
+                                          size_t slab_stride, int nbox, int nrhs, const SymArgs sy) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmemSimt &S = *reinterpret_cast<SmemSimt *>(smem_raw);
     const int tid = threadIdx.x;
     const int ncols = it.npairs * nrhs;
-    const float2 *Cd = C + (int64_t)it.disp * kNU * kNU;
+    const int sigma = sy.gcanon ? sy.gsigma[it.disp] : 0;
+    const float2 *Cd = C + (int64_t)(sy.gcanon ? sy.gcanon[it.disp] : it.disp) * kNU * kNU;
+    if (sy.gcanon) X += (size_t)sigma * sy.stride;
 
     // B loader: thread -> (column, 4 consecutive k)
     const int lcol = tid & (kTileN - 1);
@@ -124,6 +136,11 @@ __device__ __forceinline__ void simt_tile(const WorkItem it, const float2 *__res
     }
 
     float2 *Ys = Yslab + (size_t)(it.disp % kSlabs) * slab_stride;
+    uint16_t rmap[6];
+    if (sy.gcanon) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) rmap[i] = sy.map[sigma * kNU + 2 * tm + 64 * (i >> 1) + (i & 1)];
+    }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         int col = 2 * tn + 16 * (j >> 1) + (j & 1);
@@ -131,10 +148,18 @@ __device__ __forceinline__ void simt_tile(const WorkItem it, const float2 *__res
         int pair = it.pair0 + col / nrhs;
         int r = col % nrhs;
         float2 *ycol = Ys + ((int64_t)r * nbox + dst[pair]) * kNU;
+        if (sy.gcanon) {
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            float4 v = make_float4(acc[2 * i][j].x, acc[2 * i][j].y, acc[2 * i + 1][j].x, acc[2 * i + 1][j].y);
-            atomicAdd(reinterpret_cast<float4 *>(ycol + 2 * tm + 64 * i), v);
+            for (int i = 0; i < 6; ++i) {
+                const float sg = (rmap[i] & 0x100) ? -1.f : 1.f;
+                atomicAdd(ycol + (rmap[i] & 0xFF), make_float2(sg * acc[i][j].x, sg * acc[i][j].y));
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                float4 v = make_float4(acc[2 * i][j].x, acc[2 * i][j].y, acc[2 * i + 1][j].x, acc[2 * i + 1][j].y);
+                atomicAdd(reinterpret_cast<float4 *>(ycol + 2 * tm + 64 * i), v);
+            }
         }
     }
 }
@@ -143,9 +168,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 translate_simt_kernel(const WorkItem *__restrict__ items, const float2 *__restrict__ C,
                       const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
                       const float2 *__restrict__ X, float2 *__restrict__ Yslab, size_t slab_stride,
-                      int nbox, int nrhs, const int *__restrict__ gate) {
+                      int nbox, int nrhs, const SymArgs sy, const int *__restrict__ gate) {
     if (gate && *gate == 0) return;
-    simt_tile(items[blockIdx.x], C, src, dst, X, Yslab, slab_stride, nbox, nrhs);
+    simt_tile(items[blockIdx.x], C, src, dst, X, Yslab, slab_stride, nbox, nrhs, sy);
 }
 
 }  // namespace
@@ -163,8 +188,18 @@ ie_status launch_translate_simt(ie_plan p, const float2 *X, float2 *Yslab, int n
     WorkList *wl = nullptr;
     IE_TRY(work_list(p, false, nrhs, &wl));
     if (wl->n == 0) return IE_OK;
+    if (!p->d_Csimt) return set_error("the plan holds no FP32 coupling store"), IE_ERR_UNSUPPORTED;
+    SymArgs sy;
+    if (p->sym) {
+        IE_TRY(launch_permute_sym(p, X, nrhs, st, gate));
+        X = p->d_Xsym;
+        sy.gcanon = p->d_gcanon;
+        sy.gsigma = p->d_gsigma;
+        sy.map = p->d_symmap;
+        sy.stride = (size_t)nrhs * p->nbox * kNU;
+    }
     translate_simt_kernel<<<(unsigned)wl->n, kThreads, sizeof(SmemSimt), st>>>(
-        wl->d_items, p->d_Csimt, p->d_src, p->d_dst, X, Yslab, slab_stride(p), p->nbox, nrhs, gate);
+        wl->d_items, p->d_Csimt, p->d_src, p->d_dst, X, Yslab, slab_stride(p), p->nbox, nrhs, sy, gate);
     IE_CK_LAUNCH();
     return IE_OK;
 }
@@ -204,7 +239,7 @@ translate_simt_grouped_kernel(const int64_t *__restrict__ gstart, const float2 *
     int64_t q = s + (int64_t)blockIdx.y * per;
     if (q >= e) return;
     ie::WorkItem it{(int32_t)d, (int32_t)q, (int32_t)(e - q < per ? e - q : per), 0};
-    ie::simt_tile(it, C, src, dst, X, Yslab, slab_stride, nbox, nrhs);
+    ie::simt_tile(it, C, src, dst, X, Yslab, slab_stride, nbox, nrhs, ie::SymArgs());
 }
 
 // Device address of the scratch area on the current device (looked up once per
@@ -232,8 +267,9 @@ extern "C" ie_status ie_translate_noalloc(ie_plan p, const void *X, void *Y, int
     if (!p || !X || !Y) return set_error("null argument"), IE_ERR_INVALID;
     if (nrhs < 1 || nrhs > p->max_rhs || nrhs > kTileN)
         return set_error("nrhs %d outside [1, %d]", nrhs, p->max_rhs < kTileN ? p->max_rhs : kTileN), IE_ERR_INVALID;
-    if (!(p->prec_mask & IE_PRECMASK(IE_PREC_FP32)))
-        return set_error("ie_translate_noalloc runs the FP32 translation; the plan holds no FP32 store"),
+    if (!(p->prec_mask & IE_PRECMASK(IE_PREC_FP32)) || p->sym)
+        return set_error("ie_translate_noalloc runs the FP32 translation over a full block store; this plan has "
+                         "no FP32 store or a symmetry-compressed one"),
                IE_ERR_UNSUPPORTED;
     size_t off_bytes = ((size_t)(p->n_far_disp + 1) * sizeof(int64_t) + 255) / 256 * 256;
     size_t stride = (size_t)nrhs * p->nbox * kNU;                 // float2 per slab

@@ -74,11 +74,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 // Bounded wait by one thread: false when the limit is hit or the CTA already gave up.
+// SLEEP = false for the latency-critical single threads (MMA issuer, signaller): they
+// rely on try_wait's own suspension instead of backing off.
+template <bool SLEEP = true>
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
     for (uint32_t i = 0; i < kSpinLimit; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (i > 32) __nanosleep(64);
+        if (SLEEP && i > 32) __nanosleep(64);
     }
     *abort_flag = 1;
     return false;
@@ -169,6 +172,11 @@ struct TcArgs {
     int nbox, nrhs;
     int *err;
     const int *gate;
+    // symmetry-compressed store (null gcanon: one block per displacement)
+    const int32_t *gcanon;      // [disp] stored block
+    const int32_t *gsigma;      // [disp] input copy Q
+    const uint16_t *symmap;     // [48][192] output map u -> U_Q(u) | 0x100 when negated
+    int64_t sig_stride;         // elements between the input copies of Xtc
 };
 
 template <bool FP16, bool X3>
@@ -230,7 +238,8 @@ translate_tc_kernel(const TcArgs a) {
                 if (n >= nreal) continue;
                 const int j = n >> 1, part = n & 1;
                 const int p = it.pair0 + j / a.nrhs, rr = j % a.nrhs;
-                r[t2] = a.Xtc + (2 * ((int64_t)rr * a.nbox + a.src[p]) + part) * kNU;
+                const int64_t sg = a.gcanon ? a.gsigma[it.disp] : 0;
+                r[t2] = a.Xtc + sg * a.sig_stride + (2 * ((int64_t)rr * a.nbox + a.src[p]) + part) * kNU;
             }
         };
         const uint16_t *grow[2], *gnext[2];
@@ -239,7 +248,7 @@ translate_tc_kernel(const TcArgs a) {
         for (int64_t i = first; i < a.n_items && ok; i += step) {
             const WorkItem it = a.items[i];
             rows_of(i + step, gnext);   // prefetch: loads in flight during this item
-            const uint16_t *Cd = a.C + (int64_t)it.disp * kTcDispElems;
+            const uint16_t *Cd = a.C + (int64_t)(a.gcanon ? a.gcanon[it.disp] : it.disp) * kTcDispElems;
             for (int kc = 0; kc < kTcKChunks; ++kc, ++g) {
                 const int s = (int)(g % kStages);
                 const uint32_t ph = (uint32_t)((g / kStages) & 1);
@@ -300,7 +309,7 @@ translate_tc_kernel(const TcArgs a) {
                 const uint32_t idesc = f16_idesc(nmma, FP16);
                 const int buf = (int)(il % kAcc);
                 const uint32_t aph = (uint32_t)((il / kAcc) & 1);
-                if (!mbar_wait(smem_u32(&accempty[buf]), aph ^ 1, abort_flag)) {
+                if (!mbar_wait<false>(smem_u32(&accempty[buf]), aph ^ 1, abort_flag)) {
                     ok = false;
                     break;
                 }
@@ -310,7 +319,7 @@ translate_tc_kernel(const TcArgs a) {
                     const int64_t g = il * kTcKChunks + kc;
                     const int s = (int)(g % kStages);
                     const uint32_t ph = (uint32_t)((g / kStages) & 1);
-                    if (!mbar_wait(smem_u32(&full[s]), ph, abort_flag)) {
+                    if (!mbar_wait<false>(smem_u32(&full[s]), ph, abort_flag)) {
                         ok = false;
                         break;
                     }
@@ -344,7 +353,7 @@ translate_tc_kernel(const TcArgs a) {
                 for (int kc = 0; kc < kTcKChunks; ++kc, ++g) {
                     const int s = (int)(g % kStages);
                     const uint32_t ph = (uint32_t)((g / kStages) & 1);
-                    if (!mbar_wait(smem_u32(&landed[s]), ph, abort_flag)) {
+                    if (!mbar_wait<false>(smem_u32(&landed[s]), ph, abort_flag)) {
                         ok = false;
                         break;
                     }
@@ -369,7 +378,7 @@ translate_tc_kernel(const TcArgs a) {
             const int ncols = it.npairs * a.nrhs;
             const int buf = (int)(il % kAcc);
             const uint32_t aph = (uint32_t)((il / kAcc) & 1);
-            const int ed = FP16 ? a.Cexp[it.disp] : 0;
+            const int ed = FP16 ? a.Cexp[a.gcanon ? a.gcanon[it.disp] : it.disp] : 0;
             for (int j = te; j < ncols; j += kEpilogue) {
                 const int p = it.pair0 + j / a.nrhs, r = j % a.nrhs;
                 ep_off[buf * kTcTileCols + j] = ((int64_t)r * a.nbox + a.dst[p]) * (2 * kNU);
@@ -384,6 +393,12 @@ translate_tc_kernel(const TcArgs a) {
             tc_fence_after();
             const int m0 = 64 * it.mb + 16 * q;    // first complex row of this warp
             float *Ys = a.Yslab + (int64_t)(it.disp % kSlabs) * slab_f + 2 * m0 + lane;
+            float sgn = 1.f;
+            if (a.gcanon) {                        // output row of this lane in the frame of d
+                const uint16_t e = a.symmap[a.gsigma[it.disp] * kNU + m0 + (lane >> 1)];
+                Ys = a.Yslab + (int64_t)(it.disp % kSlabs) * slab_f + 2 * (e & 0xFF) + (lane & 1);
+                sgn = (e & 0x100) ? -1.f : 1.f;
+            }
             const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256);
             for (int c0 = 16 * half; c0 < 2 * ncols; c0 += 32) {
                 float v[16];
@@ -395,7 +410,7 @@ translate_tc_kernel(const TcArgs a) {
                     const float ob = __shfl_xor_sync(0xffffffffu, v[2 * jj + 1], 1);
                     float val = (lane & 1) ? v[2 * jj] + ob : v[2 * jj] - ob;
                     if (FP16) val *= ep_scale[buf * kTcTileCols + j];
-                    atomicAdd(Ys + ep_off[buf * kTcTileCols + j], val);
+                    atomicAdd(Ys + ep_off[buf * kTcTileCols + j], sgn * val);
                 }
             }
             tc_fence_before();
@@ -451,6 +466,10 @@ ie_status launch_translate_tc(ie_plan p, int prec, float2 *Yslab, int nrhs, cuda
     a.nrhs = nrhs;
     a.err = p->d_err;
     a.gate = gate;
+    a.gcanon = p->sym ? p->d_gcanon : nullptr;
+    a.gsigma = p->sym ? p->d_gsigma : nullptr;
+    a.symmap = p->sym ? p->d_symmap : nullptr;
+    a.sig_stride = 2 * a.plane;
     int grid = (int)std::min<int64_t>(wl->n, p->tc_sms > 0 ? p->tc_sms : 148);
     if (prec == IE_PREC_BF16X3)
         translate_tc_kernel<false, true><<<grid, kThreadsTc, kSmemBytes, st>>>(a);

@@ -22,6 +22,7 @@ def main():
     ap.add_argument("--prec", default="bf16x3", help="comma list of fp32,bf16x3,fp16x3,bf16x1")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--symmetry", type=int, default=0, choices=[0, 1])
     args = ap.parse_args()
     import numpy as np
     import torch
@@ -34,7 +35,7 @@ def main():
     boxes = W.sphere_shell(args.grid, args.radius)
     p = W.make_problem("profile", args.grid, boxes, 32, seed_P=61, alpha=1.0)
     mask = ie.precmask(ie.IE_PREC_FP32, *precs)
-    with ie.Plan(ie.problem_from(p, mask, args.nrhs)) as plan:
+    with ie.Plan(ie.problem_from(p, mask, args.nrhs, symmetry=args.symmetry)) as plan:
         st = plan.stats
         c = torch.from_numpy(W.coefficients(p, args.nrhs, 62).astype(np.complex64)).cuda()
         y = torch.zeros_like(c)
@@ -42,7 +43,8 @@ def main():
             for _ in range(args.reps):
                 ie.ie_matvec(plan.handle, ie.IE_FAR, prec, c, y, args.nrhs)
         torch.cuda.synchronize()
-        print(f"profile case: {st['n_boxes']} boxes, {st['n_far_pairs']} far pairs, {st['n_far_disp']} groups, "
+        print(f"profile case: {st['n_boxes']} boxes, {st['n_far_pairs']} far pairs, {st['n_far_disp']} groups "
+              f"on {st['n_coupling_blocks']} stored blocks, "
               f"{st['device_bytes'] / 1e9:.2f} GB on the device; precisions {args.prec} x {args.reps}")
 
 

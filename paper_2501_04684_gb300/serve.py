@@ -70,9 +70,11 @@ class Server:
     precs / opts: the plan's precisions and the ie_solve options of every request.
     budget: device bytes the server may hold at once.  batch: most requests merged
     into one plan (same grid only).  keep_solutions: keep each request's solution.
+    symmetry: 1 builds symmetry-compressed plans (one coupling block per sorted |d|).
     """
 
-    def __init__(self, precs, opts, budget: int, workers: int = 4, batch: int = 1, keep_solutions: bool = False):
+    def __init__(self, precs, opts, budget: int, workers: int = 4, batch: int = 1, keep_solutions: bool = False,
+                 symmetry: int = 0):
         import torch
         self.torch = torch
         self.mask = ie.precmask(*precs)
@@ -80,6 +82,7 @@ class Server:
         self.budget = int(budget)
         self.batch = max(1, int(batch))
         self.keep = keep_solutions
+        self.symmetry = int(symmetry)
         self.queue: collections.deque = collections.deque()
         self.done: list = []
         self.used = 0
@@ -130,7 +133,7 @@ class Server:
         the sum of its members' footprints at the batch's column count."""
         R = max(R, req.nrhs)
         n = int(req.problem.nb.sum())
-        plan_b = ie.ie_plan_footprint(ie.problem_from(req.problem, self.mask, R))
+        plan_b = ie.ie_plan_footprint(ie.problem_from(req.problem, self.mask, R, symmetry=self.symmetry))
         m = self.opts.restart
         solver_b = (m + 3) * R * n * 8 + 64 * (m + 2) ** 2 * R
         refine_b = 4 * R * n * 16 if self.opts.refine else 0
@@ -196,11 +199,11 @@ class Server:
         with torch.cuda.stream(stream):
             if len(group) == 1:
                 r = group[0]
-                pr = ie.problem_from(r.problem, self.mask, r.nrhs)
+                pr = ie.problem_from(r.problem, self.mask, r.nrhs, symmetry=self.symmetry)
                 khat, pol, R = r.khat, r.pol, r.nrhs
             else:
                 view = _BatchView(group)
-                pr = ie.problem_from_batch(view, self.mask)
+                pr = ie.problem_from_batch(view, self.mask, symmetry=self.symmetry)
                 R = view.R
                 khat = np.zeros((len(group), R, 3))
                 khat[:, :, 2] = 1.0

@@ -96,3 +96,15 @@ def test_batch_of_two_copies_is_valid(built):
     bad["group_alpha"] = [1.0]
     with pytest.raises(ie.IEError):
         ie.ie_plan_footprint(_tiny_problem(**bad))
+
+
+def test_symmetry_footprint_and_validation(built):
+    """The symmetry-compressed store keeps one block per sorted |d|: a much smaller
+    footprint on a shell; symmetry must be 0 or 1."""
+    p = W.shell16()
+    full = ie.ie_plan_footprint(ie.problem_from(p, ie.precmask(ie.IE_PREC_FP32, ie.IE_PREC_FP16X3)))
+    comp = ie.ie_plan_footprint(ie.problem_from(p, ie.precmask(ie.IE_PREC_FP32, ie.IE_PREC_FP16X3), symmetry=1))
+    assert comp < full / 3
+    with pytest.raises(ie.IEError) as e:
+        ie.ie_plan_footprint(_tiny_problem(symmetry=2))
+    assert e.value.status == ie.IE_ERR_INVALID
