@@ -134,7 +134,7 @@ struct ie_plan_s {
     // scratch (sized for max_rhs)
     float2 *d_X = nullptr;             // [max_rhs][nbox][192]
     float2 *d_Yslab = nullptr;         // [kSlabs][max_rhs][nbox][192]
-    uint16_t *d_Xtc = nullptr;         // [48 with symmetry][2 hl][max_rhs][nbox][2 reim][192] 16-bit
+    uint16_t *d_Xtc = nullptr;         // [48 with symmetry][2 hl][max_rhs][nbox][6 chunk][2 reim][32] 16-bit
     int32_t *d_Xexp = nullptr;         // [max_rhs][nbox] power-of-two scale of d_Xtc columns
     int *d_err = nullptr;              // device error word of bounded waits
     float2 *d_tmp = nullptr;           // [max_rhs][n] scratch of products

@@ -46,8 +46,8 @@ __global__ void copy_kernel(const float4 *__restrict__ a, float4 *__restrict__ b
     if (i < n4) b[i] = a[i];
 }
 
-// 16-bit hi/lo split of X for the tensor-core path.  Layout [hl][rhs][nbox][reim][192]:
-// row (rhs, box, reim) of 192 contiguous 16-bit values = one operand row (K-major).
+// 16-bit hi/lo split of X for the tensor-core path.  Layout [hl][rhs][nbox][chunk][reim][32]:
+// per column 384 values, K-chunk major (chunk = u / 32), re and im rows of a chunk adjacent.
 // FP16: the column is scaled by 2^-e so that max |x| < 2^14; e is stored.
 // With a symmetry map, block z writes copy z of the signed-permuted input
 // x^Q[u] = +-x[U_Q(u)] at Xtc + z * (2 planes); the scale is the same for every copy.
@@ -93,8 +93,9 @@ __global__ void split_kernel(const float2 *__restrict__ X, int nbox, int nrhs, u
         Xexp[col] = 0;
     }
     int64_t plane = (int64_t)nrhs * nbox * 2 * kNU;
-    uint16_t *row_re = Xtc + 2 * plane * sg + (col * 2) * kNU;
-    uint16_t *row_im = row_re + kNU;
+    // K-chunk-major within the column: [chunk of 32][re 32, im 32], so one K-chunk of a
+    // column (both rows) is 128 contiguous bytes for the tensor-core gathers
+    uint16_t *cre = Xtc + 2 * plane * sg + (col * 2) * kNU + (u >> 5) * 64 + (u & 31);
     float v[2] = {x.x * scale, x.y * scale};
     uint16_t hi[2], lo[2];
 #pragma unroll
@@ -109,10 +110,10 @@ __global__ void split_kernel(const float2 *__restrict__ X, int nbox, int nrhs, u
             lo[t] = __bfloat16_as_ushort(__float2bfloat16_rn(v[t] - __bfloat162float(h)));
         }
     }
-    row_re[u] = hi[0];
-    row_im[u] = hi[1];
-    row_re[plane + u] = lo[0];
-    row_im[plane + u] = lo[1];
+    cre[0] = hi[0];
+    cre[32] = hi[1];
+    cre[plane] = lo[0];
+    cre[plane + 32] = lo[1];
 }
 
 // r[i] (+)= sum_u P[i][u] y[u], y = sum over slabs (FP64).  One warp per basis row,

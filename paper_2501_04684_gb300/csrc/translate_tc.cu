@@ -48,8 +48,10 @@ constexpr int kEpiFirst = kProducers + 64;                    // first epilogue 
 constexpr int kImgBytes = 128 * kTcK * 2;        // 8 KB A image
 constexpr int kBBytes = 256 * kTcK * 2;          // 16 KB B plane (256 rows x 64 B)
 constexpr int kStageBytes = 2 * kImgBytes + 2 * kBBytes;     // 48 KB
-constexpr int kEpiBytes = kAcc * kTcTileCols * (8 + 4);       // column offsets + scales per accumulator
-constexpr int kSmemBytes = kStages * kStageBytes + kEpiBytes + 256 /*barriers*/ + 1024 /*alignment*/;
+constexpr int kRing = 4;                         // epilogue metadata buffers (producers stay < 3 items ahead)
+constexpr int kEpiBytes = kRing * kTcTileCols * (8 + 4) + kRing * 16;   // column offsets + scales + item header
+constexpr int kColBytes = 2 * kTcTileCols * 8;                 // gather base pointer of each column, 2 items
+constexpr int kSmemBytes = kStages * kStageBytes + kEpiBytes + kColBytes + 512 /*barriers*/ + 1024 /*alignment*/;
 constexpr uint32_t kTmemCols = 512;
 constexpr uint32_t kSpinLimit = 1u << 24;
 
@@ -93,6 +95,7 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatil
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 __device__ __forceinline__ void named_sync_epilogue() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void named_sync_producers() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -146,17 +149,14 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
-    uint32_t r[16];
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t r[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 struct TcArgs {
     const WorkItem *items;
@@ -164,7 +164,7 @@ struct TcArgs {
     const uint16_t *C;          // [disp][36 images]
     const int32_t *Cexp;        // [disp] or null
     const int32_t *Xexp;        // [col]
-    const uint16_t *Xtc;        // [hl][col][reim][192]
+    const uint16_t *Xtc;        // [hl][col][chunk][reim][32]
     int64_t plane;              // elements per hl plane of Xtc
     const int32_t *src, *dst;
     float *Yslab;               // float view of the complex64 slabs
@@ -185,14 +185,17 @@ translate_tc_kernel(const TcArgs a) {
     if (a.gate && *a.gate == 0) return;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    int64_t *ep_off = reinterpret_cast<int64_t *>(smem + kStages * kStageBytes);      // [kAcc][64]
-    float *ep_scale = reinterpret_cast<float *>(ep_off + kAcc * kTcTileCols);           // [kAcc][64]
-    uint64_t *full = reinterpret_cast<uint64_t *>(ep_scale + kAcc * kTcTileCols);       // [kStages]
+    int64_t *ep_off = reinterpret_cast<int64_t *>(smem + kStages * kStageBytes);      // [kRing][128]
+    float *ep_scale = reinterpret_cast<float *>(ep_off + kRing * kTcTileCols);          // [kRing][128]
+    int4 *ep_head = reinterpret_cast<int4 *>(ep_scale + kRing * kTcTileCols);           // [kRing] ncols, disp, mb
+    const uint16_t **colptr = reinterpret_cast<const uint16_t **>(ep_head + kRing);    // [2][128]
+    uint64_t *full = reinterpret_cast<uint64_t *>(colptr + 2 * kTcTileCols);            // [kStages]
     uint64_t *empty = full + kStages;                                                    // [kStages]
     uint64_t *landed = empty + kStages;                                                  // [kStages]
     uint64_t *accfull = landed + kStages;                                                // [kAcc]
     uint64_t *accempty = accfull + kAcc;                                                 // [kAcc]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accempty + kAcc);
+    uint64_t *staged = accempty + kAcc;                                                  // [kRing]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(staged + kRing);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -206,6 +209,7 @@ translate_tc_kernel(const TcArgs a) {
             mbar_init(smem_u32(&accfull[b]), 1);
             mbar_init(smem_u32(&accempty[b]), kEpilogue);
         }
+        for (int b = 0; b < kRing; ++b) mbar_init(smem_u32(&staged[b]), kProducers);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -226,30 +230,65 @@ translate_tc_kernel(const TcArgs a) {
         int64_t armed[kStages];
         for (int s = 0; s < kStages; ++s) armed[s] = -1;
         bool ok = true;
-        // source rows of this thread's B rows n = tid, tid + 128 for item i (null = padding)
-        auto rows_of = [&](int64_t i, const uint16_t *r[2]) {
-            r[0] = r[1] = nullptr;
-            if (i >= a.n_items) return;
-            const WorkItem it = a.items[i];
-            const int nreal = 2 * it.npairs * a.nrhs;
-#pragma unroll
-            for (int t2 = 0; t2 < 2; ++t2) {
-                const int n = tid + kProducers * t2;
-                if (n >= nreal) continue;
-                const int j = n >> 1, part = n & 1;
-                const int p = it.pair0 + j / a.nrhs, rr = j % a.nrhs;
-                const int64_t sg = a.gcanon ? a.gsigma[it.disp] : 0;
-                r[t2] = a.Xtc + sg * a.sig_stride + (2 * ((int64_t)rr * a.nbox + a.src[p]) + part) * kNU;
-            }
+        // Per item, thread t owns column t: its gather base (input copy, rhs, source box)
+        // and the epilogue's target offset and fp16 scale.  The loads for item i + step
+        // are issued at the start of item i and land while its stages are issued.
+        struct ColInfo {
+            const uint16_t *base;
+            int64_t off;
+            float scale;
+            int ncols, disp, mb;
         };
-        const uint16_t *grow[2], *gnext[2];
-        rows_of(first, grow);
-        int64_t g = 0;                 // stages issued by this CTA
-        for (int64_t i = first; i < a.n_items && ok; i += step) {
+        auto col_info = [&](int64_t i) {
+            ColInfo ci{nullptr, 0, 1.f, 0, 0, 0};
+            if (i >= a.n_items) return ci;
             const WorkItem it = a.items[i];
-            rows_of(i + step, gnext);   // prefetch: loads in flight during this item
+            ci.ncols = it.npairs * a.nrhs;
+            ci.disp = it.disp;
+            ci.mb = it.mb;
+            if (tid >= ci.ncols) return ci;
+            int p, rr;
+            if (a.nrhs == 1) {
+                p = it.pair0 + tid;
+                rr = 0;
+            } else {
+                p = it.pair0 + tid / a.nrhs;
+                rr = tid % a.nrhs;
+            }
+            const int src = a.src[p];
+            const int64_t sg = a.gcanon ? a.gsigma[it.disp] : 0;
+            ci.base = a.Xtc + sg * a.sig_stride + ((int64_t)rr * a.nbox + src) * (2 * kNU);
+            ci.off = ((int64_t)rr * a.nbox + a.dst[p]) * (2 * kNU);
+            if (FP16) {
+                const int ed = a.Cexp[a.gcanon ? a.gcanon[it.disp] : it.disp];
+                ci.scale = ldexpf(1.f, ed + a.Xexp[(int64_t)rr * a.nbox + src]);
+            }
+            return ci;
+        };
+        // publish item il's column data: gather bases (producers) and the epilogue ring
+        auto publish = [&](const ColInfo &ci, int64_t il) {
+            colptr[(il & 1) * kTcTileCols + tid] = ci.base;
+            const int rb = (int)(il % kRing);
+            ep_off[rb * kTcTileCols + tid] = ci.off;
+            ep_scale[rb * kTcTileCols + tid] = ci.scale;
+            if (tid == 0) ep_head[rb] = make_int4(ci.ncols, ci.disp, ci.mb, 0);
+            mbar_arrive(smem_u32(&staged[rb]));      // release: the epilogue reads after its wait
+        };
+        publish(col_info(first), 0);
+        named_sync_producers();
+        // line layout of a stage: each (column, hi/lo) K-chunk is 128 contiguous bytes
+        // (re 32 + im 32 values), fetched by 8 lanes: lanes 0-3 the re row, 4-7 the im row
+        const int sub = tid & 7, lg = tid >> 3, part = sub >> 2, c = sub & 3;
+        int64_t g = 0;                 // stages issued by this CTA
+        int64_t il = 0;
+        for (int64_t i = first; i < a.n_items; i += step, ++il) {
+            const WorkItem it = a.items[i];
+            const ColInfo nxt = col_info(i + step);
+            const int ncols = it.npairs * a.nrhs;
+            const int nl = X3 ? 2 * ncols : ncols;
+            const uint16_t *const *cols = colptr + (il & 1) * kTcTileCols;
             const uint16_t *Cd = a.C + (int64_t)(a.gcanon ? a.gcanon[it.disp] : it.disp) * kTcDispElems;
-            for (int kc = 0; kc < kTcKChunks; ++kc, ++g) {
+            for (int kc = 0; kc < kTcKChunks && ok; ++kc, ++g) {
                 const int s = (int)(g % kStages);
                 const uint32_t ph = (uint32_t)((g / kStages) & 1);
                 if (!warp_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag)) {
@@ -266,23 +305,22 @@ translate_tc_kernel(const TcArgs a) {
                     bulk_g2s(sA, img, kImgBytes, fb);
                     if (X3) bulk_g2s(sA + kImgBytes, img + kTcImageElems, kImgBytes, fb);
                 }
-#pragma unroll
-                for (int t2 = 0; t2 < 2; ++t2) {
-                    if (!grow[t2]) continue;
-                    const int n = tid + kProducers * t2;
-                    const uint32_t rbase = (uint32_t)((n >> 3) * 512 + (n & 7) * 64);
-                    const uint16_t *gs = grow[t2] + kc * kTcK;
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) {
-                        const uint32_t off = rbase + (uint32_t)((c ^ ((n >> 1) & 3)) * 16);
-                        cp_async16(sB + off, gs + c * 8);
-                        if (X3) cp_async16(sB + kBBytes + off, gs + a.plane + c * 8);
-                    }
+                for (int L = lg; L < nl; L += kProducers / 8) {
+                    const int j = X3 ? (L >> 1) : L;
+                    const int hl = X3 ? (L & 1) : 0;
+                    const int n = 2 * j + part;
+                    const uint32_t off = (uint32_t)((n >> 3) * 512 + (n & 7) * 64 + ((c ^ ((n >> 1) & 3)) << 4)) +
+                                         (hl ? (uint32_t)kBBytes : 0u);
+                    const uint16_t *src = cols[j] + (hl ? a.plane : 0) + kc * (2 * kTcK) + part * kTcK + c * 8;
+                    cp_async16(sB + off, src);
                 }
                 cp_async_arrive_noinc(smem_u32(&landed[s]));
             }
-            grow[0] = gnext[0];
-            grow[1] = gnext[1];
+            // every producer warp reaches this once per item, also after a timeout
+            if (ok && i + step < a.n_items) publish(nxt, il + 1);
+            named_sync_producers();
+            if (*abort_flag) ok = false;
+            if (!ok) break;
         }
         cp_async_wait_all();
         if (!ok) {
@@ -302,8 +340,10 @@ translate_tc_kernel(const TcArgs a) {
             const uint64_t d0 = sw64_desc(smem_u32(smem));   // stage s: + s * kStageBytes / 16
             int64_t il = 0;
             bool ok = true;
+            WorkItem nxt = first < a.n_items ? a.items[first] : WorkItem{0, 0, 0, 0};
             for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
-                const WorkItem it = a.items[i];
+                const WorkItem it = nxt;
+                if (i + step < a.n_items) nxt = a.items[i + step];   // in flight during this item
                 const int ncols = it.npairs * a.nrhs;
                 const int nmma = (2 * ncols + 15) & ~15;
                 const uint32_t idesc = f16_idesc(nmma, FP16);
@@ -370,47 +410,57 @@ translate_tc_kernel(const TcArgs a) {
         // ---------------- epilogue warps 6-13 (TMEM lane quarter = warp mod 4)
         const int q = warp & 3;
         const int half = (warp - kEpiFirst / 32) >> 2;     // which alternate 8-column chunks
-        const int te = threadIdx.x - kEpiFirst;
         const int64_t slab_f = (int64_t)a.slab_stride * 2;
         int64_t il = 0;
         for (int64_t i = first; i < a.n_items; i += step, ++il) {
-            const WorkItem it = a.items[i];
-            const int ncols = it.npairs * a.nrhs;
             const int buf = (int)(il % kAcc);
             const uint32_t aph = (uint32_t)((il / kAcc) & 1);
-            const int ed = FP16 ? a.Cexp[a.gcanon ? a.gcanon[it.disp] : it.disp] : 0;
-            for (int j = te; j < ncols; j += kEpilogue) {
-                const int p = it.pair0 + j / a.nrhs, r = j % a.nrhs;
-                ep_off[buf * kTcTileCols + j] = ((int64_t)r * a.nbox + a.dst[p]) * (2 * kNU);
-                if (FP16) ep_scale[buf * kTcTileCols + j] = ldexpf(1.f, ed + a.Xexp[(int64_t)r * a.nbox + a.src[p]]);
-            }
+            const int rb = (int)(il % kRing);
             bool ok = true;
-            if (lane == 0) ok = mbar_wait(smem_u32(&accfull[buf]), aph, abort_flag);
-            named_sync_epilogue();               // publishes ep_off and makes the abort decision uniform
+            if (lane == 0) {
+                ok = mbar_wait(smem_u32(&staged[rb]), (uint32_t)((il / kRing) & 1), abort_flag) &&
+                     mbar_wait(smem_u32(&accfull[buf]), aph, abort_flag);
+            }
+            named_sync_epilogue();               // makes the abort decision uniform
             if (*abort_flag) break;
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
             tc_fence_after();
-            const int m0 = 64 * it.mb + 16 * q;    // first complex row of this warp
-            float *Ys = a.Yslab + (int64_t)(it.disp % kSlabs) * slab_f + 2 * m0 + lane;
+            const int4 hd = ep_head[rb];
+            const int ncols = hd.x, disp = hd.y, mb = hd.z;
+            const int64_t *offs = ep_off + rb * kTcTileCols;
+            const float *scl = ep_scale + rb * kTcTileCols;
+            const int m0 = 64 * mb + 16 * q;       // first complex row of this warp
+            float *Ys = a.Yslab + (int64_t)(disp % kSlabs) * slab_f + 2 * m0 + lane;
             float sgn = 1.f;
             if (a.gcanon) {                        // output row of this lane in the frame of d
-                const uint16_t e = a.symmap[a.gsigma[it.disp] * kNU + m0 + (lane >> 1)];
-                Ys = a.Yslab + (int64_t)(it.disp % kSlabs) * slab_f + 2 * (e & 0xFF) + (lane & 1);
+                const uint16_t e = a.symmap[a.gsigma[disp] * kNU + m0 + (lane >> 1)];
+                Ys = a.Yslab + (int64_t)(disp % kSlabs) * slab_f + 2 * (e & 0xFF) + (lane & 1);
                 sgn = (e & 0x100) ? -1.f : 1.f;
             }
             const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256);
-            for (int c0 = 16 * half; c0 < 2 * ncols; c0 += 32) {
-                float v[16];
-                tmem_ld16(tbase + (uint32_t)c0, v);
+            // two 16-column chunks per TMEM wait (this warp's chunks are 32 columns apart)
+            for (int c0 = 16 * half; c0 < 2 * ncols; c0 += 64) {
+                uint32_t r0[16], r1[16];
+                const bool two = c0 + 32 < 2 * ncols;   // warp-uniform
+                tmem_ld16_nowait(tbase + (uint32_t)c0, r0);
+                if (two) tmem_ld16_nowait(tbase + (uint32_t)(c0 + 32), r1);
+                tmem_wait_ld();
 #pragma unroll
-                for (int jj = 0; jj < 8; ++jj) {
-                    const int j = (c0 >> 1) + jj;
-                    if (j >= ncols) break;             // warp-uniform
-                    const float ob = __shfl_xor_sync(0xffffffffu, v[2 * jj + 1], 1);
-                    float val = (lane & 1) ? v[2 * jj] + ob : v[2 * jj] - ob;
-                    if (FP16) val *= ep_scale[buf * kTcTileCols + j];
-                    atomicAdd(Ys + ep_off[buf * kTcTileCols + j], sgn * val);
+                for (int h = 0; h < 2; ++h) {
+                    if (h == 1 && !two) break;
+                    const uint32_t *r = h ? r1 : r0;
+                    const int jb = (c0 >> 1) + 16 * h;
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) {
+                        const int j = jb + jj;
+                        if (j >= ncols) break;             // warp-uniform
+                        const float ob = __shfl_xor_sync(0xffffffffu, __uint_as_float(r[2 * jj + 1]), 1);
+                        const float ev = __uint_as_float(r[2 * jj]);
+                        float val = (lane & 1) ? ev + ob : ev - ob;
+                        if (FP16) val *= scl[j];
+                        atomicAdd(Ys + offs[j], sgn * val);
+                    }
                 }
             }
             tc_fence_before();
