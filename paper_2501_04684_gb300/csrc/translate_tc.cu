@@ -231,50 +231,56 @@ translate_tc_kernel(const TcArgs a) {
         for (int s = 0; s < kStages; ++s) armed[s] = -1;
         bool ok = true;
         // Per item, thread t owns column t: its gather base (input copy, rhs, source box)
-        // and the epilogue's target offset and fp16 scale.  The loads for item i + step
-        // are issued at the start of item i and land while its stages are issued.
-        struct ColInfo {
-            const uint16_t *base;
-            int64_t off;
-            float scale;
-            int ncols, disp, mb;
+        // and the epilogue's target offset and fp16 scale.  No dependent global load may
+        // stall a stage, so the metadata of an item is fetched in steps over the items
+        // before it: the work item two items ahead; its pair's boxes and the block and
+        // input copy at the start of the item before; the fp16 scales at that item's
+        // third stage; the result is published at its end.
+        struct Meta {
+            int src, dst, rr, blk, sig, ed, xe, ncols, disp, mb;
         };
-        auto col_info = [&](int64_t i) {
-            ColInfo ci{nullptr, 0, 1.f, 0, 0, 0};
-            if (i >= a.n_items) return ci;
-            const WorkItem it = a.items[i];
-            ci.ncols = it.npairs * a.nrhs;
-            ci.disp = it.disp;
-            ci.mb = it.mb;
-            if (tid >= ci.ncols) return ci;
-            int p, rr;
+        auto meta_issue = [&](const WorkItem &w, bool valid) {
+            Meta m{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+            if (!valid) return m;
+            m.ncols = w.npairs * a.nrhs;
+            m.disp = w.disp;
+            m.mb = w.mb;
+            m.blk = a.gcanon ? __ldg(a.gcanon + w.disp) : w.disp;
+            m.sig = a.gcanon ? __ldg(a.gsigma + w.disp) : 0;
+            if (tid >= m.ncols) return m;
+            int p;
             if (a.nrhs == 1) {
-                p = it.pair0 + tid;
-                rr = 0;
+                p = w.pair0 + tid;
             } else {
-                p = it.pair0 + tid / a.nrhs;
-                rr = tid % a.nrhs;
+                p = w.pair0 + tid / a.nrhs;
+                m.rr = tid % a.nrhs;
             }
-            const int src = a.src[p];
-            const int64_t sg = a.gcanon ? a.gsigma[it.disp] : 0;
-            ci.base = a.Xtc + sg * a.sig_stride + ((int64_t)rr * a.nbox + src) * (2 * kNU);
-            ci.off = ((int64_t)rr * a.nbox + a.dst[p]) * (2 * kNU);
-            if (FP16) {
-                const int ed = a.Cexp[a.gcanon ? a.gcanon[it.disp] : it.disp];
-                ci.scale = ldexpf(1.f, ed + a.Xexp[(int64_t)rr * a.nbox + src]);
+            m.src = __ldg(a.src + p);
+            m.dst = __ldg(a.dst + p);
+            return m;
+        };
+        auto meta_scales = [&](Meta &m) {
+            if (FP16 && tid < m.ncols) {
+                m.ed = __ldg(a.Cexp + m.blk);
+                m.xe = __ldg(a.Xexp + (int64_t)m.rr * a.nbox + m.src);
             }
-            return ci;
         };
         // publish item il's column data: gather bases (producers) and the epilogue ring
-        auto publish = [&](const ColInfo &ci, int64_t il) {
-            colptr[(il & 1) * kTcTileCols + tid] = ci.base;
+        auto publish = [&](const Meta &m, int64_t il) {
+            const bool on = tid < m.ncols;
+            colptr[(il & 1) * kTcTileCols + tid] =
+                on ? a.Xtc + (int64_t)m.sig * a.sig_stride + ((int64_t)m.rr * a.nbox + m.src) * (2 * kNU) : nullptr;
             const int rb = (int)(il % kRing);
-            ep_off[rb * kTcTileCols + tid] = ci.off;
-            ep_scale[rb * kTcTileCols + tid] = ci.scale;
-            if (tid == 0) ep_head[rb] = make_int4(ci.ncols, ci.disp, ci.mb, 0);
+            ep_off[rb * kTcTileCols + tid] = on ? ((int64_t)m.rr * a.nbox + m.dst) * (2 * kNU) : 0;
+            ep_scale[rb * kTcTileCols + tid] = (FP16 && on) ? ldexpf(1.f, m.ed + m.xe) : 1.f;
+            if (tid == 0) ep_head[rb] = make_int4(m.ncols, m.disp, m.mb, m.sig);
             mbar_arrive(smem_u32(&staged[rb]));      // release: the epilogue reads after its wait
         };
-        publish(col_info(first), 0);
+        WorkItem w_cur = a.items[first];
+        WorkItem w_nxt = first + step < a.n_items ? a.items[first + step] : WorkItem{0, 0, 0, 0};
+        Meta m_cur = meta_issue(w_cur, true);
+        meta_scales(m_cur);
+        publish(m_cur, 0);
         named_sync_producers();
         // line layout of a stage: each (column, hi/lo) K-chunk is 128 contiguous bytes
         // (re 32 + im 32 values), fetched by 8 lanes: lanes 0-3 the re row, 4-7 the im row
@@ -282,15 +288,19 @@ translate_tc_kernel(const TcArgs a) {
         int64_t g = 0;                 // stages issued by this CTA
         int64_t il = 0;
         for (int64_t i = first; i < a.n_items; i += step, ++il) {
-            const WorkItem it = a.items[i];
-            const ColInfo nxt = col_info(i + step);
+            const WorkItem it = w_cur;
+            const int blk = m_cur.blk;
+            const bool has_next = i + step < a.n_items;
+            const WorkItem w_nn = i + 2 * step < a.n_items ? a.items[i + 2 * step] : WorkItem{0, 0, 0, 0};
+            Meta m_nxt = meta_issue(w_nxt, has_next);
             const int ncols = it.npairs * a.nrhs;
             const int nl = X3 ? 2 * ncols : ncols;
             const uint16_t *const *cols = colptr + (il & 1) * kTcTileCols;
-            const uint16_t *Cd = a.C + (int64_t)(a.gcanon ? a.gcanon[it.disp] : it.disp) * kTcDispElems;
+            const uint16_t *Cd = a.C + (int64_t)blk * kTcDispElems;
             for (int kc = 0; kc < kTcKChunks && ok; ++kc, ++g) {
                 const int s = (int)(g % kStages);
                 const uint32_t ph = (uint32_t)((g / kStages) & 1);
+                if (kc == 2) meta_scales(m_nxt);
                 if (!warp_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag)) {
                     ok = false;
                     break;
@@ -317,10 +327,13 @@ translate_tc_kernel(const TcArgs a) {
                 cp_async_arrive_noinc(smem_u32(&landed[s]));
             }
             // every producer warp reaches this once per item, also after a timeout
-            if (ok && i + step < a.n_items) publish(nxt, il + 1);
+            if (ok && has_next) publish(m_nxt, il + 1);
             named_sync_producers();
             if (*abort_flag) ok = false;
             if (!ok) break;
+            w_cur = w_nxt;
+            w_nxt = w_nn;
+            m_cur = m_nxt;
         }
         cp_async_wait_all();
         if (!ok) {
@@ -427,14 +440,14 @@ translate_tc_kernel(const TcArgs a) {
             if (!ok) break;
             tc_fence_after();
             const int4 hd = ep_head[rb];
-            const int ncols = hd.x, disp = hd.y, mb = hd.z;
+            const int ncols = hd.x, disp = hd.y, mb = hd.z, sig = hd.w;
             const int64_t *offs = ep_off + rb * kTcTileCols;
             const float *scl = ep_scale + rb * kTcTileCols;
             const int m0 = 64 * mb + 16 * q;       // first complex row of this warp
             float *Ys = a.Yslab + (int64_t)(disp % kSlabs) * slab_f + 2 * m0 + lane;
             float sgn = 1.f;
             if (a.gcanon) {                        // output row of this lane in the frame of d
-                const uint16_t e = a.symmap[a.gsigma[disp] * kNU + m0 + (lane >> 1)];
+                const uint16_t e = __ldg(a.symmap + sig * kNU + m0 + (lane >> 1));
                 Ys = a.Yslab + (int64_t)(disp % kSlabs) * slab_f + 2 * (e & 0xFF) + (lane & 1);
                 sgn = (e & 0x100) ? -1.f : 1.f;
             }
