@@ -297,6 +297,24 @@ translate_tc_kernel(const TcArgs a) {
             const int nl = X3 ? 2 * ncols : ncols;
             const uint16_t *const *cols = colptr + (il & 1) * kTcTileCols;
             const uint16_t *Cd = a.C + (int64_t)blk * kTcDispElems;
+            // this thread's lines of the item (<= 16): offset inside a stage and source of
+            // K-chunk 0, computed once per item; a stage then costs one add per copy
+            uint32_t loff[16];
+            const uint16_t *lsrc[16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const int L = lg + (kProducers / 8) * k;
+                lsrc[k] = nullptr;
+                loff[k] = 0;
+                if (L < nl) {
+                    const int j = X3 ? (L >> 1) : L;
+                    const int hl = X3 ? (L & 1) : 0;
+                    const int n = 2 * j + part;
+                    loff[k] = (uint32_t)((n >> 3) * 512 + (n & 7) * 64 + ((c ^ ((n >> 1) & 3)) << 4)) +
+                              (hl ? (uint32_t)kBBytes : 0u);
+                    lsrc[k] = cols[j] + (hl ? a.plane : 0) + part * kTcK + c * 8;
+                }
+            }
             for (int kc = 0; kc < kTcKChunks && ok; ++kc, ++g) {
                 const int s = (int)(g % kStages);
                 const uint32_t ph = (uint32_t)((g / kStages) & 1);
@@ -315,15 +333,9 @@ translate_tc_kernel(const TcArgs a) {
                     bulk_g2s(sA, img, kImgBytes, fb);
                     if (X3) bulk_g2s(sA + kImgBytes, img + kTcImageElems, kImgBytes, fb);
                 }
-                for (int L = lg; L < nl; L += kProducers / 8) {
-                    const int j = X3 ? (L >> 1) : L;
-                    const int hl = X3 ? (L & 1) : 0;
-                    const int n = 2 * j + part;
-                    const uint32_t off = (uint32_t)((n >> 3) * 512 + (n & 7) * 64 + ((c ^ ((n >> 1) & 3)) << 4)) +
-                                         (hl ? (uint32_t)kBBytes : 0u);
-                    const uint16_t *src = cols[j] + (hl ? a.plane : 0) + kc * (2 * kTcK) + part * kTcK + c * 8;
-                    cp_async16(sB + off, src);
-                }
+#pragma unroll
+                for (int k = 0; k < 16; ++k)
+                    if (lsrc[k]) cp_async16(sB + loff[k], lsrc[k] + kc * (2 * kTcK));
                 cp_async_arrive_noinc(smem_u32(&landed[s]));
             }
             // every producer warp reaches this once per item, also after a timeout
