@@ -41,7 +41,10 @@ namespace {
 constexpr int kTcTileCols = 128;                 // complex columns per work item (N <= 256)
 constexpr int kStages = 4;
 constexpr int kAcc = 2;                          // TMEM accumulators of 256 columns
-constexpr int kProducers = 128;
+constexpr int kProducers = 256;
+constexpr int kProdWarps = kProducers / 32;
+constexpr int kMmaWarp = kProdWarps, kSigWarp = kProdWarps + 1;
+constexpr int kLines = 2 * kTcTileCols / (kProducers / 8);      // B lines per producer thread and stage (<=)
 constexpr int kEpilogue = 256;
 constexpr int kThreadsTc = kProducers + 32 + 32 + kEpilogue;  // producers, MMA, signaller, epilogue
 constexpr int kEpiFirst = kProducers + 64;                    // first epilogue thread
@@ -95,7 +98,7 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatil
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 __device__ __forceinline__ void named_sync_epilogue() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
-__device__ __forceinline__ void named_sync_producers() { asm volatile("bar.sync 2, 128;" ::: "memory"); }
+__device__ __forceinline__ void named_sync_producers() { asm volatile("bar.sync 2, %0;" ::"n"(kProducers) : "memory"); }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -213,7 +216,7 @@ translate_tc_kernel(const TcArgs a) {
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 4) {
+    if (warp == kMmaWarp) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -224,8 +227,8 @@ translate_tc_kernel(const TcArgs a) {
     const uint32_t tmem_base = *tmem_slot;
 
     const int64_t first = blockIdx.x, step = gridDim.x;
-    if (warp < 4) {
-        // ---------------- producers (warps 0-3)
+    if (warp < kProdWarps) {
+        // ---------------- producers (warps 0-7)
         const int tid = threadIdx.x;
         int64_t armed[kStages];
         for (int s = 0; s < kStages; ++s) armed[s] = -1;
@@ -268,11 +271,13 @@ translate_tc_kernel(const TcArgs a) {
         // publish item il's column data: gather bases (producers) and the epilogue ring
         auto publish = [&](const Meta &m, int64_t il) {
             const bool on = tid < m.ncols;
-            colptr[(il & 1) * kTcTileCols + tid] =
-                on ? a.Xtc + (int64_t)m.sig * a.sig_stride + ((int64_t)m.rr * a.nbox + m.src) * (2 * kNU) : nullptr;
             const int rb = (int)(il % kRing);
-            ep_off[rb * kTcTileCols + tid] = on ? ((int64_t)m.rr * a.nbox + m.dst) * (2 * kNU) : 0;
-            ep_scale[rb * kTcTileCols + tid] = (FP16 && on) ? ldexpf(1.f, m.ed + m.xe) : 1.f;
+            if (tid < kTcTileCols) {
+                colptr[(il & 1) * kTcTileCols + tid] =
+                    on ? a.Xtc + (int64_t)m.sig * a.sig_stride + ((int64_t)m.rr * a.nbox + m.src) * (2 * kNU) : nullptr;
+                ep_off[rb * kTcTileCols + tid] = on ? ((int64_t)m.rr * a.nbox + m.dst) * (2 * kNU) : 0;
+                ep_scale[rb * kTcTileCols + tid] = (FP16 && on) ? ldexpf(1.f, m.ed + m.xe) : 1.f;
+            }
             if (tid == 0) ep_head[rb] = make_int4(m.ncols, m.disp, m.mb, m.sig);
             mbar_arrive(smem_u32(&staged[rb]));      // release: the epilogue reads after its wait
         };
@@ -297,12 +302,12 @@ translate_tc_kernel(const TcArgs a) {
             const int nl = X3 ? 2 * ncols : ncols;
             const uint16_t *const *cols = colptr + (il & 1) * kTcTileCols;
             const uint16_t *Cd = a.C + (int64_t)blk * kTcDispElems;
-            // this thread's lines of the item (<= 16): offset inside a stage and source of
-            // K-chunk 0, computed once per item; a stage then costs one add per copy
-            uint32_t loff[16];
-            const uint16_t *lsrc[16];
+            // this thread's lines of the item (<= kLines): offset inside a stage and source
+            // of K-chunk 0, computed once per item; a stage then costs one add per copy
+            uint32_t loff[kLines];
+            const uint16_t *lsrc[kLines];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
+            for (int k = 0; k < kLines; ++k) {
                 const int L = lg + (kProducers / 8) * k;
                 lsrc[k] = nullptr;
                 loff[k] = 0;
@@ -334,7 +339,7 @@ translate_tc_kernel(const TcArgs a) {
                     if (X3) bulk_g2s(sA + kImgBytes, img + kTcImageElems, kImgBytes, fb);
                 }
 #pragma unroll
-                for (int k = 0; k < 16; ++k)
+                for (int k = 0; k < kLines; ++k)
                     if (lsrc[k]) cp_async16(sB + loff[k], lsrc[k] + kc * (2 * kTcK));
                 cp_async_arrive_noinc(smem_u32(&landed[s]));
             }
@@ -359,7 +364,7 @@ translate_tc_kernel(const TcArgs a) {
                 }
             }
         }
-    } else if (warp == 4) {
+    } else if (warp == kMmaWarp) {
         // ---------------- MMA issuer (lane 0)
         if (lane == 0) {
             const uint64_t d0 = sw64_desc(smem_u32(smem));   // stage s: + s * kStageBytes / 16
@@ -409,7 +414,7 @@ translate_tc_kernel(const TcArgs a) {
             }
             if (!ok) atomicExch(a.err, 1);
         }
-    } else if (warp == 5) {
+    } else if (warp == kSigWarp) {
         // ---------------- signaller (lane 0)
         if (lane == 0) {
             int64_t g = 0;
@@ -494,7 +499,7 @@ translate_tc_kernel(const TcArgs a) {
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 4) {
+    if (warp == kMmaWarp) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols));
     }
