@@ -469,27 +469,43 @@ translate_tc_kernel(const TcArgs a) {
                 sgn = (e & 0x100) ? -1.f : 1.f;
             }
             const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256);
-            // two 16-column chunks per TMEM wait (this warp's chunks are 32 columns apart)
+            // two 16-column chunks per TMEM wait (this warp's chunks are 32 columns apart).
+            // Lanes 2m', 2m'+1 hold Re G and Im G rows of complex row m'; per pair of
+            // columns (k, k+1) they exchange two values, then the even lane owns the
+            // complex result of column k and the odd lane that of column k+1, added with
+            // one 8-byte reduction each.
+            const bool odd = lane & 1;
+            float *Yrow = Ys - (lane & 1);               // float offset of complex row m' (or U(m'))
             for (int c0 = 16 * half; c0 < 2 * ncols; c0 += 64) {
-                uint32_t r0[16], r1[16];
+                uint32_t r[32];
                 const bool two = c0 + 32 < 2 * ncols;   // warp-uniform
-                tmem_ld16_nowait(tbase + (uint32_t)c0, r0);
-                if (two) tmem_ld16_nowait(tbase + (uint32_t)(c0 + 32), r1);
+                tmem_ld16_nowait(tbase + (uint32_t)c0, r);
+                if (two) {
+                    tmem_ld16_nowait(tbase + (uint32_t)(c0 + 32), r + 16);
+                } else {
+#pragma unroll
+                    for (int k = 16; k < 32; ++k) r[k] = 0u;
+                }
                 tmem_wait_ld();
+                const int jb = c0 >> 1;
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    if (h == 1 && !two) break;
-                    const uint32_t *r = h ? r1 : r0;
-                    const int jb = (c0 >> 1) + 16 * h;
-#pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) {
-                        const int j = jb + jj;
-                        if (j >= ncols) break;             // warp-uniform
-                        const float ob = __shfl_xor_sync(0xffffffffu, __uint_as_float(r[2 * jj + 1]), 1);
-                        const float ev = __uint_as_float(r[2 * jj]);
-                        float val = (lane & 1) ? ev + ob : ev - ob;
-                        if (FP16) val *= scl[j];
-                        atomicAdd(Ys + offs[j], sgn * val);
+                for (int pk = 0; pk < 8; ++pk) {
+                    const int k = 2 * pk;                // columns k, k+1 of the 16 (k even)
+                    const float a0 = __uint_as_float(r[2 * k]), a1 = __uint_as_float(r[2 * k + 1]);
+                    const float b0 = __uint_as_float(r[2 * k + 2]), b1 = __uint_as_float(r[2 * k + 3]);
+                    // even lane (Re G row) sends column k+1's values, odd lane (Im G row) column k's
+                    const float g0 = __shfl_xor_sync(0xffffffffu, odd ? a0 : b0, 1);
+                    const float g1 = __shfl_xor_sync(0xffffffffu, odd ? a1 : b1, 1);
+                    // even: y_k = (Gr xr - Gi xi, Gi xr + Gr xi) with Gi from the partner
+                    // odd:  y_{k+1} with Gr from the partner
+                    float re = odd ? g0 - b1 : a0 - g1;
+                    float im = odd ? b0 + g1 : g0 + a1;
+                    const int kk = k + (odd ? 1 : 0);
+                    const int j = jb + (kk & 7) + 16 * (kk >> 3);
+                    if (j < ncols) {
+                        float sc = sgn;
+                        if (FP16) sc *= scl[j];
+                        atomicAdd(reinterpret_cast<float2 *>(Yrow + offs[j]), make_float2(sc * re, sc * im));
                     }
                 }
             }
