@@ -10,24 +10,31 @@
 // D = Ahi Bhi + Ahi Blo + Alo Bhi is accumulated in FP32 (BF16X1: Ahi Bhi only).
 //
 // Work item = (displacement, M-block of 128 real rows, run of <= 128 complex columns).
-// Persistent CTAs walk the size-sorted item list round-robin.  Warp roles:
-//   warps 0-3  producers: per K-chunk of 32, one thread bulk-copies the two
-//              pre-swizzled 8 KB A images (TMA engine, complete_tx on the stage's `full`
-//              mbarrier); the 128 threads gather the item's B rows (<= 2 each) with
-//              16-byte cp.async into the 64-byte-swizzled K-major layout (chunk c of row n
-//              at c ^ ((n / 2) mod 4)), addresses prefetched one item ahead, and arrive on
-//              the stage's `landed` mbarrier when their copies complete
-//              (cp.async.mbarrier.arrive.noinc) — nobody waits for its own copies.
-//   warp 5     signaller (one thread): per stage, waits for `landed`, issues the proxy
+// Persistent CTAs walk the size-sorted item list round-robin.  576 threads, roles:
+//   warps 0-7  producers.  Per item, thread t < columns owns column t: the pair's boxes,
+//              the block and input copy (symmetric store) are fetched one item ahead,
+//              the fp16 scales at that item's third stage, the work item two ahead, so
+//              no dependent global load stalls a stage.  The column's gather base goes
+//              to shared memory for the copies; its target offset and scale go to a
+//              4-deep ring for the epilogue, released through the `staged` mbarrier.
+//              Per K-chunk of 32 (a stage): one thread bulk-copies the two pre-swizzled
+//              8 KB A images (TMA engine, complete_tx on `full`); every (column, hi/lo)
+//              chunk of B is one 128-byte line of the chunk-major input (re and im rows
+//              adjacent), copied by 8 lanes with 16-byte cp.async into the 64-byte-
+//              swizzled K-major layout (chunk c of row n at c ^ ((n / 2) mod 4)); the
+//              copy addresses are computed once per item.  Threads arrive on `landed`
+//              when their copies complete (cp.async.mbarrier.arrive.noinc).
+//   warp 9     signaller (one thread): per stage, waits for `landed`, issues the proxy
 //              fence that makes the gathered rows visible to the tensor core, arrives on
 //              `full`.  48 KB stages, 4-deep ring.
-//   warp 4     MMA issuer (one thread): tcgen05.mma M=128, N<=256, K=16 with
+//   warp 8     MMA issuer (one thread): tcgen05.mma M=128, N<=256, K=16 with
 //              descriptors derived from one base, into one of two TMEM accumulators
-//              (2 x 256 columns).
-//   warps 6-13 epilogue (two warps per TMEM lane quarter, alternating 8-column chunks):
-//              target offsets of the item's columns staged in shared memory before the
-//              accumulator is ready; tcgen05.ld, complex recombination, fp16 rescaling,
-//              red.global.add into the slab (d mod 8).
+//              (2 x 256 columns); the next work item is prefetched.
+//   warps 10-17 epilogue (two warps per TMEM lane quarter, alternating 16-column chunks,
+//              two chunks per TMEM wait): lanes 2m' and 2m'+1 (Re and Im rows of complex
+//              row m') exchange two values per column pair, then each adds one complex
+//              result (fp16 rescaled) with an 8-byte red.global.add into the slab d mod 8,
+//              at the mapped row with the map's sign for the symmetric store.
 // Every wait is bounded and each role decides on a timeout uniformly (lane-0 wait +
 // shuffle, or a named barrier + abort flag), so no lane is ever left at a barrier; a
 // timeout sets the device error word, drains the CTA's copies, frees TMEM, returns.
