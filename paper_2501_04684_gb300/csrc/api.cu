@@ -419,8 +419,7 @@ ie_status far_product(ie_plan p, int prec, const float2 *c, float2 *y, int nrhs,
                       const int *gate) {
     size_t stride = slab_stride(p);
     IE_TRY(launch_aggregate(p, c, p->d_X, nrhs, st, gate));
-    for (int s = 0; s < kSlabs; ++s)
-        IE_TRY(launch_zero(p->d_Yslab + s * stride, (size_t)nrhs * p->nbox * kNU * sizeof(float2), st, gate));
+    IE_TRY(launch_zero_slabs(p->d_Yslab, kSlabs, stride, (size_t)nrhs * p->nbox * kNU, st, gate));
     if (prec != IE_PREC_FP32) IE_TRY(launch_split_tc(p, p->d_X, nrhs, is_fp16(prec), st, gate));
     IE_TRY(translate_timed(p, prec, p->d_X, p->d_Yslab, nrhs, st, gate));
     IE_TRY(launch_disaggregate(p, p->d_Yslab, kSlabs, stride, y, nrhs, accumulate, st, gate));
@@ -757,8 +756,7 @@ ie_status ie_translate(ie_plan p, int prec, const void *X, void *Y, int nrhs, vo
     IE_TRY(check_prec(p, prec));
     cudaStream_t st = (cudaStream_t)stream;
     size_t stride = slab_stride(p);
-    for (int s = 0; s < kSlabs; ++s)
-        IE_TRY(launch_zero(p->d_Yslab + s * stride, (size_t)nrhs * p->nbox * kNU * sizeof(float2), st));
+    IE_TRY(launch_zero_slabs(p->d_Yslab, kSlabs, stride, (size_t)nrhs * p->nbox * kNU, st));
     if (prec != IE_PREC_FP32) IE_TRY(launch_split_tc(p, (const float2 *)X, nrhs, is_fp16(prec), st));
     IE_TRY(translate_timed(p, prec, (const float2 *)X, p->d_Yslab, nrhs, st, nullptr));
     return launch_sum_slabs(p, p->d_Yslab, kSlabs, stride, (float2 *)Y, nrhs, st);

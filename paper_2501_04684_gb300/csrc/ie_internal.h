@@ -181,6 +181,9 @@ ie_status launch_disaggregate(const ie_plan p, const float2 *Yslab, int nslab, s
 ie_status launch_sum_slabs(const ie_plan p, const float2 *Yslab, int nslab, size_t slab_stride, float2 *Y, int nrhs,
                            cudaStream_t st);
 ie_status launch_zero(void *ptr, size_t bytes, cudaStream_t st, const int *gate = nullptr);
+// nslab regions of `count` complex values, `stride` complex values apart, in one launch
+ie_status launch_zero_slabs(float2 *base, int nslab, size_t stride, size_t count, cudaStream_t st,
+                            const int *gate = nullptr);
 ie_status launch_near(const ie_plan p, const float2 *c, float2 *y, int nrhs, cudaStream_t st,
                       const int *gate = nullptr);
 ie_status launch_translate_simt(ie_plan p, const float2 *X, float2 *Yslab, int nrhs, cudaStream_t st,

@@ -185,6 +185,14 @@ __global__ void zero_kernel(float4 *__restrict__ p, int64_t n4, const int *__res
     for (; i < n4; i += stride) p[i] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// nslab regions of n4 float4 each, stride4 float4 apart (blockIdx.y = region).
+__global__ void zero_slabs_kernel(float4 *__restrict__ p, int64_t n4, int64_t stride4, const int *__restrict__ gate) {
+    if (gate && *gate == 0) return;
+    float4 *q = p + (int64_t)blockIdx.y * stride4;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x)
+        q[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 __global__ void sum_slabs_kernel(const float2 *__restrict__ Yslab, int nslab, size_t slab_stride, int64_t count,
                                  float2 *__restrict__ Y) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -309,6 +317,22 @@ ie_status launch_zero(void *ptr, size_t bytes, cudaStream_t st, const int *gate)
     int64_t grid = (n4 + 255) / 256;
     if (grid > 4096) grid = 4096;
     zero_kernel<<<(unsigned)grid, 256, 0, st>>>(reinterpret_cast<float4 *>(ptr), n4, gate);
+    IE_CK_LAUNCH();
+    return IE_OK;
+}
+
+ie_status launch_zero_slabs(float2 *base, int nslab, size_t stride, size_t count, cudaStream_t st, const int *gate) {
+    if (count == 0 || nslab == 0) return IE_OK;
+    if ((count * sizeof(float2)) % 16 || (stride * sizeof(float2)) % 16) {
+        set_error("launch_zero_slabs: sizes not multiples of 16 bytes");
+        return IE_ERR_INVALID;
+    }
+    const int64_t n4 = (int64_t)(count * sizeof(float2) / 16);
+    int64_t gx = (n4 + 255) / 256;
+    if (gx > 1024) gx = 1024;
+    zero_slabs_kernel<<<dim3((unsigned)gx, (unsigned)nslab), 256, 0, st>>>(reinterpret_cast<float4 *>(base), n4,
+                                                                          (int64_t)(stride * sizeof(float2) / 16),
+                                                                          gate);
     IE_CK_LAUNCH();
     return IE_OK;
 }

@@ -17,7 +17,7 @@ constexpr int kNearWarps = 8;
 // arithmetic, so each lane keeps G x ROWS independent reads in flight.  Per block the
 // sums run in FP32 and are added into FP64 per-warp totals, combined in shared memory.
 template <int ROWS>
-__global__ void __launch_bounds__(kNearWarps * 32)
+__global__ void __launch_bounds__(kNearWarps * 32, 2)
 near_kernel(const int32_t *__restrict__ nb, const int64_t *__restrict__ off, int64_t n,
             const int32_t *__restrict__ start, const int32_t *__restrict__ src,
             const int64_t *__restrict__ boff, const float2 *__restrict__ Nblk,
