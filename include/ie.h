@@ -104,6 +104,12 @@ typedef struct {
      * canonical c = sorted |d| only, keeps 48 signed-permuted copies of the
      * translation input, and applies the output map in the translation epilogue.   */
     int symmetry;
+    /* Right-hand sides of each scatterer (optional, batched plans; NULL = every column).
+     * HOST, n_groups counts in [1, max_rhs]: in a call with nrhs columns, scatterer g
+     * takes part in the translation with its first min(nrhs, group_nrhs[g]) columns
+     * only; its other columns get no far-zone contribution (their inputs should be
+     * zero, as those of padded right-hand sides are).                              */
+    const int32_t *group_nrhs;
 } ie_problem;
 
 typedef struct {
@@ -180,7 +186,8 @@ ie_status ie_disaggregate(ie_plan plan, const void *Y, void *r, int nrhs, void *
  * up on that device (make it before any stream capture).  Every call reuses the same
  * area, so calls that overlap in time on the GPU (any streams, any plans) race; the
  * partial sums are cleared by each call.  X, Y: device complex64 [nrhs][n_boxes][192].
- * A plan built without IE_PREC_FP32 or with symmetry = 1 returns IE_ERR_UNSUPPORTED. */
+ * A plan built without IE_PREC_FP32, with symmetry = 1 or with group_nrhs returns
+ * IE_ERR_UNSUPPORTED. */
 ie_status ie_translate_noalloc(ie_plan plan, const void *X, void *Y, int nrhs, void *stream);
 
 /* Near product (eq. 2, stored Z^N) plus the self term: y = alpha c + Z^N c. */

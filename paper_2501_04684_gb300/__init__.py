@@ -47,7 +47,7 @@ class ie_problem(ctypes.Structure):
                 ("box_ijk", ctypes.c_void_p), ("nb", ctypes.c_void_p), ("P", ctypes.c_void_p),
                 ("alpha", ctypes.c_double), ("self_box_mode", ctypes.c_int), ("prec_mask", ctypes.c_uint),
                 ("max_rhs", ctypes.c_int), ("n_groups", ctypes.c_int), ("box_group", ctypes.c_void_p),
-                ("group_alpha", ctypes.c_void_p), ("symmetry", ctypes.c_int)]
+                ("group_alpha", ctypes.c_void_p), ("symmetry", ctypes.c_int), ("group_nrhs", ctypes.c_void_p)]
 
 
 class ie_plan_stats(ctypes.Structure):
@@ -169,7 +169,7 @@ def _stream(stream) -> int | None:
 
 
 def make_problem(k, eta, box_edge, grid_n, box_ijk, nb, P, alpha, prec_mask, max_rhs=1, self_box_mode=0,
-                 lattice=4, box_group=None, group_alpha=None, symmetry=0):
+                 lattice=4, box_group=None, group_alpha=None, symmetry=0, group_nrhs=None):
     """Build an ie_problem struct; keeps the host arrays alive on the returned object.
     box_group / group_alpha: batch of independent scatterers (ids non-decreasing)."""
     ijk = np.ascontiguousarray(box_ijk, dtype=np.int32)
@@ -177,13 +177,15 @@ def make_problem(k, eta, box_edge, grid_n, box_ijk, nb, P, alpha, prec_mask, max
     P_a = None if P is None else np.ascontiguousarray(np.asarray(P, dtype=np.complex128))
     bg = None if box_group is None else np.ascontiguousarray(box_group, dtype=np.int32)
     ga = None if group_alpha is None else np.ascontiguousarray(group_alpha, dtype=np.float64)
+    gr = None if group_nrhs is None else np.ascontiguousarray(group_nrhs, dtype=np.int32)
     pr = ie_problem(k=k, eta=eta, box_edge=box_edge, lattice=lattice, grid_n=grid_n, n_boxes=ijk.shape[0],
                     box_ijk=ijk.ctypes.data, nb=None if nb_a is None else nb_a.ctypes.data,
                     P=None if P_a is None else P_a.ctypes.data, alpha=alpha, self_box_mode=self_box_mode,
                     prec_mask=prec_mask, max_rhs=max_rhs, n_groups=0 if ga is None else len(ga),
                     box_group=None if bg is None else bg.ctypes.data,
-                    group_alpha=None if ga is None else ga.ctypes.data, symmetry=int(symmetry))
-    pr._keep = (ijk, nb_a, P_a, bg, ga)
+                    group_alpha=None if ga is None else ga.ctypes.data, symmetry=int(symmetry),
+                    group_nrhs=None if gr is None else gr.ctypes.data)
+    pr._keep = (ijk, nb_a, P_a, bg, ga, gr)
     return pr
 
 
@@ -193,13 +195,15 @@ def problem_from(p, prec_mask: int, max_rhs: int = 1, symmetry: int = 0):
                         max_rhs, getattr(p, "self_box_mode", 0), p.lattice, symmetry=symmetry)
 
 
-def problem_from_batch(b, prec_mask: int, max_rhs: int | None = None, symmetry: int = 0):
+def problem_from_batch(b, prec_mask: int, max_rhs: int | None = None, symmetry: int = 0, exact_rhs: bool = False):
     """ie_problem of a batch of scatterers (workloads.Batch-like: members in order,
-    box_group ids, one self term per member)."""
+    box_group ids, one self term per member).  exact_rhs: translate only each member's
+    own right-hand sides (b.nrhs), not the padding up to the batch's largest count."""
     m0 = b.members[0]
     return make_problem(m0.k, m0.eta, m0.a, b.G, b.box_ijk, b.nb, b.P, m0.alpha, prec_mask,
                         b.max_rhs if max_rhs is None else max_rhs, getattr(m0, "self_box_mode", 0), m0.lattice,
-                        box_group=b.box_group, group_alpha=b.group_alpha, symmetry=symmetry)
+                        box_group=b.box_group, group_alpha=b.group_alpha, symmetry=symmetry,
+                        group_nrhs=np.asarray(b.nrhs, dtype=np.int32) if exact_rhs else None)
 
 
 # ---------------------------------------------------------------- C ABI, same names

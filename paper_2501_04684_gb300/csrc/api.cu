@@ -80,6 +80,13 @@ ie_status validate(const ie_problem *pr) {
     if (pr->prec_mask == 0 || (pr->prec_mask & ~known)) return set_error("bad prec_mask"), IE_ERR_INVALID;
     if (pr->self_box_mode != 0 && pr->self_box_mode != 1) return set_error("self_box_mode must be 0 or 1"), IE_ERR_INVALID;
     if (pr->symmetry != 0 && pr->symmetry != 1) return set_error("symmetry must be 0 or 1"), IE_ERR_INVALID;
+    if (pr->group_nrhs) {
+        if (!pr->box_group) return set_error("group_nrhs needs box_group"), IE_ERR_INVALID;
+        for (int g = 0; g < pr->n_groups; ++g)
+            if (pr->group_nrhs[g] < 1 || pr->group_nrhs[g] > pr->max_rhs)
+                return set_error("group_nrhs[%d] = %d outside [1, %d]", g, pr->group_nrhs[g], pr->max_rhs),
+                       IE_ERR_INVALID;
+    }
     if (pr->nb)
         for (int b = 0; b < pr->n_boxes; ++b)
             if (pr->nb[b] < 1 || pr->nb[b] > kNU)
@@ -359,18 +366,31 @@ ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out) {
         return IE_OK;
     }
     int cols = tc ? tc_tile_columns() : simt_tile_columns();
-    int per = cols / nrhs;
-    if (per < 1) return set_error("nrhs %d exceeds the tile width %d", nrhs, cols), IE_ERR_INVALID;
+    if (nrhs > cols) return set_error("nrhs %d exceeds the tile width %d", nrhs, cols), IE_ERR_INVALID;
+    // right-hand-side columns of a pair: the call's nrhs, or fewer for a scatterer that has fewer
+    auto nr_of = [&](int64_t pair) {
+        if (p->gnrhs.empty()) return nrhs;
+        return std::min(nrhs, (int)p->gnrhs[p->box_group[p->h_src[pair]]]);
+    };
     std::vector<WorkItem> items;
+    auto emit = [&](int64_t d, int64_t q, int np, int nr) {
+        if (tc) {
+            for (int mb = 0; mb < 3; ++mb) items.push_back({(int32_t)d, (int32_t)q, np, mb, nr});
+        } else {
+            items.push_back({(int32_t)d, (int32_t)q, np, 0, nr});
+        }
+    };
     for (int64_t d = 0; d < p->n_far_disp; ++d) {
         int64_t s = p->h_gstart[d], e = p->h_gstart[d + 1];
-        for (int64_t q = s; q < e; q += per) {
-            int np = (int)std::min<int64_t>(per, e - q);
-            if (tc) {
-                for (int mb = 0; mb < 3; ++mb) items.push_back({(int32_t)d, (int32_t)q, np, mb});
-            } else {
-                items.push_back({(int32_t)d, (int32_t)q, np, 0});
-            }
+        // runs of pairs with the same column count (pairs of one scatterer are contiguous)
+        int64_t q = s;
+        while (q < e) {
+            const int nr = nr_of(q);
+            const int per = cols / nr;
+            int np = 0;
+            while (q + np < e && np < per && nr_of(q + np) == nr) ++np;
+            emit(d, q, np, nr);
+            q += np;
         }
     }
     if (tc)
@@ -531,6 +551,9 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
     for (int gi = 0; gi <= p->ngroups; ++gi) p->goff[gi] = p->off[p->gbox[gi]];
     if (pr->box_group)
         for (int gi = 0; gi < p->ngroups; ++gi) p->galpha[gi] = pr->group_alpha[gi];
+    if (pr->group_nrhs) p->gnrhs.assign(pr->group_nrhs, pr->group_nrhs + p->ngroups);
+    p->box_group.resize(p->nbox);
+    for (int b = 0; b < p->nbox; ++b) p->box_group[b] = group_of(pr, b);
 
     FarGroups fg;
     far_groups(pr, g, true, fg, p->n_far_pairs, p->n_far_disp);
@@ -653,6 +676,12 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
         }
         if (!keep32) cudaFreeAsync(C32, st);
         PT(cst);
+    }
+
+    // host copy of the pairs' source boxes: per-scatterer column counts cut the work lists
+    if (!p->gnrhs.empty()) {
+        PC(cudaStreamSynchronize(st));   // the upload of fg.src has completed
+        p->h_src = std::move(fg.src);
     }
 
     // near blocks

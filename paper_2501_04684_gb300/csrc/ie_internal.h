@@ -72,6 +72,8 @@ struct WorkItem {
     int32_t pair0;       // first pair (global index into src/dst)
     int32_t npairs;      // pairs in this item (x nrhs columns)
     int32_t mb;          // tensor-core M-block (0..2); unused by the FP32 path
+    int32_t nr;          // right-hand-side columns of each pair (the call's nrhs, or fewer for
+                         // scatterers with fewer right-hand sides)
 };
 
 struct WorkList {
@@ -94,6 +96,9 @@ struct ie_plan_s {
     std::vector<double> galpha;        // ngroups
     int32_t *d_box_group = nullptr;    // [nbox]
     double *d_alpha_box = nullptr;     // [nbox] self term of each box's scatterer
+    std::vector<int32_t> gnrhs;        // ngroups right-hand sides per scatterer (empty: all)
+    std::vector<int32_t> box_group;    // nbox scatterer of each box
+    std::vector<int32_t> h_src;        // source box of every far pair (kept only with gnrhs)
     std::vector<int32_t> ijk, nb;
     std::vector<int64_t> off;          // nbox + 1
 

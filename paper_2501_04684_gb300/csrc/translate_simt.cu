@@ -61,7 +61,7 @@ __device__ __forceinline__ void simt_tile(const WorkItem it, const float2 *__res
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SmemSimt &S = *reinterpret_cast<SmemSimt *>(smem_raw);
     const int tid = threadIdx.x;
-    const int ncols = it.npairs * nrhs;
+    const int ncols = it.npairs * it.nr;
     const int sigma = sy.gcanon ? sy.gsigma[it.disp] : 0;
     const float2 *Cd = C + (int64_t)(sy.gcanon ? sy.gcanon[it.disp] : it.disp) * kNU * kNU;
     if (sy.gcanon) X += (size_t)sigma * sy.stride;
@@ -70,8 +70,8 @@ __device__ __forceinline__ void simt_tile(const WorkItem it, const float2 *__res
     const int lcol = tid & (kTileN - 1);
     const int lkq = tid >> 6;                    // 0..3
     int lc = lcol < ncols ? lcol : 0;
-    const int lpair = it.pair0 + lc / nrhs;
-    const int lr = lc % nrhs;
+    const int lpair = it.pair0 + lc / it.nr;
+    const int lr = lc % it.nr;
     const float2 *xcol = X + ((int64_t)lr * nbox + src[lpair]) * kNU;
 
     auto load_chunk = [&](int kc, int buf) {
@@ -145,8 +145,8 @@ __device__ __forceinline__ void simt_tile(const WorkItem it, const float2 *__res
     for (int j = 0; j < 8; ++j) {
         int col = 2 * tn + 16 * (j >> 1) + (j & 1);
         if (col >= ncols) continue;
-        int pair = it.pair0 + col / nrhs;
-        int r = col % nrhs;
+        int pair = it.pair0 + col / it.nr;
+        int r = col % it.nr;
         float2 *ycol = Ys + ((int64_t)r * nbox + dst[pair]) * kNU;
         if (sy.gcanon) {
 #pragma unroll
@@ -238,7 +238,7 @@ translate_simt_grouped_kernel(const int64_t *__restrict__ gstart, const float2 *
     int64_t s = gstart[d], e = gstart[d + 1];
     int64_t q = s + (int64_t)blockIdx.y * per;
     if (q >= e) return;
-    ie::WorkItem it{(int32_t)d, (int32_t)q, (int32_t)(e - q < per ? e - q : per), 0};
+    ie::WorkItem it{(int32_t)d, (int32_t)q, (int32_t)(e - q < per ? e - q : per), 0, nrhs};
     ie::simt_tile(it, C, src, dst, X, Yslab, slab_stride, nbox, nrhs, ie::SymArgs());
 }
 
@@ -267,7 +267,7 @@ extern "C" ie_status ie_translate_noalloc(ie_plan p, const void *X, void *Y, int
     if (!p || !X || !Y) return set_error("null argument"), IE_ERR_INVALID;
     if (nrhs < 1 || nrhs > p->max_rhs || nrhs > kTileN)
         return set_error("nrhs %d outside [1, %d]", nrhs, p->max_rhs < kTileN ? p->max_rhs : kTileN), IE_ERR_INVALID;
-    if (!(p->prec_mask & IE_PRECMASK(IE_PREC_FP32)) || p->sym)
+    if (!(p->prec_mask & IE_PRECMASK(IE_PREC_FP32)) || p->sym || !p->gnrhs.empty())
         return set_error("ie_translate_noalloc runs the FP32 translation over a full block store; this plan has "
                          "no FP32 store or a symmetry-compressed one"),
                IE_ERR_UNSUPPORTED;

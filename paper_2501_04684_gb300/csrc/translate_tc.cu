@@ -252,18 +252,18 @@ translate_tc_kernel(const TcArgs a) {
         auto meta_issue = [&](const WorkItem &w, bool valid) {
             Meta m{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             if (!valid) return m;
-            m.ncols = w.npairs * a.nrhs;
+            m.ncols = w.npairs * w.nr;
             m.disp = w.disp;
             m.mb = w.mb;
             m.blk = a.gcanon ? __ldg(a.gcanon + w.disp) : w.disp;
             m.sig = a.gcanon ? __ldg(a.gsigma + w.disp) : 0;
             if (tid >= m.ncols) return m;
             int p;
-            if (a.nrhs == 1) {
+            if (w.nr == 1) {
                 p = w.pair0 + tid;
             } else {
-                p = w.pair0 + tid / a.nrhs;
-                m.rr = tid % a.nrhs;
+                p = w.pair0 + tid / w.nr;
+                m.rr = tid % w.nr;
             }
             m.src = __ldg(a.src + p);
             m.dst = __ldg(a.dst + p);
@@ -289,7 +289,7 @@ translate_tc_kernel(const TcArgs a) {
             mbar_arrive(smem_u32(&staged[rb]));      // release: the epilogue reads after its wait
         };
         WorkItem w_cur = a.items[first];
-        WorkItem w_nxt = first + step < a.n_items ? a.items[first + step] : WorkItem{0, 0, 0, 0};
+        WorkItem w_nxt = first + step < a.n_items ? a.items[first + step] : WorkItem{0, 0, 0, 0, 1};
         Meta m_cur = meta_issue(w_cur, true);
         meta_scales(m_cur);
         publish(m_cur, 0);
@@ -303,9 +303,9 @@ translate_tc_kernel(const TcArgs a) {
             const WorkItem it = w_cur;
             const int blk = m_cur.blk;
             const bool has_next = i + step < a.n_items;
-            const WorkItem w_nn = i + 2 * step < a.n_items ? a.items[i + 2 * step] : WorkItem{0, 0, 0, 0};
+            const WorkItem w_nn = i + 2 * step < a.n_items ? a.items[i + 2 * step] : WorkItem{0, 0, 0, 0, 1};
             Meta m_nxt = meta_issue(w_nxt, has_next);
-            const int ncols = it.npairs * a.nrhs;
+            const int ncols = it.npairs * it.nr;
             const int nl = X3 ? 2 * ncols : ncols;
             const uint16_t *const *cols = colptr + (il & 1) * kTcTileCols;
             const uint16_t *Cd = a.C + (int64_t)blk * kTcDispElems;
@@ -377,11 +377,11 @@ translate_tc_kernel(const TcArgs a) {
             const uint64_t d0 = sw64_desc(smem_u32(smem));   // stage s: + s * kStageBytes / 16
             int64_t il = 0;
             bool ok = true;
-            WorkItem nxt = first < a.n_items ? a.items[first] : WorkItem{0, 0, 0, 0};
+            WorkItem nxt = first < a.n_items ? a.items[first] : WorkItem{0, 0, 0, 0, 1};
             for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
                 const WorkItem it = nxt;
                 if (i + step < a.n_items) nxt = a.items[i + step];   // in flight during this item
-                const int ncols = it.npairs * a.nrhs;
+                const int ncols = it.npairs * it.nr;
                 const int nmma = (2 * ncols + 15) & ~15;
                 const uint32_t idesc = f16_idesc(nmma, FP16);
                 const int buf = (int)(il % kAcc);

@@ -54,6 +54,7 @@ class _BatchView:
         self.members = [r.problem for r in reqs]
         self.G = reqs[0].problem.G
         self.R = max(r.nrhs for r in reqs)
+        self.nrhs = [r.nrhs for r in reqs]
 
     box_ijk = property(lambda s: np.concatenate([m.box_ijk for m in s.members]).astype(np.int32))
     nb = property(lambda s: np.concatenate([m.nb for m in s.members]).astype(np.int32))
@@ -203,7 +204,7 @@ class Server:
                 khat, pol, R = r.khat, r.pol, r.nrhs
             else:
                 view = _BatchView(group)
-                pr = ie.problem_from_batch(view, self.mask, symmetry=self.symmetry)
+                pr = ie.problem_from_batch(view, self.mask, symmetry=self.symmetry, exact_rhs=True)
                 R = view.R
                 khat = np.zeros((len(group), R, 3))
                 khat[:, :, 2] = 1.0

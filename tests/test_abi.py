@@ -73,6 +73,9 @@ def test_footprint_is_host_only_and_counts_pairs(built):
     dict(box_group=np.r_[np.ones(32), np.zeros(32)], group_alpha=[1.0, 1.0]),   # ids decreasing
     dict(box_group=np.full(64, 2), group_alpha=[1.0, 1.0]),                     # id out of range
     dict(box_group=np.zeros(64)),                                               # no self terms
+    dict(group_nrhs=[1]),                                                       # counts without groups
+    dict(box_group=np.zeros(64), group_alpha=[1.0], group_nrhs=[2]),            # count above max_rhs
+    dict(box_group=np.zeros(64), group_alpha=[1.0], group_nrhs=[0]),            # count below 1
 ])
 def test_validation_rejects(built, bad):
     pr = _tiny_problem(**bad)

@@ -162,3 +162,39 @@ def test_batch_solve_member_alone_same_iterations(batch, plan):
     st, info = ie.ie_solve(plan.handle, v, x, R, ie.solve_opts(tol=1e-6, restart=50))
     assert st == ie.IE_OK
     assert abs(info["iterations"] - max(its)) <= 1, (info, its)   # rounding may move the last step
+
+
+@pytest.fixture(scope="module")
+def plan_exact(batch):
+    with ie.Plan(ie.problem_from_batch(batch, ie.precmask(ie.IE_PREC_FP32, ie.IE_PREC_FP16X3), exact_rhs=True)) as pl:
+        yield pl
+
+
+@pytest.mark.parametrize("prec", [ie.IE_PREC_FP32, ie.IE_PREC_FP16X3], ids=_name)
+def test_batch_exact_rhs_far_matvec(prec, batch, coeffs, refs, plan_exact):
+    """With per-scatterer right-hand-side counts, a member's own columns match the
+    oracle and its padding columns get no far-zone contribution."""
+    _, packed = coeffs
+    R = batch.max_rhs
+    y = empty((R, batch.n))
+    ie.ie_matvec(plan_exact.handle, ie.IE_FAR, prec, dev(packed), y, R)
+    for g, got in enumerate(batch.split(host(y))):
+        q = batch.nrhs[g]
+        assert rel_l2(got[:q], refs["far"][g][:q]) <= BOUND[prec], (g, _name(prec))
+        assert not np.any(got[q:]), g
+
+
+def test_batch_exact_rhs_fewer_items_and_solve(batch, plan, plan_exact):
+    kh, pol = batch.padded_waves()
+    R = batch.max_rhs
+    v = empty((R, batch.n))
+    ie.ie_rhs_plane_wave(plan_exact.handle, kh, pol, v)
+    x = empty((R, batch.n))
+    st, info = ie.ie_solve(plan_exact.handle, v, x, R, ie.solve_opts(tol=1e-5, prec=ie.IE_PREC_FP16X3))
+    assert st == ie.IE_OK, info
+    res = _true_residuals(batch, host(v), host(x))
+    assert res.max() <= 1e-5, res
+    # the padded plan's tensor-core work list for the same nrhs has more items
+    y = empty((R, batch.n))
+    ie.ie_matvec(plan.handle, ie.IE_FAR, ie.IE_PREC_FP16X3, v, y, R)
+    assert ie.ie_plan_stats_get(plan_exact.handle)["n_work_tc"] < ie.ie_plan_stats_get(plan.handle)["n_work_tc"]
