@@ -272,13 +272,18 @@ def time_far(ctx, plan, c, nrhs, precs, reps, warmup=3):
     return out
 
 
-def tc_roofline(pairs_x_rhs: int, kernel_ms: float, products: int, summary: str | None, kernel: str) -> dict:
+def tc_roofline(pairs_x_rhs: int, kernel_ms: float, products: int, summary: str | None, kernel: str,
+                sustained: bool = False) -> dict:
+    """Roofline of a translation launch; sustained = the kernel runs for seconds, so the
+    power-capped sustained dense peak is the bound."""
     peaks = measured_peaks()
     flops = products * pairs_x_rhs * 8 * 192 * 192
     ach = flops / (kernel_ms / 1e3) / 1e12
-    r = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16"], "unit": "TFLOP/s", "frac": ach / peaks["bf16"],
+    peak = peaks["bf16_sustained"] if sustained else peaks["bf16"]
+    source = peaks["source"].replace("burst", "sustained") if sustained else peaks["source"]
+    r = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
          "traffic": profiled_traffic(summary, "translate_tc.cu") if summary else None,
-         "kernel": kernel, "peak_source": peaks["source"], "algorithmic_flops_per_launch": flops, "dram_gbs": None}
+         "kernel": kernel, "peak_source": source, "algorithmic_flops_per_launch": flops, "dram_gbs": None}
     if r["traffic"]:
         r["dram_gbs"] = r["traffic"] / (kernel_ms / 1e3) / 1e9
     return r
@@ -487,7 +492,7 @@ def run_batch64(ctx):
         "far_pair_rhs": pair_rhs,
         "gpu_launches": int(solve["launches"]), "clocks": solve["clocks"],
         "roofline": tc_roofline(pair_rhs, far["fp16x3"]["translate_kernel_ms"], 3, None,
-                                "translate_tc_kernel<fp16,x3>"),
+                                "translate_tc_kernel<fp16,x3>", sustained=True),
     }
     return out
 
