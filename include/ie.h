@@ -152,6 +152,34 @@ ie_status ie_plan_stats_get(ie_plan plan, ie_plan_stats *out);
  * stream and its duration added to translate_ms (the call then waits for it). */
 ie_status ie_plan_profile(ie_plan plan, int enable);
 
+/* Autotuner of the tensor-core translation (no counterpart in the paper): for calls with
+ * this nrhs, times the translation of precision `prec` with tile widths of 128, 112, 96
+ * and 64 columns and two work-item orders (largest first; displacement order, which runs
+ * the tiles of one group on neighbouring CTAs together) and keeps the fastest for the
+ * plan.  Synchronises `stream`; overwrites the plan's scratch.  info (may be NULL): the
+ * chosen tile width and order, its time per launch and that of the default (128, 0).
+ * Errors: IE_ERR_INVALID, IE_ERR_UNSUPPORTED (FP32 or a precision not in the plan). */
+typedef struct {
+    int tile_columns;      /* complex columns per work item chosen                       */
+    int order;             /* 0: items largest first, 1: displacement order              */
+    double ms;             /* its translation time per launch                            */
+    double default_ms;     /* the default's (128 columns, order 0)                       */
+    int candidates;        /* configurations timed                                       */
+} ie_tune_info;
+ie_status ie_plan_tune(ie_plan plan, int prec, int nrhs, ie_tune_info *info, void *stream);
+
+/* Status of the plan's earlier asynchronous work: synchronises `stream`; returns
+ * IE_ERR_TIMEOUT if a translation launch gave up one of its bounded device waits since
+ * the last check (its product is then incomplete; the plan stays usable), IE_OK otherwise.
+ * ie_solve checks this itself before it returns. */
+ie_status ie_plan_check(ie_plan plan, void *stream);
+
+/* Diagnostic (no counterpart in the paper): one thread waits, with the translation
+ * kernels' bounded wait, on an mbarrier that nothing signals, for about limit_ms
+ * (0 < limit_ms <= 10000).  Returns IE_ERR_TIMEOUT when the wait gave up and reported
+ * it, as designed; any other status means the bound does not work. */
+ie_status ie_diag_bounded_wait(double limit_ms, void *stream);
+
 /* Release every device allocation of the plan (synchronises the device first). */
 ie_status ie_plan_destroy(ie_plan plan);
 

@@ -30,7 +30,8 @@ EXPORTED = [
     "ie_aggregate", "ie_translate", "ie_disaggregate", "ie_near", "ie_coupling_blocks", "ie_rhs_plane_wave",
     "ie_solve_opts_default", "ie_solve", "ie_solver_create", "ie_solver_footprint", "ie_solver_start",
     "ie_solver_advance", "ie_solver_poll", "ie_solver_destroy", "ie_status_str", "ie_last_error", "ie_version",
-    "ie_plan_profile", "ie_kernel_launches", "ie_translate_noalloc",
+    "ie_plan_profile", "ie_kernel_launches", "ie_translate_noalloc", "ie_plan_check", "ie_diag_bounded_wait",
+    "ie_plan_tune",
 ]
 
 
@@ -56,6 +57,11 @@ class ie_plan_stats(ctypes.Structure):
                 ("n_work_tc", ctypes.c_int64), ("device_bytes", ctypes.c_size_t), ("plan_seconds", ctypes.c_double),
                 ("translate_ms", ctypes.c_double), ("translate_launches", ctypes.c_int64),
                 ("n_groups", ctypes.c_int), ("max_rhs", ctypes.c_int), ("n_coupling_blocks", ctypes.c_int64)]
+
+
+class ie_tune_info(ctypes.Structure):
+    _fields_ = [("tile_columns", ctypes.c_int), ("order", ctypes.c_int), ("ms", ctypes.c_double),
+                ("default_ms", ctypes.c_double), ("candidates", ctypes.c_int)]
 
 
 class ie_solve_opts(ctypes.Structure):
@@ -109,6 +115,9 @@ def lib() -> ctypes.CDLL:
     L.ie_last_error.restype = ctypes.c_char_p
     L.ie_version.restype = ctypes.c_char_p
     L.ie_kernel_launches.restype = ctypes.c_int64
+    L.ie_plan_check.argtypes = [vp, vp]
+    L.ie_diag_bounded_wait.argtypes = [ctypes.c_double, vp]
+    L.ie_plan_tune.argtypes = [vp, i, i, P(ie_tune_info), vp]
     for name in EXPORTED:          # every declared symbol must resolve
         getattr(L, name)
     _lib = L
@@ -353,6 +362,23 @@ def ie_solver_poll(solver):
 def ie_solver_destroy(solver):
     _solver_sizes.pop(solver, None)
     return _check(lib().ie_solver_destroy(solver), "ie_solver_destroy")
+
+
+def ie_plan_tune(plan, prec, nrhs, stream=None) -> dict:
+    """Autotunes the tensor-core translation of `prec` for calls with nrhs columns."""
+    info = ie_tune_info()
+    _check(lib().ie_plan_tune(plan, prec, nrhs, ctypes.byref(info), _stream(stream)), "ie_plan_tune")
+    return {f: getattr(info, f) for f, _ in info._fields_}
+
+
+def ie_plan_check(plan, stream=None):
+    """IE_OK, or raises with IE_ERR_TIMEOUT when a translation gave up a bounded wait."""
+    return _check(lib().ie_plan_check(plan, _stream(stream)), "ie_plan_check")
+
+
+def ie_diag_bounded_wait(limit_ms: float = 50.0, stream=None) -> int:
+    """Runs the bounded-wait diagnostic; returns its status (IE_ERR_TIMEOUT is the design)."""
+    return int(lib().ie_diag_bounded_wait(float(limit_ms), _stream(stream)))
 
 
 def ie_kernel_launches() -> int:

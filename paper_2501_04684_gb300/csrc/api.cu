@@ -356,16 +356,27 @@ size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, i
 
 // Work list of one translation kernel for `nrhs`: every displacement group cut into
 // runs of at most (tile columns / nrhs) pairs; the tensor-core list repeats each run
-// for its three M-blocks and orders runs by size (largest first) for the persistent
-// kernel's static round-robin.
+// for its three M-blocks and, in order 0, orders runs by size (largest first) for the
+// persistent kernel's static round-robin (order 1 keeps displacement order, so that
+// the tiles of one group run at the same time on neighbouring CTAs).  The tensor-core
+// tile width and order come from ie_plan_tune (default: the full 128 columns, order 0).
 ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out) {
     auto &cache = tc ? p->tc_work : p->simt_work;
-    auto it = cache.find(nrhs);
+    int cols = tc ? tc_tile_columns() : simt_tile_columns(), order = 0;
+    if (tc) {
+        auto t = p->tc_tuned.find(nrhs);
+        if (t != p->tc_tuned.end()) cols = t->second.first, order = t->second.second;
+    }
+    const int key = tc ? (nrhs * 1024 + cols) * 2 + order : nrhs;
+    auto it = cache.find(key);
     if (it != cache.end()) {
         *out = &it->second;
+        if (tc)
+            p->n_work_tc = it->second.n;
+        else
+            p->n_work_simt = it->second.n;
         return IE_OK;
     }
-    int cols = tc ? tc_tile_columns() : simt_tile_columns();
     if (nrhs > cols) return set_error("nrhs %d exceeds the tile width %d", nrhs, cols), IE_ERR_INVALID;
     // right-hand-side columns of a pair: the call's nrhs, or fewer for a scatterer that has fewer
     auto nr_of = [&](int64_t pair) {
@@ -393,9 +404,9 @@ ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out) {
             q += np;
         }
     }
-    if (tc)
+    if (tc && order == 0)
         std::stable_sort(items.begin(), items.end(),
-                         [](const WorkItem &a, const WorkItem &b) { return a.npairs > b.npairs; });
+                         [](const WorkItem &a, const WorkItem &b) { return a.npairs * a.nr > b.npairs * b.nr; });
     WorkList wl;
     wl.n = (int64_t)items.size();
     if (wl.n) {
@@ -406,8 +417,8 @@ ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out) {
         p->n_work_tc = wl.n;
     else
         p->n_work_simt = wl.n;
-    cache[nrhs] = wl;
-    *out = &cache[nrhs];
+    cache[key] = wl;
+    *out = &cache[key];
     return IE_OK;
 }
 
@@ -444,6 +455,16 @@ ie_status far_product(ie_plan p, int prec, const float2 *c, float2 *y, int nrhs,
     IE_TRY(translate_timed(p, prec, p->d_X, p->d_Yslab, nrhs, st, gate));
     IE_TRY(launch_disaggregate(p, p->d_Yslab, kSlabs, stride, y, nrhs, accumulate, st, gate));
     return IE_OK;
+}
+
+ie_status take_device_error(ie_plan p, cudaStream_t st) {
+    IE_CK(cudaStreamSynchronize(st));
+    int w = 0;
+    IE_CK(cudaMemcpy(&w, p->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (w == 0) return IE_OK;
+    IE_CK(cudaMemset(p->d_err, 0, sizeof(int)));
+    set_error("a translation kernel gave up a bounded wait (its result is incomplete)");
+    return IE_ERR_TIMEOUT;
 }
 
 ie_status apply(ie_plan p, int which, int prec, const float2 *c, float2 *y, int nrhs, cudaStream_t st,
@@ -718,6 +739,72 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
     return IE_OK;
 #undef PT
 #undef PC
+}
+
+ie_status ie_plan_tune(ie_plan p, int prec, int nrhs, ie_tune_info *info, void *stream) {
+    if (!p) return set_error("null plan"), IE_ERR_INVALID;
+    IE_TRY(check_prec(p, prec));
+    IE_TRY(check_rhs(p, nrhs));
+    if (prec == IE_PREC_FP32) return set_error("the FP32 translation has no tuned tile"), IE_ERR_UNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    // timing input: zero fields split into the 16-bit planes (the kernel's work does not
+    // depend on the values)
+    IE_TRY(launch_zero(p->d_X, (size_t)nrhs * p->nbox * kNU * sizeof(float2), st));
+    IE_TRY(launch_split_tc(p, p->d_X, nrhs, is_fp16(prec), st));
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    IE_CK(cudaEventCreate(&ev[0]));
+    IE_CK(cudaEventCreate(&ev[1]));
+    const int cands[] = {128, 112, 96, 64};
+    std::pair<int, int> best{tc_tile_columns(), 0};
+    double best_ms = 1e30, default_ms = 0;
+    int tried = 0;
+    ie_status e = IE_OK;
+    for (int cols : cands) {
+        if (cols > tc_tile_columns() || cols < nrhs) continue;
+        for (int order = 0; order < 2 && e == IE_OK; ++order) {
+            p->tc_tuned[nrhs] = {cols, order};
+            e = launch_translate_tc(p, prec, p->d_Yslab, nrhs, st, nullptr);   // builds the list, warms up
+            if (e != IE_OK) break;
+            if (cudaEventRecord(ev[0], st) != cudaSuccess) e = IE_ERR_CUDA;
+            for (int r = 0; r < 2 && e == IE_OK; ++r) e = launch_translate_tc(p, prec, p->d_Yslab, nrhs, st, nullptr);
+            float ms = 0;
+            if (e == IE_OK && (cudaEventRecord(ev[1], st) != cudaSuccess || cudaEventSynchronize(ev[1]) != cudaSuccess ||
+                               cudaEventElapsedTime(&ms, ev[0], ev[1]) != cudaSuccess))
+                e = IE_ERR_CUDA;
+            if (e != IE_OK) break;
+            ms *= 0.5f;
+            ++tried;
+            if (cols == tc_tile_columns() && order == 0) default_ms = ms;
+            if (ms < best_ms) best_ms = ms, best = {cols, order};
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (e != IE_OK) {
+        p->tc_tuned.erase(nrhs);
+        if (e == IE_ERR_CUDA) set_error("ie_plan_tune: timing failed");
+        return e;
+    }
+    p->tc_tuned[nrhs] = best;
+    IE_TRY(take_device_error(p, st));
+    if (info) {
+        info->tile_columns = best.first;
+        info->order = best.second;
+        info->ms = best_ms;
+        info->default_ms = default_ms;
+        info->candidates = tried;
+    }
+    return IE_OK;
+}
+
+ie_status ie_plan_check(ie_plan p, void *stream) {
+    if (!p) return set_error("null plan"), IE_ERR_INVALID;
+    return take_device_error(p, (cudaStream_t)stream);
+}
+
+ie_status ie_diag_bounded_wait(double limit_ms, void *stream) {
+    if (!(limit_ms > 0) || limit_ms > 10000) return set_error("limit_ms must be in (0, 10000]"), IE_ERR_INVALID;
+    return bounded_wait_selftest(limit_ms, (cudaStream_t)stream);
 }
 
 ie_status ie_plan_stats_get(ie_plan p, ie_plan_stats *o) {

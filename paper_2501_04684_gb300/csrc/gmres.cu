@@ -1040,6 +1040,7 @@ ie_status ie_solve(ie_plan p, const void *v, void *c, int nrhs, const ie_solve_o
     }
     inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (info) *info = inf;
+    IE_TRY(take_device_error(p, st));   // a translation that gave up a wait voids the solve
     return result;
 }
 

@@ -144,7 +144,8 @@ struct ie_plan_s {
     int *d_err = nullptr;              // device error word of bounded waits
     float2 *d_tmp = nullptr;           // [max_rhs][n] scratch of products
 
-    std::map<int, ie::WorkList> simt_work, tc_work;   // keyed by nrhs
+    std::map<int, ie::WorkList> simt_work, tc_work;   // keyed by nrhs (tensor core: and its tuning)
+    std::map<int, std::pair<int, int>> tc_tuned;      // nrhs -> (tile columns, item order) from ie_plan_tune
     std::vector<void *> allocs;
     size_t bytes = 0;
     double plan_seconds = 0;
@@ -210,6 +211,10 @@ ie_status translate_timed(ie_plan p, int prec, const float2 *X, float2 *Yslab, i
                           const int *gate);
 int simt_tile_columns();
 int tc_tile_columns();
+// runs one bounded device wait on an mbarrier nothing signals (IE_ERR_TIMEOUT expected)
+ie_status bounded_wait_selftest(double limit_ms, cudaStream_t st);
+// synchronises st; IE_ERR_TIMEOUT (and the word cleared) if a translation gave up a wait
+ie_status take_device_error(ie_plan p, cudaStream_t st);
 
 size_t slab_stride(const ie_plan p);   // elements between far-field slabs
 

@@ -63,7 +63,7 @@ constexpr int kEpiBytes = kRing * kTcTileCols * (8 + 4) + kRing * 16;   // colum
 constexpr int kColBytes = 2 * kTcTileCols * 8;                 // gather base pointer of each column, 2 items
 constexpr int kSmemBytes = kStages * kStageBytes + kEpiBytes + kColBytes + 512 /*barriers*/ + 1024 /*alignment*/;
 constexpr uint32_t kTmemCols = 512;
-constexpr uint32_t kSpinLimit = 1u << 24;
+constexpr long long kWaitCycles = 1ll << 31;     // bounded waits give up after ~1 s of SM clock
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -85,14 +85,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait by one thread: false when the limit is hit or the CTA already gave up.
+// Bounded wait by one thread: false when `limit` SM cycles pass without the phase
+// completing (then the CTA's abort flag is raised) or the CTA already gave up.
 // SLEEP = false for the latency-critical single threads (MMA issuer, signaller): they
 // rely on try_wait's own suspension instead of backing off.
 template <bool SLEEP = true>
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          long long limit = kWaitCycles) {
+    const long long t0 = clock64();
+    for (uint32_t i = 0;; ++i) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
+        if (clock64() - t0 > limit) break;
         if (SLEEP && i > 32) __nanosleep(64);
     }
     *abort_flag = 1;
@@ -367,7 +371,8 @@ translate_tc_kernel(const TcArgs a) {
                 for (int s = 0; s < kStages; ++s) {
                     if (armed[s] < 0) continue;
                     const uint32_t ph = (uint32_t)((armed[s] / kStages) & 1);
-                    for (uint32_t w = 0; w < kSpinLimit && !mbar_try_wait(smem_u32(&full[s]), ph); ++w) __nanosleep(64);
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(smem_u32(&full[s]), ph) && clock64() - t0 < kWaitCycles) __nanosleep(64);
                 }
             }
         }
@@ -537,6 +542,36 @@ ie_status set_attr() {
 }  // namespace
 
 int tc_tile_columns() { return kTcTileCols; }
+
+namespace {
+// One thread waits, with the translation kernels' bounded wait, on an mbarrier that
+// nothing arrives on; the wait must give up and report it.
+__global__ void bounded_wait_selftest_kernel(long long limit, int *out) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x != 0) return;
+    abort_flag = 0;
+    mbar_init(smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const bool ok = mbar_wait(smem_u32(&bar), 0, &abort_flag, limit);
+    out[0] = ok ? 0 : 1;
+    out[1] = abort_flag;
+}
+}  // namespace
+
+ie_status bounded_wait_selftest(double limit_ms, cudaStream_t st) {
+    int *d = nullptr;
+    IE_CK(cudaMallocAsync(&d, 2 * sizeof(int), st));
+    const long long limit = (long long)(limit_ms * 2.0e6);   // SM cycles at ~2 GHz
+    bounded_wait_selftest_kernel<<<1, 32, 0, st>>>(limit, d);
+    IE_CK_LAUNCH();
+    int h[2] = {0, 0};
+    IE_CK(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
+    IE_CK(cudaStreamSynchronize(st));
+    IE_CK(cudaFreeAsync(d, st));
+    if (h[0] == 1 && h[1] == 1) return set_error("bounded wait gave up as designed"), IE_ERR_TIMEOUT;
+    return set_error("bounded wait self-test: the wait did not report a timeout"), IE_ERR_CUDA;
+}
 
 ie_status prepare_translate_tc() {
     IE_TRY((set_attr<false, true>()));

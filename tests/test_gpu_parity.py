@@ -235,3 +235,19 @@ def test_multi_rhs_solve_each_matches_alone(tiny):
             st, _ = ie.ie_solve(plan.handle, v[r:r + 1].contiguous(), c1, 1, ie.solve_opts(tol=1e-6))
             assert st == ie.IE_OK
             assert rel_l2(host(c1)[0], both[r]) <= 1e-5
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(tiny):
+    """A device wait on a signal that never comes gives up and reports IE_ERR_TIMEOUT;
+    the context stays usable (a product afterwards is still correct) and a plan whose
+    launches all completed reports IE_OK."""
+    import time
+    t0 = time.perf_counter()
+    assert ie.ie_diag_bounded_wait(50.0) == ie.IE_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 10.0
+    c = W.coefficients(tiny, 1, 210)
+    with plan_for(tiny) as plan:
+        y = empty((1, tiny.n))
+        ie.ie_matvec(plan.handle, ie.IE_FULL, ie.IE_PREC_FP32, dev(c), y, 1)
+        assert ie.ie_plan_check(plan.handle) == ie.IE_OK
+        assert rel_l2(host(y), oracle.operator(tiny, c, "full")) <= TOL

@@ -200,3 +200,20 @@ def test_fp16x3_solve_shell16_true_residual():
     Zx = oracle.operator(p, xs, "full", targets=targets)
     res = np.linalg.norm(Zx - vref[:, rows]) / np.linalg.norm(vref[:, rows])
     assert res <= 1e-5, res
+
+
+def test_autotuner_choice_is_valid_and_products_stay_correct():
+    """ie_plan_tune times 8 configurations, keeps the fastest, and the plan's products
+    with the tuned work lists still match the oracle."""
+    p, c = ragged_problem(seed=430, nrhs=3)
+    ref = oracle.operator(p, c, "full")
+    with plan_for(p, precs=ALL, max_rhs=3) as plan:
+        for prec in (ie.IE_PREC_FP16X3, ie.IE_PREC_BF16X1):
+            info = ie.ie_plan_tune(plan.handle, prec, 3)
+            assert info["tile_columns"] in (128, 112, 96, 64) and info["order"] in (0, 1), info
+            assert info["candidates"] == 8 and 0 < info["ms"] <= info["default_ms"], info
+            y = empty((3, p.n))
+            ie.ie_matvec(plan.handle, ie.IE_FULL, prec, dev(c), y, 3)
+            assert rel_l2(host(y), ref) <= BOUND[prec], _name(prec)
+        with pytest.raises(ie.IEError):
+            ie.ie_plan_tune(plan.handle, ie.IE_PREC_FP32, 1)
