@@ -606,22 +606,25 @@ HEADLINE = "fp16x3"
 HEADLINE_TOL = 1e-5
 
 
-def source_digest(source: str) -> str:
-    """sha256 (16 hex digits) of a kernel source with // comments and blank lines removed,
+def source_digest(*sources: str) -> str:
+    """sha256 (16 hex digits) of kernel sources with // comments and blank lines removed,
     so that editing comments keeps a profile valid while any code change voids it."""
     import hashlib
     import re
-    text = open(os.path.join(ROOT, "paper_2501_04684_gb300", "csrc", source)).read()
-    code = [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
-    return hashlib.sha256("\n".join(ln for ln in code if ln.strip()).encode()).hexdigest()[:16]
+    lines = []
+    for source in sources:
+        text = open(os.path.join(ROOT, "paper_2501_04684_gb300", "csrc", source)).read()
+        lines += [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
+    return hashlib.sha256("\n".join(ln for ln in lines if ln.strip()).encode()).hexdigest()[:16]
 
 
-def profiled_traffic(summary: str, source: str):
+def profiled_traffic(summary: str, *sources: str):
     """DRAM bytes per launch from a committed ncu summary, or None once the kernel code
-    has changed since the counters were taken (the summary records the code digest)."""
+    (its source and the work-list builder in api.cu) has changed since the counters were
+    taken (the summary records the code digest)."""
     try:
         text = open(os.path.join(ROOT, "profiles", summary)).read()
-        digest = source_digest(source)
+        digest = source_digest(*sources, "api.cu")
     except OSError:
         return None
     fields = dict(line.split(": ", 1) for line in text.splitlines() if ": " in line and not line.startswith(("|", " ")))

@@ -157,13 +157,13 @@ ie_status ie_plan_profile(ie_plan plan, int enable);
  * and 64 columns and two work-item orders (largest first; displacement order, which runs
  * the tiles of one group on neighbouring CTAs together) and keeps the fastest for the
  * plan.  Synchronises `stream`; overwrites the plan's scratch.  info (may be NULL): the
- * chosen tile width and order, its time per launch and that of the default (128, 0).
+ * chosen tile width and order, its time per launch and that of the default (128, 1).
  * Errors: IE_ERR_INVALID, IE_ERR_UNSUPPORTED (FP32 or a precision not in the plan). */
 typedef struct {
     int tile_columns;      /* complex columns per work item chosen                       */
     int order;             /* 0: items largest first, 1: displacement order              */
     double ms;             /* its translation time per launch                            */
-    double default_ms;     /* the default's (128 columns, order 0)                       */
+    double default_ms;     /* the default's (128 columns, order 1)                       */
     int candidates;        /* configurations timed                                       */
 } ie_tune_info;
 ie_status ie_plan_tune(ie_plan plan, int prec, int nrhs, ie_tune_info *info, void *stream);

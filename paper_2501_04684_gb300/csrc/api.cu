@@ -356,13 +356,14 @@ size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, i
 
 // Work list of one translation kernel for `nrhs`: every displacement group cut into
 // runs of at most (tile columns / nrhs) pairs; the tensor-core list repeats each run
-// for its three M-blocks and, in order 0, orders runs by size (largest first) for the
-// persistent kernel's static round-robin (order 1 keeps displacement order, so that
-// the tiles of one group run at the same time on neighbouring CTAs).  The tensor-core
-// tile width and order come from ie_plan_tune (default: the full 128 columns, order 0).
+// for its three M-blocks and, in order 1, keeps displacement order, so that the tiles
+// of one group (which share the group's coupling images) run at the same time on
+// neighbouring CTAs of the persistent kernel's static round-robin; order 0 sorts runs by
+// size (largest first).  The tensor-core tile width and order come from ie_plan_tune
+// (default: the full 128 columns, order 1, the fastest on the shells measured).
 ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out) {
     auto &cache = tc ? p->tc_work : p->simt_work;
-    int cols = tc ? tc_tile_columns() : simt_tile_columns(), order = 0;
+    int cols = tc ? tc_tile_columns() : simt_tile_columns(), order = 1;
     if (tc) {
         auto t = p->tc_tuned.find(nrhs);
         if (t != p->tc_tuned.end()) cols = t->second.first, order = t->second.second;
@@ -755,7 +756,7 @@ ie_status ie_plan_tune(ie_plan p, int prec, int nrhs, ie_tune_info *info, void *
     IE_CK(cudaEventCreate(&ev[0]));
     IE_CK(cudaEventCreate(&ev[1]));
     const int cands[] = {128, 112, 96, 64};
-    std::pair<int, int> best{tc_tile_columns(), 0};
+    std::pair<int, int> best{tc_tile_columns(), 1};
     double best_ms = 1e30, default_ms = 0;
     int tried = 0;
     ie_status e = IE_OK;
@@ -774,7 +775,7 @@ ie_status ie_plan_tune(ie_plan p, int prec, int nrhs, ie_tune_info *info, void *
             if (e != IE_OK) break;
             ms *= 0.5f;
             ++tried;
-            if (cols == tc_tile_columns() && order == 0) default_ms = ms;
+            if (cols == tc_tile_columns() && order == 1) default_ms = ms;
             if (ms < best_ms) best_ms = ms, best = {cols, order};
         }
     }

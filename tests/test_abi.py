@@ -111,3 +111,13 @@ def test_symmetry_footprint_and_validation(built):
     with pytest.raises(ie.IEError) as e:
         ie.ie_plan_footprint(_tiny_problem(symmetry=2))
     assert e.value.status == ie.IE_ERR_INVALID
+
+
+def test_diagnostic_and_tuner_argument_checks(built):
+    """Argument errors are reported before any device work (no GPU needed)."""
+    L = ie.lib()
+    assert L.ie_diag_bounded_wait(0.0, None) == ie.IE_ERR_INVALID
+    assert L.ie_diag_bounded_wait(1e6, None) == ie.IE_ERR_INVALID
+    info = ie.ie_tune_info()
+    assert L.ie_plan_tune(None, ie.IE_PREC_FP16X3, 1, ctypes.byref(info), None) == ie.IE_ERR_INVALID
+    assert L.ie_plan_check(None, None) == ie.IE_ERR_INVALID
