@@ -531,6 +531,7 @@ ie_status ie_plan_footprint(const ie_problem *pr, size_t *bytes) {
 }
 
 ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
+    ie::NvtxRange nvtx_range("ie_plan_create");
     auto t0 = std::chrono::steady_clock::now();
     if (!out) return set_error("null out"), IE_ERR_INVALID;
     *out = nullptr;
@@ -743,6 +744,7 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
 }
 
 ie_status ie_plan_tune(ie_plan p, int prec, int nrhs, ie_tune_info *info, void *stream) {
+    ie::NvtxRange nvtx_range("ie_plan_tune");
     if (!p) return set_error("null plan"), IE_ERR_INVALID;
     IE_TRY(check_prec(p, prec));
     IE_TRY(check_rhs(p, nrhs));
@@ -853,6 +855,7 @@ ie_status ie_plan_destroy(ie_plan p) {
 }
 
 ie_status ie_matvec(ie_plan p, int which, int prec, const void *c, void *y, int nrhs, void *stream) {
+    ie::NvtxRange nvtx_range("ie_matvec");
     if (!p || !c || !y) return set_error("null argument"), IE_ERR_INVALID;
     if (which < IE_FAR || which > IE_FULL) return set_error("bad which %d", which), IE_ERR_INVALID;
     IE_TRY(check_rhs(p, nrhs));
@@ -868,6 +871,7 @@ ie_status ie_aggregate(ie_plan p, const void *c, void *X, int nrhs, void *stream
 }
 
 ie_status ie_translate(ie_plan p, int prec, const void *X, void *Y, int nrhs, void *stream) {
+    ie::NvtxRange nvtx_range("ie_translate");
     if (!p || !X || !Y) return set_error("null argument"), IE_ERR_INVALID;
     IE_TRY(check_rhs(p, nrhs));
     IE_TRY(check_prec(p, prec));

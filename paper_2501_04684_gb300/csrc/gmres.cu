@@ -913,6 +913,7 @@ ie_status ie_solver_start(ie_solver s, const void *v, void *c, void *stream) {
 }
 
 ie_status ie_solver_advance(ie_solver s, int cycles, void *stream) {
+    ie::NvtxRange nvtx_range("ie_solver_advance");
     if (!s || cycles < 0) return set_error("bad argument"), IE_ERR_INVALID;
     cudaStream_t st = (cudaStream_t)stream;
     for (int c = 0; c < cycles; ++c) {
@@ -950,6 +951,7 @@ ie_status ie_solver_poll(ie_solver s, int *done, ie_solve_info *info) {
 
 ie_status ie_solve(ie_plan p, const void *v, void *c, int nrhs, const ie_solve_opts *opts, ie_solve_info *info,
                    void *stream) {
+    ie::NvtxRange nvtx_range("ie_solve");
     auto t0 = std::chrono::steady_clock::now();
     if (!p || !v || !c) return set_error("null argument"), IE_ERR_INVALID;
     ie_solve_opts o;

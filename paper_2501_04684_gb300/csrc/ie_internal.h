@@ -10,9 +10,21 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ie.h"
 
 namespace ie {
+
+// Host-side NVTX range for the duration of a scope (seen by Nsight tools; a no-op
+// without one attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 
 constexpr int kLattice = 4;
 constexpr int kSites = 64;          // 4^3 dipole sites per box
