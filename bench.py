@@ -607,24 +607,29 @@ HEADLINE_TOL = 1e-5
 
 
 def source_digest(*sources: str) -> str:
-    """sha256 (16 hex digits) of kernel sources with // comments and blank lines removed,
-    so that editing comments keeps a profile valid while any code change voids it."""
+    """sha256 (16 hex digits) of kernel code with // comments and blank lines removed, so
+    that editing comments keeps a profile valid while any code change voids it.  A source
+    "file.cu:signature" stands for the one function of file.cu that starts with signature."""
     import hashlib
     import re
     lines = []
     for source in sources:
-        text = open(os.path.join(ROOT, "paper_2501_04684_gb300", "csrc", source)).read()
+        name, _, sig = source.partition(":")
+        text = open(os.path.join(ROOT, "paper_2501_04684_gb300", "csrc", name)).read()
+        if sig:
+            i = text.index(sig)
+            text = text[i:text.index("\n}\n", i) + 3]
         lines += [re.sub(r"//.*$", "", ln).rstrip() for ln in text.splitlines()]
     return hashlib.sha256("\n".join(ln for ln in lines if ln.strip()).encode()).hexdigest()[:16]
 
 
 def profiled_traffic(summary: str, *sources: str):
     """DRAM bytes per launch from a committed ncu summary, or None once the kernel code
-    (its source and the work-list builder in api.cu) has changed since the counters were
-    taken (the summary records the code digest)."""
+    (its source and the work-list builder, api.cu's work_list) has changed since the
+    counters were taken (the summary records the code digest)."""
     try:
         text = open(os.path.join(ROOT, "profiles", summary)).read()
-        digest = source_digest(*sources, "api.cu")
+        digest = source_digest(*sources, "api.cu:ie_status work_list(")
     except OSError:
         return None
     fields = dict(line.split(": ", 1) for line in text.splitlines() if ": " in line and not line.startswith(("|", " ")))
