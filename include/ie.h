@@ -23,7 +23,8 @@
  *  - Dipole-space vectors are [rhs][n_boxes][192] complex64.
  *  - All calls are stream-ordered on `stream` (a cudaStream_t passed as void*,
  *    NULL = legacy default stream) and return without waiting, except
- *    ie_plan_create, ie_plan_destroy and ie_solve, which synchronise it.
+ *    ie_plan_create, ie_plan_destroy, ie_plan_tune, ie_plan_check,
+ *    ie_diag_bounded_wait and ie_solve, which synchronise it.
  *  - A plan owns all of its device memory.  Nothing throws across the ABI; every
  *    call returns an ie_status, and ie_last_error() gives a message for the
  *    calling thread's last failure.
