@@ -11,7 +11,7 @@ import pytest
 import oracle
 import paper_2501_04684_gb300 as ie
 import workloads as W
-from gpu_util import dev, empty, host, plan_for, rel_l2
+from gpu_util import dev, empty, host, plan_for, rel_l2, torch_cuda
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-6
@@ -251,3 +251,47 @@ def test_bounded_wait_reports_timeout_and_context_survives(tiny):
         ie.ie_matvec(plan.handle, ie.IE_FULL, ie.IE_PREC_FP32, dev(c), y, 1)
         assert ie.ie_plan_check(plan.handle) == ie.IE_OK
         assert rel_l2(host(y), oracle.operator(tiny, c, "full")) <= TOL
+
+
+def test_solve_not_converged_reports_status_and_best_iterate(tiny):
+    """Stopping at max_iters returns IE_ERR_NOT_CONVERGED with the iteration count and
+    the residual reached, and the iterate written is better than x = 0."""
+    kh, pol = W.plane_wave_spec(1)
+    v = oracle.plane_wave_rhs(tiny, kh, pol)
+    with plan_for(tiny) as plan:
+        x = empty((1, tiny.n))
+        st, info = ie.ie_solve(plan.handle, dev(v), x, 1, ie.solve_opts(tol=1e-12, max_iters=3, restart=50))
+        assert st == ie.IE_ERR_NOT_CONVERGED
+        assert info["converged"] == 0 and info["iterations"] == 3 and 0 < info["relres"] < 1, info
+        xs = host(x)
+    res = np.linalg.norm(oracle.operator(tiny, xs, "full")[0] - v[0]) / np.linalg.norm(v[0])
+    assert abs(res - info["relres"]) <= 1e-3 * max(res, 1e-12) + 1e-6 and res < 1
+
+
+def test_stepped_solver_matches_ie_solve(tiny):
+    """The solver object (create / start / advance one cycle at a time / poll) reaches
+    the same solution as ie_solve."""
+    kh, pol = W.plane_wave_spec(2, seed=211)
+    v = dev(oracle.plane_wave_rhs(tiny, kh, pol))
+    opts = ie.solve_opts(tol=1e-6, restart=4)              # several restart cycles
+    with plan_for(tiny, max_rhs=2) as plan:
+        x_ref = empty((2, tiny.n))
+        st, info_ref = ie.ie_solve(plan.handle, v, x_ref, 2, opts)
+        assert st == ie.IE_OK
+        s = ie.ie_solver_create(plan.handle, 2, opts)
+        try:
+            x = empty((2, tiny.n))
+            ie.ie_solver_start(s, v, x)
+            cycles = 0
+            while True:
+                ie.ie_solver_advance(s, 1)
+                cycles += 1
+                torch_cuda().cuda.synchronize()
+                done, info = ie.ie_solver_poll(s)
+                if done or cycles > 100:
+                    break
+            assert done and info["converged"] == 1 and cycles > 1, (cycles, info)
+            assert info["iterations"] == info_ref["iterations"]
+            assert rel_l2(host(x), host(x_ref)) <= 1e-6
+        finally:
+            ie.ie_solver_destroy(s)
