@@ -43,6 +43,12 @@ def parse():
     ap.add_argument("--workload", default="shell16", choices=["shell16", "shell32", "batch64", "serve"],
                     help="shell16 is the headline line; the others measure the precision, batching and "
                          "serving workloads")
+    ap.add_argument("--lfb", default=None, choices=["lfb8", "lfb256"],
+                    help="shell16 only: the same geometry with box edge lambda/8 or lambda/256 "
+                         "(low-frequency regime)")
+    ap.add_argument("--mapped", action="store_true",
+                    help="shell16 only: P built on the GPU by the mapping construction (eq. 11) from seeded "
+                         "point-dipole basis functions instead of random")
     ap.add_argument("--symmetry", type=int, default=0, choices=[0, 1],
                     help="1: symmetry-compressed coupling store (one block per sorted |d|)")
     ap.add_argument("--requests", type=int, default=12, help="serve: requests per run")
@@ -293,6 +299,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if (args.lfb is not None or args.mapped) and args.workload != "shell16":
+        raise SystemExit("--lfb and --mapped apply to the shell16 workload only")
     ctx = Ctx(args)
     runner = {"shell16": run_shell16, "shell32": run_shell32, "batch64": run_batch64, "serve": run_serve}
     result = runner[args.workload](ctx)
@@ -306,8 +314,13 @@ def main():
 def run_shell16(ctx):
     args, ie, W, torch, np = ctx.args, ctx.ie, ctx.W, ctx.torch, ctx.np
     world, stream = ctx.world, ctx.stream
-    p = W.shell16()
-    p.alpha = W.alpha_for("shell16")
+    p = W.shell16() if args.lfb is None else W.lfb(W.shell16(), args.lfb)
+    workload = WORKLOAD if args.lfb is None else WORKLOAD.replace("a=lambda/4", f"a=lambda/{round(1 / p.a)}")
+    mapping = None
+    if args.mapped:
+        p, mapping = map_shell(ctx, p)
+        workload = workload.replace("basis unknowns", "basis unknowns, P mapped from point-dipole functions")
+    p.alpha = W.alpha_for(p.name)
     precs = [ie.IE_PREC_FP32, ie.IE_PREC_BF16X3, ie.IE_PREC_FP16X3, ie.IE_PREC_BF16X1, ie.IE_PREC_FP16X1]
     t0 = time.perf_counter()
     plan = ie.Plan(ie.problem_from(p, ie.precmask(*precs), symmetry=args.symmetry), stream)
@@ -354,6 +367,9 @@ def run_shell16(ctx):
     pairs = st["n_far_pairs"]
     roofline = tc_roofline(pairs, far["fp16x3"]["translate_kernel_ms"], 3, "translate_tc_fp16x3_shell16.md",
                            "translate_tc_kernel<fp16,x3>")
+    if args.lfb is not None and roofline.get("traffic") is not None:
+        roofline["traffic_note"] = ("captured at a=lambda/4: the box edge changes only the values, not the "
+                                    "work list or the bytes moved")
     simt_ach = pairs * 8 * 192 * 192 / (far["fp32"]["translate_kernel_ms"] / 1e3) / 1e12
     roofline_fp32 = {"bound": "alu", "achieved": simt_ach, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": simt_ach / FP32_SIMT_PEAK_TFLOPS, "kernel": "translate_simt_kernel",
@@ -365,7 +381,7 @@ def run_shell16(ctx):
         "metric": METRIC, "value": head["solves_per_s"], "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": hp["dtype"], "data": "synthetic",
-        "config": {"workload": WORKLOAD, "path": HEADLINE, "path_desc": hp["desc"], "tol": hp["opts"].tol,
+        "config": {"workload": workload, "path": HEADLINE, "path_desc": hp["desc"], "tol": hp["opts"].tol,
                    "nrhs": 1, "symmetry": args.symmetry,
                    "l2": ("no flush needed: each product streams >= 4.9 GB of coupling blocks (> 129 MB L2)"
                           if not args.symmetry else
@@ -385,10 +401,38 @@ def run_shell16(ctx):
         "roofline": roofline,
         "roofline_fp32": roofline_fp32,
     }
+    if mapping is not None:
+        result["mapping"] = mapping
     if ctx.rank == 0 and world == 1:
-        result["cpu_baseline"] = cpu_baseline(p, oracle_products("shell16", HEADLINE_TOL) or head["matvecs"])
+        result["cpu_baseline"] = cpu_baseline(p, oracle_products(p.name, HEADLINE_TOL) or head["matvecs"])
     plan.close()
     return result
+
+
+def map_shell(ctx, p):
+    """P of the shell from seeded point-dipole functions by ie_map_basis (host in, host out,
+    timed with the copies), and the map kernel's FP64 roofline."""
+    import dataclasses
+    ie, W, np = ctx.ie, ctx.W, ctx.np
+    fun_off, pos, mom = W.point_dipole_basis(p.nb, W.SEED_MAPPED["shell16"], a=p.a)
+    ie.ie_map_basis(p.k, p.eta, p.a, fun_off[:9], pos, mom, stream=ctx.stream)          # warm-up
+    times = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        P, res = ie.ie_map_basis(p.k, p.eta, p.a, fun_off, pos, mom, stream=ctx.stream)
+        times.append(time.perf_counter() - t0)
+    n_fun = len(fun_off) - 1
+    t = sorted(times)[1]
+    # algorithmic FP64 work per function: C = A^+ B (192 x 384 complex MACs) and the
+    # residual A C - B (the same), 8 real flops per complex MAC
+    flops = n_fun * 2 * 192 * 384 * 8
+    ach = flops / t / 1e12
+    q = dataclasses.replace(p, P=P, name=p.name + "_mapped")
+    return q, {"functions": n_fun, "dipoles": int(fun_off[-1]), "ms": t * 1e3, "functions_per_s": n_fun / t,
+               "residual_on_S_max": float(res.max()), "residual_on_S_median": float(np.median(res)),
+               "roofline": {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                            "note": "whole call: host copies of 124 MB of P and the one-off QR included"}}
 
 
 def run_shell32(ctx):
@@ -602,6 +646,7 @@ def solve_paths(ie) -> dict:
     }
 
 
+FP64_PEAK_TFLOPS = 1.25    # GB300 FP64 rate (non-tensor); far below its FP32 and tensor rates
 HEADLINE = "fp16x3"
 HEADLINE_TOL = 1e-5
 

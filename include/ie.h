@@ -24,7 +24,7 @@
  *  - All calls are stream-ordered on `stream` (a cudaStream_t passed as void*,
  *    NULL = legacy default stream) and return without waiting, except
  *    ie_plan_create, ie_plan_destroy, ie_plan_tune, ie_plan_check,
- *    ie_diag_bounded_wait and ie_solve, which synchronise it.
+ *    ie_diag_bounded_wait, ie_solve and ie_map_basis, which synchronise it.
  *  - A plan owns all of its device memory.  Nothing throws across the ABI; every
  *    call returns an ie_status, and ie_last_error() gives a message for the
  *    calling thread's last failure.
@@ -301,6 +301,55 @@ ie_status ie_solver_advance(ie_solver s, int cycles, void *stream);
 ie_status ie_solver_poll(ie_solver s, int *done, ie_solve_info *info);
 
 ie_status ie_solver_destroy(ie_solver s);
+
+/* ---- mapping construction (§2.1): the rows of P_b from subdomain basis functions --
+ *
+ * A basis function made of point dipoles radiates B_f, its field at N_s sample
+ * points r_l on a sphere S about its box centre (eq. 4, eq. 10).  The 192 uniform
+ * dipoles radiate A (3 N_s x 192) there.  Eq. 11 takes the least-squares fit
+ * C_f = A^+ B_f (eq. 9-10: the uniform dipoles whose field best matches the
+ * function's on S), and row f of P_b is C_f^T: x_b = P_b^T c_b is then Alg. 1.
+ * The same rows serve the inverse mapping of eq. 15-17 when the test functions
+ * are the basis functions: D(R) = D(-R) = D(R)^T makes the tested fields of the
+ * virtual dipoles B_f^T, and (A^T)^+ = (A^+)^T, so Alg. 3 reads r_b = P_b y_b.
+ *
+ * S has radius sample_radius * box_edge; its samples form the spherical Fibonacci
+ * lattice: polar angle arccos(1 - (2l+1)/N_s), azimuth 2 pi l / golden ratio,
+ * l = 0 .. N_s-1.  A^+ comes from a Householder QR of A in FP64 (A has full column
+ * rank for N_s >= 64; its condition number is about 1e7 at N_s = 128), and the
+ * fields and products are FP64 throughout.
+ *
+ * tikhonov = 0 gives eq. 11's plain pseudo-inverse.  Its coefficients oscillate with
+ * norms ~100x those of the function's field, and the far product then cancels:
+ * FP32 evaluation loses about two more digits.  tikhonov = t > 0 solves instead
+ * min ||A C - B||^2 + (t ||A||_F)^2 ||C||^2 (QR of [A; t ||A||_F I]); t = 1e-5 cuts
+ * the coefficient norms ~25x at an unchanged field error outside S. */
+typedef struct {
+    double k, eta, box_edge;   /* as in ie_problem                                     */
+    int lattice;               /* dipoles per box edge; must be 4                      */
+    int n_samples;             /* N_s, 64 .. 256 (the paper: N_s = 2 N_d = 128)        */
+    double sample_radius;      /* radius of S in box edges, > sqrt(3)/2 so that S
+                                  encloses the box (the paper: 1.5)                   */
+    double tikhonov;           /* >= 0, relative to ||A||_F; 0 = eq. 11 as printed     */
+} ie_mapping_spec;
+
+/* Map n_fun basis functions.  All pointers are HOST memory; the call copies them
+ * to the device, runs there and copies the results back before returning.
+ *   fun_off   n_fun + 1 offsets, fun_off[0] = 0, non-decreasing: function f owns
+ *             point dipoles fun_off[f] .. fun_off[f+1]-1 (none: a zero row)
+ *   pos       fun_off[n_fun] x 3 doubles, dipole positions relative to the centre
+ *             of the function's box; each strictly inside S
+ *   mom       fun_off[n_fun] x 3 complex128 (re, im interleaved) dipole moments
+ *   P         out: n_fun x 192 complex128, row f = C_f^T (rows in the order given,
+ *             so functions listed box by box pack as ie_problem.P)
+ *   residual  out, may be NULL: n_fun doubles ||A C_f - B_f|| / ||B_f||, the
+ *             field mismatch on S (0 for a function without dipoles)
+ * Errors: IE_ERR_INVALID for a bad spec, offsets, a non-finite value or a dipole
+ * outside S (nothing runs); IE_ERR_OOM / IE_ERR_CUDA from the device; IE_ERR_INVALID
+ * also if A is numerically rank deficient (a zero Householder column). */
+ie_status ie_map_basis(const ie_mapping_spec *spec, int64_t n_fun, const int64_t *fun_off,
+                       const double *pos, const double *mom, double *P, double *residual,
+                       void *stream);
 
 /* ---- diagnostics -------------------------------------------------------------- */
 const char *ie_status_str(ie_status s);

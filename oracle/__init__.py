@@ -20,11 +20,22 @@ What each function follows (paper sections / equations / algorithms):
   far_matvec_grouped    Alg. 2 grouped by displacement: E_j += G_w P_i per far pair
   gmres                 restarted GMRES without preconditioning (§5), FP64
   plane_wave_rhs        unit plane-wave excitation (§5) tested with P: v = P e
+  fibonacci_sphere      sample points of the field-matching sphere S, §2.1
+  mapping_matrix        A of eq. 10: fields of the uniform dipoles at the samples on S
+  function_fields       B_k of eq. 10: fields of one point-dipole basis function on S
+  map_basis             eq. 11, C_k = A^+ B_k (least squares), rows of P_b
+  inverse_map_fields    eq. 15-17 literally: Q = (A^T)^+ E, tested on a basis function
+  point_dipole_far      far interactions of the point-dipole basis functions themselves
+                        (the original system that the mapping replaces), brute force
 
 Parity status: every function above is pinned by the CPU tests in
 tests/test_oracle_pins.py (closed-form Hertzian dipole field, reciprocity,
 translation invariance, counts printed in §2.2, brute force vs grouped, dense
-LU vs GMRES, explicit pure-Python construction on a tiny case).
+LU vs GMRES, explicit pure-Python construction on a tiny case; for the mapping:
+the Fibonacci lattice's closed form, exact reproduction of a uniform dipole,
+superposition, the least-squares normal equations, the far field of the
+equivalent dipoles against the source's own field, and the inverse mapping
+computed literally against the transpose of the forward one).
 """
 from __future__ import annotations
 
@@ -67,6 +78,8 @@ def _load():
         L.or_coupling_block.argtypes = [d, d, d, i, p, p]
         L.or_coupling_blocks.argtypes = [d, d, d, i, i64, p, p]
         L.or_plane_wave.argtypes = [d, d, i, i, i64, p, i64, p, p, p]
+        L.or_point_dipole_far.argtypes = [d, d, i64, p, p, p, p, p, p, p]
+        L.or_point_fields.argtypes = [d, d, i64, p, i64, p, p, p]
         L.or_num_threads.restype = i
         _lib = L
     return _lib
@@ -404,3 +417,121 @@ def operator_norm(p, iters: int = 30, seed: int = 7, matvec=None, log=None):
         if log:
             log(f"power it {it}: sigma {sigma:.6e} ({time.time() - t0:.1f}s)")
     return float(sigma), hist
+
+
+# ---------------------------------------------------------------- §2.1 mapping, eq. 9-11 / 15-17
+GOLDEN_RATIO = 0.5 + 0.5 * 5.0 ** 0.5
+
+
+def fibonacci_sphere(n: int, radius: float) -> np.ndarray:
+    """(n, 3) spherical Fibonacci lattice of §2.1 about the box centre: point l = 0..n-1 at
+    polar angle arccos(1 - (2l+1)/n) and azimuth 2 pi l / golden ratio.  (The printed
+    formulas give the two angles the other names; the arccos one is the polar angle.)"""
+    l = np.arange(n, dtype=np.float64)
+    polar = np.arccos(1.0 - (2.0 * l + 1.0) / n)
+    azim = 2.0 * np.pi * l / GOLDEN_RATIO
+    return radius * np.stack([np.sin(polar) * np.cos(azim), np.sin(polar) * np.sin(azim), np.cos(polar)], 1)
+
+
+def lattice_offsets(a: float, L: int) -> np.ndarray:
+    """(L^3, 3) uniform dipole positions relative to their box centre (site order of site_positions)."""
+    pos = np.zeros((1, L ** 3, 3))
+    ijk = np.zeros((1, 3), dtype=np.int32)
+    _load().or_site_positions(a, L, 1, 1, _ptr(ijk), _ptr(pos))
+    return pos[0]
+
+
+def mapping_matrix(k: float, eta: float, a: float, L: int, n_samples: int, radius_rel: float = 1.5):
+    """A of eq. 10, (3 n_samples, 3 L^3): entry (3l + alpha, 3j + beta) is the alpha component
+    of the field at sample l on S (radius radius_rel * a) of a unit beta-directed dipole at
+    uniform site j.  Returns (A, samples)."""
+    S = fibonacci_sphere(n_samples, radius_rel * a)
+    sites = lattice_offsets(a, L)
+    A = np.zeros((3 * n_samples, 3 * len(sites)), dtype=np.complex128)
+    for l, r in enumerate(S):
+        for j, q in enumerate(sites):
+            A[3 * l:3 * l + 3, 3 * j:3 * j + 3] = dyad(k, eta, r - q)
+    return A, S
+
+
+def point_fields(k: float, eta: float, obs, src, mom) -> np.ndarray:
+    """(n_obs, 3) field at obs of point dipoles (src (n, 3), complex moments mom (n, 3)):
+    eq. 4 with the integral a sum, brute force in C."""
+    obs = np.ascontiguousarray(obs, dtype=np.float64).reshape(-1, 3)
+    src = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, 3)
+    m = _c128(np.asarray(mom).reshape(-1, 3))
+    out = np.zeros((obs.shape[0], 3), dtype=np.complex128)
+    _load().or_point_fields(k, eta, obs.shape[0], _ptr(obs), src.shape[0], _ptr(src), _ptr(m), _ptr(out))
+    return out
+
+
+def function_fields(k: float, eta: float, samples, pos, mom) -> np.ndarray:
+    """B_k of eq. 10 for a basis function made of point dipoles (positions pos (m, 3)
+    relative to the box centre, complex moments mom (m, 3)): its field at the samples,
+    stacked (3 n_samples,)."""
+    return point_fields(k, eta, samples, pos, mom).reshape(-1)
+
+
+def map_basis(k, eta, a, L, n_samples, radius_rel, fun_off, pos, mom, tikhonov: float = 0.0):
+    """Eq. 11 for every basis function: C_k = A^+ B_k, the least-squares coefficients of
+    the uniform dipoles whose field best matches the function's field on S (eq. 9-10).
+    Function f owns point dipoles fun_off[f] .. fun_off[f+1]-1.  Returns (P, residual):
+    P (n_fun, 3 L^3) with row f = C_f^T, residual[f] = ||A C_f - B_f|| / ||B_f||.
+    tikhonov = t > 0 (not in the paper) adds (t ||A||_F)^2 ||C_k||^2 to the squared misfit,
+    i.e. the least-squares problem [A; t ||A||_F I] C_k ~ [B_k; 0]."""
+    A, S = mapping_matrix(k, eta, a, L, n_samples, radius_rel)
+    n_fun = len(fun_off) - 1
+    mom = np.asarray(mom, dtype=np.complex128).reshape(-1, 3)
+    pos = np.asarray(pos, dtype=np.float64).reshape(-1, 3)
+    B = np.zeros((A.shape[0], n_fun), dtype=np.complex128)
+    for f in range(n_fun):
+        lo, hi = int(fun_off[f]), int(fun_off[f + 1])
+        if hi > lo:
+            B[:, f] = function_fields(k, eta, S, pos[lo:hi], mom[lo:hi])
+    if tikhonov > 0:
+        lam = tikhonov * np.linalg.norm(A)
+        nu = A.shape[1]
+        C = np.linalg.lstsq(np.vstack([A, lam * np.eye(nu)]), np.vstack([B, np.zeros((nu, n_fun))]), rcond=None)[0]
+    else:
+        C = np.linalg.lstsq(A, B, rcond=None)[0]
+    nb = np.linalg.norm(B, axis=0)
+    res = np.where(nb > 0, np.linalg.norm(A @ C - B, axis=0) / np.where(nb > 0, nb, 1.0), 0.0)
+    return C.T.copy(), res
+
+
+def inverse_map_fields(k, eta, a, L, n_samples, radius_rel, E, pos, mom) -> complex:
+    """Eq. 15-17 as written, for one test function: the virtual dipoles on S get the
+    coefficients Q = (A^T)^+ E that best reproduce the fields E (3 L^3,) at the uniform
+    sites (eq. 16-17); their field is then tested on the function (point dipoles pos, mom):
+    sum over its dipoles of mom . E_vd(pos) with E_vd from eq. 15."""
+    A, S = mapping_matrix(k, eta, a, L, n_samples, radius_rel)
+    Q = np.linalg.lstsq(A.T, np.asarray(E, dtype=np.complex128), rcond=None)[0]
+    total = 0.0 + 0.0j
+    for x, p in zip(np.atleast_2d(pos), np.atleast_2d(np.asarray(mom, dtype=np.complex128))):
+        field = np.zeros(3, dtype=np.complex128)
+        for l, r in enumerate(S):
+            field += dyad(k, eta, x - r) @ Q[3 * l:3 * l + 3]
+        total += p @ field
+    return total
+
+
+def point_dipole_far(p, fun_off, pos, mom, c) -> np.ndarray:
+    """Far part of the original subdomain system for point-dipole basis functions (box b's
+    functions are listed in box order, p.nb[b] of them; pos relative to each box centre):
+    y_f = sum over dipoles d of f of mom_d . E(r_d), E the field of c_g-weighted dipoles of
+    every function g in a box at Chebyshev distance >= 2 (eq. 3-4 with point sources)."""
+    fun_off = np.ascontiguousarray(fun_off, dtype=np.int64)
+    n_fun = len(fun_off) - 1
+    fun_box = np.repeat(np.arange(p.n_boxes, dtype=np.int32), np.asarray(p.nb, dtype=np.int64))
+    assert len(fun_box) == n_fun
+    ijk = np.ascontiguousarray(p.box_ijk, dtype=np.int32)
+    centre = p.a * (ijk.astype(np.float64) + 0.5 - p.G / 2.0)
+    counts = np.diff(fun_off)
+    dip_box = np.repeat(fun_box, counts)
+    absolute = np.ascontiguousarray(np.asarray(pos, dtype=np.float64).reshape(-1, 3) + centre[dip_box])
+    m = _c128(np.asarray(mom).reshape(-1, 3))
+    cc = _c128(np.asarray(c).reshape(-1))
+    out = np.zeros(n_fun, dtype=np.complex128)
+    _load().or_point_dipole_far(p.k, p.eta, n_fun, _ptr(fun_off), _ptr(fun_box), _ptr(ijk), _ptr(absolute),
+                                _ptr(m), _ptr(cc), _ptr(out))
+    return out

@@ -201,3 +201,88 @@ void or_plane_wave(double k, double a, int L, int G, int64_t nbox, const int32_t
                 }
             }
 }
+
+/*
+ * Far-zone interactions of point-dipole subdomain basis functions by brute force: the
+ * original system that the mapping of §2.1 replaces (eq. 3-4 with point sources,
+ * tested on the basis functions themselves).  Function f (box fun_box[f]) owns dipoles
+ * fun_off[f] .. fun_off[f+1]-1 at absolute positions pos and complex moments mom.
+ *   out[f] = sum over dipoles d of f of  mom_d . sum over dipoles e of functions g whose
+ *            box is at Chebyshev distance >= 2 from f's box of  D(r_d - r_e) (c_g mom_e)
+ * c, out: [n_fun] complex.
+ */
+void or_point_dipole_far(double k, double eta, int64_t n_fun, const int64_t *fun_off, const int32_t *fun_box,
+                         const int32_t *ijk, const double *pos, const double *mom, const double *c, double *out) {
+    int64_t nd = fun_off[n_fun];
+    double *w = (double *)malloc(sizeof(double) * 6 * (size_t)(nd > 0 ? nd : 1));
+    int32_t *dbox = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nd > 0 ? nd : 1));
+    for (int64_t g = 0; g < n_fun; ++g)
+        for (int64_t e = fun_off[g]; e < fun_off[g + 1]; ++e) {
+            dbox[e] = fun_box[g];
+            for (int b = 0; b < 3; ++b) {
+                double mr = mom[6 * e + 2 * b], mi = mom[6 * e + 2 * b + 1];
+                w[6 * e + 2 * b] = c[2 * g] * mr - c[2 * g + 1] * mi;
+                w[6 * e + 2 * b + 1] = c[2 * g] * mi + c[2 * g + 1] * mr;
+            }
+        }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t f = 0; f < n_fun; ++f) {
+        const int32_t *tf = ijk + 3 * fun_box[f];
+        double acc_r = 0.0, acc_i = 0.0;
+        for (int64_t d = fun_off[f]; d < fun_off[f + 1]; ++d) {
+            double E[6] = {0, 0, 0, 0, 0, 0};
+            for (int64_t e = 0; e < nd; ++e) {
+                const int32_t *sb = ijk + 3 * dbox[e];
+                int cheb = 0;
+                for (int q = 0; q < 3; ++q) {
+                    int dd = abs(tf[q] - sb[q]);
+                    if (dd > cheb) cheb = dd;
+                }
+                if (cheb < 2) continue;
+                double R[3] = {pos[3 * d] - pos[3 * e], pos[3 * d + 1] - pos[3 * e + 1], pos[3 * d + 2] - pos[3 * e + 2]};
+                double D[18];
+                or_dyad(k, eta, R, D);
+                for (int al = 0; al < 3; ++al)
+                    for (int be = 0; be < 3; ++be) {
+                        double dr = D[2 * (3 * al + be)], di = D[2 * (3 * al + be) + 1];
+                        double xr = w[6 * e + 2 * be], xi = w[6 * e + 2 * be + 1];
+                        E[2 * al] += dr * xr - di * xi;
+                        E[2 * al + 1] += dr * xi + di * xr;
+                    }
+            }
+            for (int al = 0; al < 3; ++al) {
+                double mr = mom[6 * d + 2 * al], mi = mom[6 * d + 2 * al + 1];
+                acc_r += mr * E[2 * al] - mi * E[2 * al + 1];
+                acc_i += mr * E[2 * al + 1] + mi * E[2 * al];
+            }
+        }
+        out[2 * f] = acc_r;
+        out[2 * f + 1] = acc_i;
+    }
+    free(w);
+    free(dbox);
+}
+
+/* Field of point dipoles at observation points (eq. 4 with point sources):
+ * out[o] = sum_s D(obs_o - src_s) mom_s.  obs: [n_obs][3], src: [n_src][3],
+ * mom: [n_src][3] complex, out: [n_obs][3] complex (overwritten). */
+void or_point_fields(double k, double eta, int64_t n_obs, const double *obs, int64_t n_src, const double *src,
+                     const double *mom, double *out) {
+#pragma omp parallel for schedule(static)
+    for (int64_t o = 0; o < n_obs; ++o) {
+        double E[6] = {0, 0, 0, 0, 0, 0};
+        for (int64_t s = 0; s < n_src; ++s) {
+            double R[3] = {obs[3 * o] - src[3 * s], obs[3 * o + 1] - src[3 * s + 1], obs[3 * o + 2] - src[3 * s + 2]};
+            double D[18];
+            or_dyad(k, eta, R, D);
+            for (int al = 0; al < 3; ++al)
+                for (int be = 0; be < 3; ++be) {
+                    double dr = D[2 * (3 * al + be)], di = D[2 * (3 * al + be) + 1];
+                    double xr = mom[6 * s + 2 * be], xi = mom[6 * s + 2 * be + 1];
+                    E[2 * al] += dr * xr - di * xi;
+                    E[2 * al + 1] += dr * xi + di * xr;
+                }
+        }
+        for (int i = 0; i < 6; ++i) out[6 * o + i] = E[i];
+    }
+}

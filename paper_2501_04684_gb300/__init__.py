@@ -31,7 +31,7 @@ EXPORTED = [
     "ie_solve_opts_default", "ie_solve", "ie_solver_create", "ie_solver_footprint", "ie_solver_start",
     "ie_solver_advance", "ie_solver_poll", "ie_solver_destroy", "ie_status_str", "ie_last_error", "ie_version",
     "ie_plan_profile", "ie_kernel_launches", "ie_translate_noalloc", "ie_plan_check", "ie_diag_bounded_wait",
-    "ie_plan_tune",
+    "ie_plan_tune", "ie_map_basis",
 ]
 
 
@@ -62,6 +62,12 @@ class ie_plan_stats(ctypes.Structure):
 class ie_tune_info(ctypes.Structure):
     _fields_ = [("tile_columns", ctypes.c_int), ("order", ctypes.c_int), ("ms", ctypes.c_double),
                 ("default_ms", ctypes.c_double), ("candidates", ctypes.c_int)]
+
+
+class ie_mapping_spec(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_double), ("eta", ctypes.c_double), ("box_edge", ctypes.c_double),
+                ("lattice", ctypes.c_int), ("n_samples", ctypes.c_int), ("sample_radius", ctypes.c_double),
+                ("tikhonov", ctypes.c_double)]
 
 
 class ie_solve_opts(ctypes.Structure):
@@ -118,6 +124,7 @@ def lib() -> ctypes.CDLL:
     L.ie_plan_check.argtypes = [vp, vp]
     L.ie_diag_bounded_wait.argtypes = [ctypes.c_double, vp]
     L.ie_plan_tune.argtypes = [vp, i, i, P(ie_tune_info), vp]
+    L.ie_map_basis.argtypes = [P(ie_mapping_spec), ctypes.c_int64, vp, vp, vp, vp, vp, vp]
     for name in EXPORTED:          # every declared symbol must resolve
         getattr(L, name)
     _lib = L
@@ -289,6 +296,29 @@ def ie_coupling_blocks(plan, d, out, stream=None):
     _need(out, d.shape[0] * NU * NU, "out")
     return _check(lib().ie_coupling_blocks(plan, d.ctypes.data, d.shape[0], _ptr(out), _stream(stream)),
                   "ie_coupling_blocks")
+
+
+def ie_map_basis(k, eta, box_edge, fun_off, pos, mom, n_samples=128, sample_radius=1.5, lattice=4,
+                 tikhonov=0.0, residual=True, stream=None):
+    """Rows of P for point-dipole basis functions (host arrays in, host arrays out).
+
+    fun_off (n_fun+1,) int64; pos (m, 3) float64 relative to each function's box centre;
+    mom (m, 3) complex128.  Returns (P (n_fun, 192) complex128, residual (n_fun,) or None).
+    """
+    fun_off = np.ascontiguousarray(fun_off, dtype=np.int64).reshape(-1)
+    n_fun = fun_off.shape[0] - 1
+    pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
+    mom = np.ascontiguousarray(mom, dtype=np.complex128).reshape(-1, 3)
+    if n_fun < 0 or pos.shape[0] != mom.shape[0] or pos.shape[0] < fun_off[-1]:
+        raise ValueError("fun_off, pos and mom disagree")
+    spec = ie_mapping_spec(k=k, eta=eta, box_edge=box_edge, lattice=lattice, n_samples=n_samples,
+                           sample_radius=sample_radius, tikhonov=tikhonov)
+    P = np.zeros((max(n_fun, 0), NU), dtype=np.complex128)
+    res = np.zeros(max(n_fun, 0), dtype=np.float64) if residual else None
+    _check(lib().ie_map_basis(ctypes.byref(spec), n_fun, fun_off.ctypes.data, pos.ctypes.data, mom.ctypes.data,
+                              P.ctypes.data, None if res is None else res.ctypes.data, _stream(stream)),
+           "ie_map_basis")
+    return P, res
 
 
 def ie_rhs_plane_wave(plan, khat, pol, v, stream=None):

@@ -44,6 +44,29 @@ constexpr int kTcImageElems = 128 * kTcK;
 constexpr int kTcImagesPerDisp = 3 * kTcKChunks * 2;            // 36
 constexpr size_t kTcDispElems = (size_t)kTcImageElems * kTcImagesPerDisp;   // 147,456
 
+// D(R) of eq. 5 with psi of eq. 6, FP64.  out[3*i+j] = D_ij.
+__device__ inline void dyad_fp64(double k, double eta, double Rx, double Ry, double Rz, double2 out[9]) {
+    constexpr double kPi = 3.14159265358979323846;
+    double r = sqrt(Rx * Rx + Ry * Ry + Rz * Rz);
+    double kr = k * r;
+    double s, c;
+    sincos(kr, &s, &c);
+    double sc = k * eta / (4.0 * kPi * r);
+    double psi_re = -sc * s, psi_im = -sc * c;          // -j k eta e^{-jkr} / (4 pi r)
+    double ikr = 1.0 / kr, ikr2 = ikr * ikr;
+    double a_re = 1.0 - ikr2, a_im = -ikr;              // 1 - j/kr - 1/kr^2
+    double b_re = 1.0 - 3.0 * ikr2, b_im = -3.0 * ikr;  // 1 - 3j/kr - 3/kr^2
+    double rh[3] = {Rx / r, Ry / r, Rz / r};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double t_re = (i == j ? a_re : 0.0) - rh[i] * rh[j] * b_re;
+            double t_im = (i == j ? a_im : 0.0) - rh[i] * rh[j] * b_im;
+            out[3 * i + j] = make_double2(psi_re * t_re - psi_im * t_im, psi_re * t_im + psi_im * t_re);
+        }
+}
+
 void set_error(const char *fmt, ...);
 const char *last_error();
 

@@ -121,3 +121,41 @@ def test_diagnostic_and_tuner_argument_checks(built):
     info = ie.ie_tune_info()
     assert L.ie_plan_tune(None, ie.IE_PREC_FP16X3, 1, ctypes.byref(info), None) == ie.IE_ERR_INVALID
     assert L.ie_plan_check(None, None) == ie.IE_ERR_INVALID
+
+
+MAP_BAD = [
+    dict(lattice=3), dict(n_samples=63), dict(n_samples=257), dict(sample_radius=0.8),
+    dict(sample_radius=float("nan")), dict(box_edge=0.0), dict(k=-1.0), dict(tikhonov=-1e-5),
+    dict(pos_scale=1.6),          # a dipole outside S (radius 1.5 a)
+    dict(off0=1), dict(decreasing=True), dict(nan_mom=True),
+]
+
+
+@pytest.mark.parametrize("bad", MAP_BAD, ids=lambda b: ",".join(b))
+def test_map_basis_validation_rejects(built, bad):
+    """ie_map_basis checks its spec, offsets and dipoles on the host before any device work."""
+    a = W.BOX_EDGE
+    fun_off, pos, mom = W.point_dipole_basis([2], 3, a=a)
+    fun_off, pos, mom = fun_off.copy(), pos.copy(), mom.copy()
+    args = dict(k=W.K0, eta=W.ETA0, box_edge=a, lattice=4, n_samples=128, sample_radius=1.5, tikhonov=0.0)
+    args.update({k: v for k, v in bad.items() if k in args})
+    if "pos_scale" in bad:
+        pos[0] = np.array([1.0, 0.0, 0.0]) * bad["pos_scale"] * a
+    if "off0" in bad:
+        fun_off[0] = 1
+    if "decreasing" in bad:
+        fun_off[1] = fun_off[2] + 1
+        pos, mom = np.vstack([pos, pos]), np.vstack([mom, mom])
+    if "nan_mom" in bad:
+        mom[0, 1] = complex(np.nan, 0.0)
+    with pytest.raises(ie.IEError) as e:
+        ie.ie_map_basis(args["k"], args["eta"], args["box_edge"], fun_off, pos, mom, n_samples=args["n_samples"],
+                        sample_radius=args["sample_radius"], lattice=args["lattice"], tikhonov=args["tikhonov"],
+                        stream=0)
+    assert e.value.status == ie.IE_ERR_INVALID
+
+
+def test_map_basis_of_no_functions_is_a_no_op(built):
+    P, res = ie.ie_map_basis(W.K0, W.ETA0, W.BOX_EDGE, np.zeros(1, dtype=np.int64), np.zeros((0, 3)),
+                             np.zeros((0, 3), dtype=np.complex128), stream=0)
+    assert P.shape == (0, 192) and res.shape == (0,)

@@ -121,6 +121,38 @@ def test_dyad_static_and_radiation_limits():
     assert np.linalg.norm(D - lim) <= 1e-5 * np.linalg.norm(lim)
 
 
+def _sph_j0_j2(x):
+    """Spherical Bessel j0, j2 from their power series x^l sum_n (-x^2/2)^n / (n! (2n+2l+1)!!)."""
+    def series(l):
+        term, total, n = x ** l / math.prod(range(2 * l + 1, 0, -2)), 0.0, 0
+        while abs(term) > 1e-30 * max(abs(total), 1e-300) or n < 3:
+            total += term
+            n += 1
+            term *= (-x * x / 2) / (n * (2 * n + 2 * l + 1))
+        return total
+    return series(0), series(2)
+
+
+@pytest.mark.parametrize("kr", [1e-3, 6e-3, 0.031, 0.3, 2.0])
+def test_dyad_radiative_part_in_the_low_frequency_regime(kr):
+    """Re D = -k eta (I + grad grad / k^2) sin(kR)/(4 pi R) is regular at R = 0; written with
+    spherical Bessel functions it is -(k^2 eta / 4 pi) [(2/3 j0 - j2/3) I + j2 Rhat Rhat].  At
+    small kR eq. 5-6 reach it through a cancellation of 1/(kR) terms, so the FP64 dyad keeps
+    about eps/(kR)^2 of relative accuracy: the budget the low-frequency workloads rely on."""
+    g = W.rng(104)
+    j0, j2 = _sph_j0_j2(kr)
+    for _ in range(10):
+        R = g.standard_normal(3)
+        R *= (kr / K) / np.linalg.norm(R)
+        rh = R / np.linalg.norm(R)
+        ref = -(K * K * ETA / (4 * math.pi)) * ((2 / 3 * j0 - j2 / 3) * np.eye(3) + j2 * np.outer(rh, rh))
+        D = oracle.dyad(K, ETA, R)
+        assert np.abs(D.real - ref).max() <= (2e-15 / kr ** 2 + 1e-14) * np.abs(ref).max()
+        # the static part dominates the reactive (imaginary) part by about 3/(kR)^3
+        if kr < 0.1:
+            assert np.abs(D.imag).max() >= 1.0 / kr ** 3 * np.abs(ref).max()
+
+
 # ------------------------------------------------------------------ §2.2 counts
 def test_translation_vector_counts_printed_in_the_paper():
     gold = json.load(open(os.path.join(GOLDEN, "paper_counts.json")))
@@ -396,3 +428,115 @@ def test_plane_wave_properties():
     for b in range(pt.n_boxes):
         Pbig[o[b]:o[b + 1], 192 * b:192 * (b + 1)] = pt.P[o[b]:o[b + 1]]
     assert np.allclose(v[0], Pbig @ ebig[0], rtol=1e-13, atol=0)
+
+
+# ------------------------------------------------------------------ mapping (§2.1, eq. 9-11, 15-17)
+EDGES = [W.BOX_EDGE, W.LFB_EDGES["lfb256"]]
+
+
+def test_fibonacci_sphere_closed_form():
+    """Equal-area bands: z_l = R (1 - (2l+1)/n) exactly; azimuth steps of 2 pi / golden ratio;
+    every point on the sphere; nearest neighbours near the mean spacing sqrt(4 pi / n) R."""
+    for n, R in ((128, 0.375), (64, 1.0), (256, 2.0)):
+        S = oracle.fibonacci_sphere(n, R)
+        assert np.allclose(np.linalg.norm(S, axis=1), R, rtol=1e-14, atol=0)
+        assert np.allclose(S[:, 2], R * (1 - (2 * np.arange(n) + 1) / n), rtol=0, atol=1e-14 * R)
+        az = np.arctan2(S[:, 1], S[:, 0])
+        step = np.mod(np.diff(az), 2 * math.pi)
+        assert np.allclose(step, np.mod(2 * math.pi * (2 / (1 + math.sqrt(5))), 2 * math.pi), atol=1e-12)
+        d = np.linalg.norm(S[:, None] - S[None], axis=2) + np.eye(n) * 10 * R
+        nn = d.min(1) / (math.sqrt(4 * math.pi / n) * R)
+        assert nn.min() > 0.8 and nn.max() < 1.05
+        assert np.linalg.norm(S.mean(0)) < 2e-3 * R
+
+
+@pytest.mark.parametrize("a", EDGES)
+def test_mapping_reproduces_a_uniform_dipole(a):
+    """A basis function that is itself uniform dipole j, direction beta, has B = A e_{3j+beta};
+    A has full column rank (3 N_s = 384 >= 192), so eq. 11 returns e_{3j+beta}."""
+    sites = oracle.lattice_offsets(a, 4)
+    cases = [(0, 0), (17, 1), (42, 2), (63, 0)]
+    off = np.arange(len(cases) + 1, dtype=np.int64)
+    pos = np.array([sites[j] for j, _ in cases])
+    mom = np.array([np.eye(3)[b] for _, b in cases], dtype=np.complex128)
+    P, res = oracle.map_basis(K, ETA, a, 4, 128, 1.5, off, pos, mom)
+    for f, (j, b) in enumerate(cases):
+        e = np.zeros(192)
+        e[3 * j + b] = 1
+        assert np.abs(P[f] - e).max() < 1e-8
+        assert res[f] < 1e-10
+
+
+def test_mapping_superposition_over_the_dipoles_of_a_function():
+    a = W.BOX_EDGE
+    fun_off, pos, mom = W.point_dipole_basis([3], 910, a=a, max_dipoles=3)
+    fun_off = np.array([0, 3], dtype=np.int64)
+    pos, mom = pos[:3], mom[:3]
+    if len(pos) < 3:
+        pos = np.vstack([pos, [[0.01, -0.02, 0.03]] * (3 - len(pos))])
+        mom = np.vstack([mom, [[1, 1j, 0]] * (3 - len(mom))])
+    whole, _ = oracle.map_basis(K, ETA, a, 4, 128, 1.5, fun_off, pos, mom)
+    parts, _ = oracle.map_basis(K, ETA, a, 4, 128, 1.5, np.arange(4, dtype=np.int64), pos, mom)
+    assert np.linalg.norm(whole[0] - parts.sum(0)) <= 1e-10 * np.linalg.norm(whole[0])
+
+
+@pytest.mark.parametrize("a", EDGES)
+def test_equivalent_dipoles_reproduce_the_far_field(a):
+    """The uniqueness argument of §2.1: fields matched on S (radius 1.5a) match outside it.
+    The 192 uniform dipoles with eq. 11's coefficients radiate, at points 2a..6a from the box
+    centre, the field of the basis function itself to within ~1e-3 (Table 1's error level);
+    the field mismatch on S (eq. 10's residual) stays below 1e-2."""
+    fun_off, pos, mom = W.point_dipole_basis(np.full(4, 6), 900, a=a)
+    P, res = oracle.map_basis(K, ETA, a, 4, 128, 1.5, fun_off, pos, mom)
+    assert res.max() < 1e-2
+    sites = oracle.lattice_offsets(a, 4)
+    g = W.rng(905)
+    for f in range(len(fun_off) - 1):
+        src = slice(fun_off[f], fun_off[f + 1])
+        for _ in range(6):
+            u = g.standard_normal(3)
+            R = u / np.linalg.norm(u) * a * g.uniform(2.0, 6.0)
+            exact = sum(oracle.dyad(K, ETA, R - x) @ m for x, m in zip(pos[src], mom[src]))
+            equiv = sum(oracle.dyad(K, ETA, R - sites[j]) @ P[f, 3 * j:3 * j + 3] for j in range(64))
+            assert np.linalg.norm(equiv - exact) <= 5e-3 * np.linalg.norm(exact)
+
+
+@pytest.mark.parametrize("a", EDGES)
+def test_inverse_mapping_is_the_transposed_forward_map(a):
+    """Eq. 15-17 computed literally (virtual dipoles on S fitted to the fields at the uniform
+    sites, then tested on the function) equal P_f . E: D(R) = D(-R) = D(R)^T makes the tested
+    virtual-dipole fields B_f^T and (A^T)^+ = (A^+)^T.  For fields E of a source 3a away the
+    result is the function's exact response to that source within ~1e-4."""
+    fun_off, pos, mom = W.point_dipole_basis(np.full(1, 3), 920, a=a)
+    P, _ = oracle.map_basis(K, ETA, a, 4, 128, 1.5, fun_off, pos, mom)
+    sites = oracle.lattice_offsets(a, 4)
+    src, pm = np.array([3.0 * a, 0.4 * a, -0.2 * a]), np.array([1.0, 0.5j, -0.3])
+    E = np.concatenate([oracle.dyad(K, ETA, s - src) @ pm for s in sites])
+    for f in range(len(fun_off) - 1):
+        sl = slice(fun_off[f], fun_off[f + 1])
+        V = oracle.inverse_map_fields(K, ETA, a, 4, 128, 1.5, E, pos[sl], mom[sl])
+        assert abs(V - P[f] @ E) <= 1e-9 * abs(V)
+        exact = sum(m @ (oracle.dyad(K, ETA, x - src) @ pm) for x, m in zip(pos[sl], mom[sl]))
+        assert abs(V - exact) <= 1e-3 * abs(exact)
+
+
+def test_tikhonov_mapping_keeps_the_far_field_and_tames_the_coefficients():
+    """Eq. 11's plain pseudo-inverse gives oscillating coefficients (A's condition number is
+    about 1e7).  A Tikhonov weight of 1e-5 ||A||_F leaves the error of the mapped far product
+    against the point dipoles' own far interactions and the misfit on S nearly unchanged,
+    while the coefficient norms fall by more than 10x."""
+    import dataclasses
+    p = W.tiny(nb=4)
+    fun_off, pos, mom = W.point_dipole_basis(p.nb, 945, a=p.a)
+    c = W.coefficients(p, 1, 946)
+    direct = oracle.point_dipole_far(p, fun_off, pos, mom, c[0])
+    out = {}
+    for t in (0.0, 1e-5):
+        P, res = oracle.map_basis(K, ETA, p.a, 4, 128, 1.5, fun_off, pos, mom, tikhonov=t)
+        y = oracle.far_matvec(dataclasses.replace(p, P=P), c)[0]
+        out[t] = (np.linalg.norm(y - direct) / np.linalg.norm(direct), np.median(np.linalg.norm(P, axis=1)),
+                  res.max())
+    (e0, n0, r0), (e1, n1, r1) = out[0.0], out[1e-5]
+    assert e0 < 1e-3 and e1 < 1.2 * e0
+    assert n1 < n0 / 10
+    assert r1 < 1.3 * r0

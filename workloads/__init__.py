@@ -22,6 +22,12 @@ discretisation, §5):
   serve    Poisson arrivals; sphere shells with box counts log-uniform in
            [200, 20000] on the smallest grid in {16, 32, 64} that holds them,
            1..4 plane waves each (seed 51).
+  *_lfb8, *_lfb256
+           the same geometry and seeds with box edge a = lambda/8 or lambda/256
+           (the paper's low-frequency regime, §3 and §6).  The closest far site
+           pairs then have kR = 0.98 or 0.031; at lambda/256 a shell16 object is
+           1/16 wavelength across, so every interaction is quasi-static and the
+           1/(kR)^2 terms of the dyad dominate.
 """
 from __future__ import annotations
 
@@ -180,9 +186,49 @@ def shell16(nb: int = 32, identity: bool = False) -> Problem:
     return make_problem(name, 16, sphere_shell(16, 7.0), nb, seed_P=21, identity=identity)
 
 
+def tiny_identity() -> Problem:
+    """4x4x4 grid, every box occupied, identity P (nb = 192: c is the dipole vector)."""
+    return make_problem("tiny_identity", 4, full_grid(4), NU, seed_P=11, identity=True)
+
+
 def shell32(nb: int = 32) -> Problem:
     """32^3 grid, shell of radius 14 boxes (5,000 boxes) (seed 31)."""
     return make_problem("shell32", 32, sphere_shell(32, 14.0), nb, seed_P=31)
+
+
+LFB_EDGES = {"lfb8": 1.0 / 8.0, "lfb256": 1.0 / 256.0}
+
+
+def lfb(p: Problem, tag: str) -> Problem:
+    """The workload `p` with its box edge shrunk to LFB_EDGES[tag] wavelengths.
+
+    Geometry, P and seeds are unchanged; the name gains the tag and the frozen alpha
+    (if any) is the one make_alpha.py recorded under that name.
+    """
+    name = f"{p.name}_{tag}"
+    return Problem(name=name, G=p.G, box_ijk=p.box_ijk, nb=p.nb, P=p.P,
+                   alpha=alpha_for(name, default=float("nan")), k=p.k, eta=p.eta,
+                   a=LFB_EDGES[tag], lattice=p.lattice, self_box_mode=p.self_box_mode)
+
+
+def point_dipole_basis(nb, seed: int, a: float = BOX_EDGE, max_dipoles: int = 3):
+    """Seeded subdomain basis functions made of point dipoles, the input of the mapping
+    construction (§2.1): box b owns nb[b] functions, each of 1..max_dipoles dipoles at
+    positions uniform in the box (relative to its centre) with complex N(0,1) moments.
+
+    Returns (fun_off (n_fun+1,) int64, pos (m, 3) float64, mom (m, 3) complex128), the
+    functions in box order, so that mapped rows pack as P does.
+    """
+    g = rng(seed)
+    nb = np.asarray(nb, dtype=np.int64)
+    n_fun = int(nb.sum())
+    counts = g.integers(1, max_dipoles + 1, size=n_fun)
+    fun_off = np.zeros(n_fun + 1, dtype=np.int64)
+    np.cumsum(counts, out=fun_off[1:])
+    m = int(fun_off[-1])
+    pos = g.uniform(-0.5 * a, 0.5 * a, size=(m, 3))
+    mom = complex_normal(g, (m, 3))
+    return fun_off, pos, mom
 
 
 def coefficients(p: Problem, nrhs: int, seed: int) -> np.ndarray:
@@ -192,6 +238,8 @@ def coefficients(p: Problem, nrhs: int, seed: int) -> np.ndarray:
 
 SEED_C = {"tiny": 12, "shell16": 22, "shell16_identity": 22, "shell32": 32}
 SEED_SUBSAMPLE = {"shell32": 33, "shell16": 23, "tiny": 13}
+SEED_MAPPED = {"tiny": 940, "shell16": 942}     # point-dipole basis functions of the mapped workloads
+MAPPED_TIKHONOV = 1e-5                          # Tikhonov weight of their mapping, relative to ||A||_F
 
 
 def subsample_boxes(p: Problem, count: int, seed: int) -> np.ndarray:

@@ -22,11 +22,27 @@ import oracle  # noqa: E402
 import workloads as W  # noqa: E402
 
 ALPHA_REL = 1.25
+
+
+def mapped(p):
+    """p with P replaced by the oracle's mapping (eq. 11) of seeded point-dipole functions."""
+    fun_off, pos, mom = W.point_dipole_basis(p.nb, W.SEED_MAPPED[p.name], a=p.a)
+    P, _ = oracle.map_basis(p.k, p.eta, p.a, p.lattice, 128, 1.5, fun_off, pos, mom, tikhonov=W.MAPPED_TIKHONOV)
+    p.P = P
+    p.name = p.name + "_mapped"
+    return p
+
+
 BUILDERS = {
     "tiny": lambda: W.tiny(),
     "shell16": lambda: W.shell16(),
     "shell16_identity": lambda: W.shell16(identity=True),
     "shell32": lambda: W.shell32(),
+    "tiny_lfb8": lambda: W.lfb(W.tiny(), "lfb8"),
+    "tiny_lfb256": lambda: W.lfb(W.tiny(), "lfb256"),
+    "shell16_lfb256": lambda: W.lfb(W.shell16(), "lfb256"),
+    "tiny_mapped": lambda: mapped(W.tiny()),
+    "shell16_mapped": lambda: mapped(W.shell16()),
 }
 
 
