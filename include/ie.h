@@ -24,7 +24,8 @@
  *  - All calls are stream-ordered on `stream` (a cudaStream_t passed as void*,
  *    NULL = legacy default stream) and return without waiting, except
  *    ie_plan_create, ie_plan_destroy, ie_plan_tune, ie_plan_check,
- *    ie_diag_bounded_wait, ie_solve and ie_map_basis, which synchronise it.
+ *    ie_diag_bounded_wait, ie_solve, ie_map_basis and ie_cvfcnn_set_weights,
+ *    which synchronise it.
  *  - A plan owns all of its device memory.  Nothing throws across the ABI; every
  *    call returns an ie_status, and ie_last_error() gives a message for the
  *    calling thread's last failure.
@@ -61,8 +62,24 @@ typedef enum {
  *  FP16X3  as BF16X3 with fp16 halves.
  *  BF16X1  tcgen05, one bf16 product (hi*hi) — the cheapest, least accurate form.
  *  FP16X1  tcgen05, one fp16 product (hi*hi) from the FP16X3 store: three more bits
- *          than BF16X1; with FP16X3 it makes a mixed pair that shares one store. */
-typedef enum { IE_PREC_FP32 = 1, IE_PREC_BF16X3 = 2, IE_PREC_FP16X3 = 3, IE_PREC_BF16X1 = 4, IE_PREC_FP16X1 = 5 } ie_prec;
+ *          than BF16X1; with FP16X3 it makes a mixed pair that shares one store.
+ *  CVFCNN  the translation surrogate of §3: per stored block a complex network
+ *          192 -> H -> 192 (input scaled by its l-infinity norm, one hidden layer
+ *          with the Cartesian ReLU max(Re z, 0) + j max(Im z, 0), linear output,
+ *          output rescaled), evaluated in FP32 on the SIMT cores.  Its weights are
+ *          fitted at plan creation in closed form: the network whose output is the
+ *          best rank-H approximation of the block (truncated SVD by one-sided Jacobi
+ *          in FP64), with hidden biases that keep every pre-activation in the ReLU's
+ *          linear region on the unit l-infinity ball; ie_cvfcnn_set_weights loads
+ *          any other weights.  Error against G_d: the SVD tail (ie_plan_stats). */
+typedef enum {
+    IE_PREC_FP32 = 1,
+    IE_PREC_BF16X3 = 2,
+    IE_PREC_FP16X3 = 3,
+    IE_PREC_BF16X1 = 4,
+    IE_PREC_FP16X1 = 5,
+    IE_PREC_CVFCNN = 6
+} ie_prec;
 #define IE_PRECMASK(p) (1u << (unsigned)(p))
 
 /* Which part of Z a product applies. */
@@ -111,6 +128,9 @@ typedef struct {
      * only; its other columns get no far-zone contribution (their inputs should be
      * zero, as those of padded right-hand sides are).                              */
     const int32_t *group_nrhs;
+    /* Hidden width H of the CVFCNN surrogates (IE_PREC_CVFCNN in prec_mask), 1..64;
+     * 0 = 50, the paper's choice.                                                  */
+    int cvfcnn_hidden;
 } ie_problem;
 
 typedef struct {
@@ -130,6 +150,13 @@ typedef struct {
     int max_rhs;               /* the plan's max_rhs                                  */
     int64_t n_coupling_blocks; /* stored far blocks: n_far_disp, or the canonical
                                   displacements with symmetry = 1                     */
+    int cvfcnn_hidden;         /* H of the surrogates (0: none prepared)             */
+    int cvfcnn_sweeps;         /* most Jacobi sweeps any block's SVD took (at most
+                                  30; clustered tiny singular values can use them up,
+                                  cvfcnn_tail is exact either way)                  */
+    double cvfcnn_tail;        /* largest relative Frobenius tail of a block's SVD
+                                  beyond H: the surrogate's expected relative error
+                                  on inputs with independent entries (e^u of §3)     */
 } ie_plan_stats;
 
 /* Build a plan: validate the geometry, group far box pairs by displacement, generate
@@ -350,6 +377,22 @@ typedef struct {
 ie_status ie_map_basis(const ie_mapping_spec *spec, int64_t n_fun, const int64_t *fun_off,
                        const double *pos, const double *mom, double *P, double *residual,
                        void *stream);
+
+/* ---- CVFCNN surrogates (§3) ------------------------------------------------------ */
+
+/* Displacements of the stored far blocks, in the plan's block order (the canonical
+ * sorted |d| with symmetry = 1, else every far displacement): disp, HOST,
+ * n_coupling_blocks x 3. */
+ie_status ie_plan_blocks(ie_plan plan, int32_t *disp);
+
+/* Replace the fitted surrogate weights (plan prepared with IE_PREC_CVFCNN).  HOST
+ * complex64 (re, im interleaved), per stored block in ie_plan_blocks order, H the
+ * plan's cvfcnn_hidden:  W1 [blocks][H][192], b1 [blocks][H], W2 [blocks][192][H],
+ * b2 [blocks][192].  The network of block c maps x to s (W2 relu(W1 x / s + b1) + b2),
+ * s = max_u |x_u| (0 for x = 0); with symmetry = 1 displacement d = Q c applies it in
+ * the frame of c (input through S_Q^T, output through S_Q).  Synchronises stream. */
+ie_status ie_cvfcnn_set_weights(ie_plan plan, const float *W1, const float *b1, const float *W2, const float *b2,
+                                void *stream);
 
 /* ---- diagnostics -------------------------------------------------------------- */
 const char *ie_status_str(ie_status s);

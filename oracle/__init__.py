@@ -27,6 +27,11 @@ What each function follows (paper sections / equations / algorithms):
   inverse_map_fields    eq. 15-17 literally: Q = (A^T)^+ E, tested on a basis function
   point_dipole_far      far interactions of the point-dipole basis functions themselves
                         (the original system that the mapping replaces), brute force
+  cvfcnn_forward        the translation network of §3 (l-inf input scaling, one hidden
+                        layer with the Cartesian ReLU, linear output, rescaling)
+  cvfcnn_fit            closed-form weights: the network in its linear regime equal to
+                        the truncated SVD of a translation matrix (numpy's SVD)
+  cvfcnn_far_matvec     Alg. 2 with the networks in place of eq. 13's matrices
 
 Parity status: every function above is pinned by the CPU tests in
 tests/test_oracle_pins.py (closed-form Hertzian dipole field, reciprocity,
@@ -535,3 +540,95 @@ def point_dipole_far(p, fun_off, pos, mom, c) -> np.ndarray:
     _load().or_point_dipole_far(p.k, p.eta, n_fun, _ptr(fun_off), _ptr(fun_box), _ptr(ijk), _ptr(absolute),
                                 _ptr(m), _ptr(cc), _ptr(out))
     return out
+
+
+# ---------------------------------------------------------------- §3 translation networks
+def cvfcnn_forward(W1, b1, W2, b2, x) -> np.ndarray:
+    """The network of §3 on inputs x (..., 192): s = max_u |x_u|, z = W1 (x / s) + b1,
+    h = max(Re z, 0) + j max(Im z, 0) (Cartesian ReLU), output s (W2 h + b2); 0 for x = 0."""
+    x = _c128(x)
+    s = np.abs(x).max(axis=-1, keepdims=True)
+    safe = np.where(s > 0, s, 1.0)
+    z = (x / safe) @ np.asarray(W1).T + b1
+    h = np.maximum(z.real, 0.0) + 1j * np.maximum(z.imag, 0.0)
+    o = h @ np.asarray(W2).T + b2
+    return np.where(s > 0, s * o, 0.0)
+
+
+def cvfcnn_fit(C, H: int):
+    """Weights of a width-H network whose output on the unit l-inf ball is U_H S_H V_H^H x,
+    the truncated SVD of C (the best rank-H approximation): W1 = V_H^H, W2 = U_H S_H,
+    b1_h = beta_h (1 + j) with beta_h = sum_u |W1_hu| (so Re and Im of W1 x + b1 stay >= 0
+    for |x_u| <= 1 and the ReLU passes them), b2 = -W2 b1."""
+    U, S, Vh = np.linalg.svd(_c128(C))
+    W1 = Vh[:H].copy()
+    W2 = U[:, :H] * S[:H]
+    b1 = np.abs(W1).sum(axis=1) * (1.0 + 1.0j)
+    b2 = -W2 @ b1
+    return W1, b1, W2, b2
+
+
+def signed_permutation(Q, L: int) -> np.ndarray:
+    """S_Q (3 L^3 x 3 L^3) with G_{Qd} = S_Q G_d S_Q^T: site s goes where Q takes its
+    centred lattice offset, and its 3 components transform by Q."""
+    Q = np.asarray(Q, dtype=np.float64)
+    ns = L ** 3
+    S = np.zeros((3 * ns, 3 * ns))
+    for s in range(ns):
+        ii = np.array([s % L, (s // L) % L, s // (L * L)])
+        jj = (Q @ (ii + 0.5 - L / 2.0) + L / 2.0 - 0.5).round().astype(int)
+        s2 = jj[0] + L * jj[1] + L * L * jj[2]
+        S[3 * s2:3 * s2 + 3, 3 * s:3 * s + 3] = Q
+    return S
+
+
+def canonical_frame(d):
+    """(c, Q): c = |d| sorted ascending and a signed permutation Q with Q c = d."""
+    d = np.asarray(d, dtype=np.int64)
+    order = np.argsort(np.abs(d), kind="stable")
+    c = np.abs(d)[order]
+    Q = np.zeros((3, 3))
+    for k, axis in enumerate(order):
+        Q[axis, k] = 1.0 if d[axis] >= 0 else -1.0
+    return c, Q
+
+
+def cvfcnn_far_matvec(p, c, H: int = 50, weights=None, targets=None) -> np.ndarray:
+    """Z^F c with Alg. 2's translation E_t += G_d x_b replaced by the network of d.
+    weights None: each canonical c = sorted |d| gets cvfcnn_fit(G_c, H), applied to
+    displacement d = Q c in the frame of c: y = S_Q net_c(S_Q^T x).  weights: a dict
+    from displacement tuples to (W1, b1, W2, b2), applied directly."""
+    X = aggregate(p, c)
+    nrhs = X.shape[0]
+    ds, groups = pair_groups(p, FAR)
+    tset = None if targets is None else set(int(t) for t in targets)
+    Y = np.zeros_like(X)
+    fitted = {}
+    for d, (src, dst) in zip(ds, groups):
+        src = np.asarray(src)
+        dst = np.asarray(dst)
+        if tset is not None:
+            keep = np.array([int(t) in tset for t in dst], dtype=bool)
+            src, dst = src[keep], dst[keep]
+        if len(src) == 0:
+            continue
+        if weights is not None:
+            net, S = weights[tuple(int(v) for v in d)], None
+        else:
+            cc, Q = canonical_frame(d)
+            key = tuple(int(v) for v in cc)
+            if key not in fitted:
+                fitted[key] = cvfcnn_fit(coupling_block(p, np.array(key, dtype=np.int32)), H)
+            net, S = fitted[key], signed_permutation(Q, p.lattice)
+        for r in range(nrhs):
+            xin = X[r, src]
+            if S is not None:
+                xin = xin @ S                  # rows (S^T x)^T
+            out = cvfcnn_forward(*net, xin)
+            if S is not None:
+                out = out @ S.T                # rows (S o)^T
+            np.add.at(Y[r], dst, out)
+    if targets is None:
+        return disaggregate(p, Y)
+    targets = np.asarray(targets)
+    return disaggregate(p, Y[:, targets], boxes=targets)

@@ -19,10 +19,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libie.so")
 
 IE_OK, IE_ERR_INVALID, IE_ERR_OOM, IE_ERR_CUDA, IE_ERR_NOT_CONVERGED, IE_ERR_TIMEOUT, IE_ERR_UNSUPPORTED = range(7)
-IE_PREC_FP32, IE_PREC_BF16X3, IE_PREC_FP16X3, IE_PREC_BF16X1, IE_PREC_FP16X1 = 1, 2, 3, 4, 5
+IE_PREC_FP32, IE_PREC_BF16X3, IE_PREC_FP16X3, IE_PREC_BF16X1, IE_PREC_FP16X1, IE_PREC_CVFCNN = 1, 2, 3, 4, 5, 6
 IE_FAR, IE_NEAR, IE_FULL = 1, 2, 3
 PREC_NAMES = {IE_PREC_FP32: "fp32", IE_PREC_BF16X3: "bf16x3", IE_PREC_FP16X3: "fp16x3", IE_PREC_BF16X1: "bf16x1",
-              IE_PREC_FP16X1: "fp16x1"}
+              IE_PREC_FP16X1: "fp16x1", IE_PREC_CVFCNN: "cvfcnn"}
 NU = 192                      # dipole unknowns per box (4^3 lattice x 3 orientations)
 
 EXPORTED = [
@@ -31,7 +31,7 @@ EXPORTED = [
     "ie_solve_opts_default", "ie_solve", "ie_solver_create", "ie_solver_footprint", "ie_solver_start",
     "ie_solver_advance", "ie_solver_poll", "ie_solver_destroy", "ie_status_str", "ie_last_error", "ie_version",
     "ie_plan_profile", "ie_kernel_launches", "ie_translate_noalloc", "ie_plan_check", "ie_diag_bounded_wait",
-    "ie_plan_tune", "ie_map_basis",
+    "ie_plan_tune", "ie_map_basis", "ie_plan_blocks", "ie_cvfcnn_set_weights",
 ]
 
 
@@ -48,7 +48,8 @@ class ie_problem(ctypes.Structure):
                 ("box_ijk", ctypes.c_void_p), ("nb", ctypes.c_void_p), ("P", ctypes.c_void_p),
                 ("alpha", ctypes.c_double), ("self_box_mode", ctypes.c_int), ("prec_mask", ctypes.c_uint),
                 ("max_rhs", ctypes.c_int), ("n_groups", ctypes.c_int), ("box_group", ctypes.c_void_p),
-                ("group_alpha", ctypes.c_void_p), ("symmetry", ctypes.c_int), ("group_nrhs", ctypes.c_void_p)]
+                ("group_alpha", ctypes.c_void_p), ("symmetry", ctypes.c_int), ("group_nrhs", ctypes.c_void_p),
+                ("cvfcnn_hidden", ctypes.c_int)]
 
 
 class ie_plan_stats(ctypes.Structure):
@@ -56,7 +57,8 @@ class ie_plan_stats(ctypes.Structure):
                 ("n_far_disp", ctypes.c_int64), ("n_near_pairs", ctypes.c_int64), ("n_work_simt", ctypes.c_int64),
                 ("n_work_tc", ctypes.c_int64), ("device_bytes", ctypes.c_size_t), ("plan_seconds", ctypes.c_double),
                 ("translate_ms", ctypes.c_double), ("translate_launches", ctypes.c_int64),
-                ("n_groups", ctypes.c_int), ("max_rhs", ctypes.c_int), ("n_coupling_blocks", ctypes.c_int64)]
+                ("n_groups", ctypes.c_int), ("max_rhs", ctypes.c_int), ("n_coupling_blocks", ctypes.c_int64),
+                ("cvfcnn_hidden", ctypes.c_int), ("cvfcnn_sweeps", ctypes.c_int), ("cvfcnn_tail", ctypes.c_double)]
 
 
 class ie_tune_info(ctypes.Structure):
@@ -125,6 +127,8 @@ def lib() -> ctypes.CDLL:
     L.ie_diag_bounded_wait.argtypes = [ctypes.c_double, vp]
     L.ie_plan_tune.argtypes = [vp, i, i, P(ie_tune_info), vp]
     L.ie_map_basis.argtypes = [P(ie_mapping_spec), ctypes.c_int64, vp, vp, vp, vp, vp, vp]
+    L.ie_plan_blocks.argtypes = [vp, vp]
+    L.ie_cvfcnn_set_weights.argtypes = [vp, vp, vp, vp, vp, vp]
     for name in EXPORTED:          # every declared symbol must resolve
         getattr(L, name)
     _lib = L
@@ -185,7 +189,7 @@ def _stream(stream) -> int | None:
 
 
 def make_problem(k, eta, box_edge, grid_n, box_ijk, nb, P, alpha, prec_mask, max_rhs=1, self_box_mode=0,
-                 lattice=4, box_group=None, group_alpha=None, symmetry=0, group_nrhs=None):
+                 lattice=4, box_group=None, group_alpha=None, symmetry=0, group_nrhs=None, cvfcnn_hidden=0):
     """Build an ie_problem struct; keeps the host arrays alive on the returned object.
     box_group / group_alpha: batch of independent scatterers (ids non-decreasing)."""
     ijk = np.ascontiguousarray(box_ijk, dtype=np.int32)
@@ -200,15 +204,16 @@ def make_problem(k, eta, box_edge, grid_n, box_ijk, nb, P, alpha, prec_mask, max
                     prec_mask=prec_mask, max_rhs=max_rhs, n_groups=0 if ga is None else len(ga),
                     box_group=None if bg is None else bg.ctypes.data,
                     group_alpha=None if ga is None else ga.ctypes.data, symmetry=int(symmetry),
-                    group_nrhs=None if gr is None else gr.ctypes.data)
+                    group_nrhs=None if gr is None else gr.ctypes.data, cvfcnn_hidden=int(cvfcnn_hidden))
     pr._keep = (ijk, nb_a, P_a, bg, ga, gr)
     return pr
 
 
-def problem_from(p, prec_mask: int, max_rhs: int = 1, symmetry: int = 0):
+def problem_from(p, prec_mask: int, max_rhs: int = 1, symmetry: int = 0, cvfcnn_hidden: int = 0):
     """ie_problem from a workloads.Problem-like object."""
     return make_problem(p.k, p.eta, p.a, p.G, p.box_ijk, None if p.P is None else p.nb, p.P, p.alpha, prec_mask,
-                        max_rhs, getattr(p, "self_box_mode", 0), p.lattice, symmetry=symmetry)
+                        max_rhs, getattr(p, "self_box_mode", 0), p.lattice, symmetry=symmetry,
+                        cvfcnn_hidden=cvfcnn_hidden)
 
 
 def problem_from_batch(b, prec_mask: int, max_rhs: int | None = None, symmetry: int = 0, exact_rhs: bool = False):
@@ -319,6 +324,28 @@ def ie_map_basis(k, eta, box_edge, fun_off, pos, mom, n_samples=128, sample_radi
                               P.ctypes.data, None if res is None else res.ctypes.data, _stream(stream)),
            "ie_map_basis")
     return P, res
+
+
+def ie_plan_blocks(plan) -> np.ndarray:
+    """(n_coupling_blocks, 3) displacements of the stored far blocks, in block order."""
+    n = int(ie_plan_stats_get(plan)["n_coupling_blocks"])
+    out = np.zeros((n, 3), dtype=np.int32)
+    _check(lib().ie_plan_blocks(plan, out.ctypes.data), "ie_plan_blocks")
+    return out
+
+
+def ie_cvfcnn_set_weights(plan, W1, b1, W2, b2, stream=None):
+    """Surrogate weights per stored block: W1 (blocks, H, 192), b1 (blocks, H),
+    W2 (blocks, 192, H), b2 (blocks, 192), complex (converted to complex64)."""
+    arrs = [np.ascontiguousarray(a, dtype=np.complex64) for a in (W1, b1, W2, b2)]
+    st = ie_plan_stats_get(plan)
+    nblk, H = int(st["n_coupling_blocks"]), int(st["cvfcnn_hidden"])
+    shapes = [(nblk, H, NU), (nblk, H), (nblk, NU, H), (nblk, NU)]
+    for a, shp, name in zip(arrs, shapes, ("W1", "b1", "W2", "b2")):
+        if a.shape != shp:
+            raise ValueError(f"{name} has shape {a.shape}, expected {shp}")
+    _check(lib().ie_cvfcnn_set_weights(plan, *[a.ctypes.data for a in arrs], _stream(stream)),
+           "ie_cvfcnn_set_weights")
 
 
 def ie_rhs_plane_wave(plan, khat, pol, v, stream=None):

@@ -47,10 +47,12 @@ ie_status dalloc(ie_plan p, void **ptr, size_t bytes) {
 
 ie_status prepare_translate_simt();
 ie_status prepare_translate_tc();
+ie_status prepare_translate_cvfcnn();
 
 ie_status prepare_kernels() {
     IE_TRY(prepare_translate_simt());
     IE_TRY(prepare_translate_tc());
+    IE_TRY(prepare_translate_cvfcnn());
     return IE_OK;
 }
 
@@ -64,6 +66,10 @@ bool wants_bf16(unsigned mask) {
     return mask & (IE_PRECMASK(IE_PREC_BF16X3) | IE_PRECMASK(IE_PREC_BF16X1));
 }
 bool wants_fp16(unsigned mask) { return mask & (IE_PRECMASK(IE_PREC_FP16X3) | IE_PRECMASK(IE_PREC_FP16X1)); }
+bool wants_cvfcnn(unsigned mask) { return mask & IE_PRECMASK(IE_PREC_CVFCNN); }
+// FP32 translation inputs are read by the FP32 and the CVFCNN kernels
+bool wants_x32(unsigned mask) { return mask & (IE_PRECMASK(IE_PREC_FP32) | IE_PRECMASK(IE_PREC_CVFCNN)); }
+constexpr int kCvDefaultHidden = 50;   // the paper's H
 
 ie_status validate(const ie_problem *pr) {
     if (!pr) return set_error("null problem"), IE_ERR_INVALID;
@@ -76,8 +82,10 @@ ie_status validate(const ie_problem *pr) {
     if (!(pr->k > 0) || !(pr->box_edge > 0) || !(pr->eta > 0))
         return set_error("k, eta and box_edge must be positive"), IE_ERR_INVALID;
     unsigned known = IE_PRECMASK(IE_PREC_FP32) | IE_PRECMASK(IE_PREC_BF16X3) | IE_PRECMASK(IE_PREC_FP16X3) |
-                     IE_PRECMASK(IE_PREC_BF16X1) | IE_PRECMASK(IE_PREC_FP16X1);
+                     IE_PRECMASK(IE_PREC_BF16X1) | IE_PRECMASK(IE_PREC_FP16X1) | IE_PRECMASK(IE_PREC_CVFCNN);
     if (pr->prec_mask == 0 || (pr->prec_mask & ~known)) return set_error("bad prec_mask"), IE_ERR_INVALID;
+    if (wants_cvfcnn(pr->prec_mask) && (pr->cvfcnn_hidden < 0 || pr->cvfcnn_hidden > kCvHp))
+        return set_error("cvfcnn_hidden %d outside [0, %d]", pr->cvfcnn_hidden, kCvHp), IE_ERR_INVALID;
     if (pr->self_box_mode != 0 && pr->self_box_mode != 1) return set_error("self_box_mode must be 0 or 1"), IE_ERR_INVALID;
     if (pr->symmetry != 0 && pr->symmetry != 1) return set_error("symmetry must be 0 or 1"), IE_ERR_INVALID;
     if (pr->group_nrhs) {
@@ -322,7 +330,7 @@ size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, i
         add(nd * 2 * sizeof(int32_t));                       // block and Q of each group
         add((size_t)kSym * kNU * sizeof(uint16_t));
         add(nblk * 3 * sizeof(int32_t));
-        if (pr->prec_mask & IE_PRECMASK(IE_PREC_FP32))       // permuted FP32 inputs
+        if (wants_x32(pr->prec_mask))                        // permuted FP32 inputs
             add((size_t)kSym * pr->max_rhs * nbox * kNU * sizeof(float2));
     }
     if (pr->prec_mask & IE_PRECMASK(IE_PREC_FP32))
@@ -333,6 +341,11 @@ size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, i
     if (wants_fp16(pr->prec_mask)) {
         add((size_t)nblk * kTcDispElems * sizeof(uint16_t));
         add(nblk * sizeof(int32_t));
+    }
+    if (wants_cvfcnn(pr->prec_mask)) {
+        add((size_t)nblk * kCvBlockElems * sizeof(float2));
+        // FP64 fit scratch (block and right singular vectors), freed before the plan returns
+        add((size_t)std::min<int64_t>(nblk, kCvFitChunk) * 2 * kNU * kNU * sizeof(double2));
     }
     add((nbox + 1) * sizeof(int32_t));
     add(nnear * sizeof(int32_t));
@@ -434,6 +447,8 @@ ie_status translate_timed(ie_plan p, int prec, const float2 *X, float2 *Yslab, i
     if (timed) IE_CK(cudaEventRecord(p->prof_ev[0], st));
     if (prec == IE_PREC_FP32)
         IE_TRY(launch_translate_simt(p, X, Yslab, nrhs, st, gate));
+    else if (prec == IE_PREC_CVFCNN)
+        IE_TRY(launch_translate_cvfcnn(p, X, Yslab, nrhs, st, gate));
     else
         IE_TRY(launch_translate_tc(p, prec, Yslab, nrhs, st, gate));
     if (timed) {
@@ -452,7 +467,7 @@ ie_status far_product(ie_plan p, int prec, const float2 *c, float2 *y, int nrhs,
     size_t stride = slab_stride(p);
     IE_TRY(launch_aggregate(p, c, p->d_X, nrhs, st, gate));
     IE_TRY(launch_zero_slabs(p->d_Yslab, kSlabs, stride, (size_t)nrhs * p->nbox * kNU, st, gate));
-    if (prec != IE_PREC_FP32) IE_TRY(launch_split_tc(p, p->d_X, nrhs, is_fp16(prec), st, gate));
+    if (is_tc(prec)) IE_TRY(launch_split_tc(p, p->d_X, nrhs, is_fp16(prec), st, gate));
     IE_TRY(translate_timed(p, prec, p->d_X, p->d_Yslab, nrhs, st, gate));
     IE_TRY(launch_disaggregate(p, p->d_Yslab, kSlabs, stride, y, nrhs, accumulate, st, gate));
     return IE_OK;
@@ -481,7 +496,7 @@ ie_status apply(ie_plan p, int which, int prec, const float2 *c, float2 *y, int 
 using namespace ie;
 
 static ie_status check_prec(ie_plan p, int prec) {
-    if (prec < IE_PREC_FP32 || prec > IE_PREC_FP16X1) return set_error("unknown precision %d", prec), IE_ERR_INVALID;
+    if (prec < IE_PREC_FP32 || prec > IE_PREC_CVFCNN) return set_error("unknown precision %d", prec), IE_ERR_INVALID;
     if (!(p->prec_mask & IE_PRECMASK(prec)))
         return set_error("precision %d not prepared by this plan", prec), IE_ERR_UNSUPPORTED;
     return IE_OK;
@@ -555,6 +570,7 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
     p->self_mode = pr->self_box_mode;
     p->max_rhs = pr->max_rhs;
     p->prec_mask = pr->prec_mask;
+    p->cv_hidden = wants_cvfcnn(pr->prec_mask) ? (pr->cvfcnn_hidden ? pr->cvfcnn_hidden : kCvDefaultHidden) : 0;
     p->identity = (pr->P == nullptr);
     p->ijk.assign(pr->box_ijk, pr->box_ijk + 3 * (size_t)pr->n_boxes);
     p->nb.resize(p->nbox);
@@ -669,6 +685,7 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
             PC(cudaMemcpy(p->d_canon_disp, canon_disp.data(), canon_disp.size() * sizeof(int32_t),
                           cudaMemcpyHostToDevice));
             gen_disp = p->d_canon_disp;
+            p->h_canon_disp = canon_disp;
         }
         const int64_t nd = p->n_blocks;
         if (wants_bf16(p->prec_mask)) PT(dalloc_t(p, &p->d_Cbf16, (size_t)nd * kTcDispElems));
@@ -699,6 +716,7 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
         }
         if (!keep32) cudaFreeAsync(C32, st);
         PT(cst);
+        if (wants_cvfcnn(p->prec_mask)) PT(launch_cvfcnn_fit(p, gen_disp, st));
     }
 
     // host copy of the pairs' source boxes: per-scatterer column counts cut the work lists
@@ -727,7 +745,7 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
         PT(dalloc_t(p, &p->d_Xtc, (size_t)(p->sym ? kSym : 1) * 2 * col * 2 * kNU));
         PT(dalloc_t(p, &p->d_Xexp, col));
     }
-    if (p->sym && (p->prec_mask & IE_PRECMASK(IE_PREC_FP32))) PT(dalloc_t(p, &p->d_Xsym, (size_t)kSym * col * kNU));
+    if (p->sym && wants_x32(p->prec_mask)) PT(dalloc_t(p, &p->d_Xsym, (size_t)kSym * col * kNU));
     PT(dalloc_t(p, &p->d_err, 4));
     PC(cudaMemsetAsync(p->d_err, 0, 4 * sizeof(int), st));
     PT(dalloc_t(p, &p->d_tmp, (size_t)p->max_rhs * p->n));
@@ -748,7 +766,7 @@ ie_status ie_plan_tune(ie_plan p, int prec, int nrhs, ie_tune_info *info, void *
     if (!p) return set_error("null plan"), IE_ERR_INVALID;
     IE_TRY(check_prec(p, prec));
     IE_TRY(check_rhs(p, nrhs));
-    if (prec == IE_PREC_FP32) return set_error("the FP32 translation has no tuned tile"), IE_ERR_UNSUPPORTED;
+    if (!is_tc(prec)) return set_error("only the tensor-core translation has a tuned tile"), IE_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     // timing input: zero fields split into the 16-bit planes (the kernel's work does not
     // depend on the values)
@@ -826,6 +844,9 @@ ie_status ie_plan_stats_get(ie_plan p, ie_plan_stats *o) {
     o->n_groups = p->ngroups;
     o->max_rhs = p->max_rhs;
     o->n_coupling_blocks = p->n_blocks;
+    o->cvfcnn_hidden = p->cv_hidden;
+    o->cvfcnn_sweeps = p->cv_sweeps;
+    o->cvfcnn_tail = p->cv_tail;
     return IE_OK;
 }
 
@@ -878,7 +899,7 @@ ie_status ie_translate(ie_plan p, int prec, const void *X, void *Y, int nrhs, vo
     cudaStream_t st = (cudaStream_t)stream;
     size_t stride = slab_stride(p);
     IE_TRY(launch_zero_slabs(p->d_Yslab, kSlabs, stride, (size_t)nrhs * p->nbox * kNU, st));
-    if (prec != IE_PREC_FP32) IE_TRY(launch_split_tc(p, (const float2 *)X, nrhs, is_fp16(prec), st));
+    if (is_tc(prec)) IE_TRY(launch_split_tc(p, (const float2 *)X, nrhs, is_fp16(prec), st));
     IE_TRY(translate_timed(p, prec, (const float2 *)X, p->d_Yslab, nrhs, st, nullptr));
     return launch_sum_slabs(p, p->d_Yslab, kSlabs, stride, (float2 *)Y, nrhs, st);
 }
@@ -893,6 +914,13 @@ ie_status ie_near(ie_plan p, const void *c, void *y, int nrhs, void *stream) {
     if (!p || !c || !y) return set_error("null argument"), IE_ERR_INVALID;
     IE_TRY(check_rhs(p, nrhs));
     return launch_near(p, (const float2 *)c, (float2 *)y, nrhs, (cudaStream_t)stream);
+}
+
+ie_status ie_plan_blocks(ie_plan p, int32_t *disp) {
+    if (!p || !disp) return set_error("null argument"), IE_ERR_INVALID;
+    const std::vector<int32_t> &src = p->sym ? p->h_canon_disp : p->h_disp;
+    std::copy(src.begin(), src.end(), disp);
+    return IE_OK;
 }
 
 ie_status ie_coupling_blocks(ie_plan p, const int32_t *d, int nd, void *outp, void *stream) {

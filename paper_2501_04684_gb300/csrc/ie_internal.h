@@ -32,8 +32,21 @@ constexpr int kNU = 192;            // 3 unknowns per site
 constexpr int kSlabs = 8;           // FP32 partial-sum slabs of the far field (see translate_simt.cu)
 // Precisions whose products use the fp16 split store (per-block power-of-two scaling).
 inline bool is_fp16(int prec) { return prec == IE_PREC_FP16X3 || prec == IE_PREC_FP16X1; }
+// Precisions whose translation runs on the tensor cores (split 16-bit inputs).
+inline bool is_tc(int prec) { return prec >= IE_PREC_BF16X3 && prec <= IE_PREC_FP16X1; }
 constexpr int kSym = 48;             // signed permutations of the three axes
 constexpr int64_t kCouplingChunk = 4096;   // displacements per staging chunk of the 16-bit coupling images
+
+// CVFCNN surrogate weights of one stored block, complex64, hidden width padded to
+// kCvHp (padding rows / columns zero): W1^T [192][kCvHp], b1 [kCvHp], W2^T [kCvHp][192],
+// b2 [192] (the transposes are the operand layouts of the two SIMT GEMMs).
+constexpr int kCvHp = 64;
+constexpr size_t kCvW1 = 0;
+constexpr size_t kCvB1 = kCvW1 + (size_t)kNU * kCvHp;
+constexpr size_t kCvW2 = kCvB1 + kCvHp;
+constexpr size_t kCvB2 = kCvW2 + (size_t)kCvHp * kNU;
+constexpr size_t kCvBlockElems = kCvB2 + kNU;
+constexpr int64_t kCvFitChunk = 512;   // blocks per fit pass (two FP64 192 x 192 scratch matrices each)
 
 // Tensor-core store of one coupling block: 3 M-blocks (128 real-embedded rows) x
 // 6 K-chunks (32 source unknowns) x {hi, lo}, each a 128 x 32 16-bit image laid out
@@ -161,7 +174,13 @@ struct ie_plan_s {
     int32_t *d_gsigma = nullptr;       // [n_far_disp] signed permutation Q (0..47) with Q c = d
     uint16_t *d_symmap = nullptr;      // [48][192] u -> U(u) | 0x100 when negated (G_d[U(u)][U(v)] = +-G_c[u][v])
     int32_t *d_canon_disp = nullptr;   // [n_blocks x 3]
+    std::vector<int32_t> h_canon_disp; // host copy
     float2 *d_Xsym = nullptr;          // [48][max_rhs][nbox][192] signed-permuted FP32 translation inputs
+    // CVFCNN surrogates (IE_PREC_CVFCNN), one network per stored block
+    int cv_hidden = 0;
+    int cv_sweeps = 0;
+    double cv_tail = 0;
+    float2 *d_cvW = nullptr;           // [n_blocks][kCvBlockElems]
 
     // near zone: per target box a run of (source box, block offset)
     int64_t n_near_pairs = 0;
@@ -229,6 +248,10 @@ ie_status launch_near(const ie_plan p, const float2 *c, float2 *y, int nrhs, cud
                       const int *gate = nullptr);
 ie_status launch_translate_simt(ie_plan p, const float2 *X, float2 *Yslab, int nrhs, cudaStream_t st,
                                 const int *gate = nullptr);
+ie_status launch_translate_cvfcnn(ie_plan p, const float2 *X, float2 *Yslab, int nrhs, cudaStream_t st,
+                                  const int *gate = nullptr);
+// fits the surrogate of every stored block (blk_disp: device, n_blocks x 3)
+ie_status launch_cvfcnn_fit(ie_plan p, const int32_t *blk_disp, cudaStream_t st);
 ie_status launch_translate_tc(ie_plan p, int prec, float2 *Yslab, int nrhs, cudaStream_t st,
                               const int *gate = nullptr);
 ie_status launch_plane_wave(const ie_plan p, const double *d_khat, const double *d_pol, int nrhs, float2 *v,

@@ -540,3 +540,105 @@ def test_tikhonov_mapping_keeps_the_far_field_and_tames_the_coefficients():
     assert e0 < 1e-3 and e1 < 1.2 * e0
     assert n1 < n0 / 10
     assert r1 < 1.3 * r0
+
+
+# ------------------------------------------------------------------ translation networks (§3)
+def test_cvfcnn_forward_by_hand():
+    """The network of §3 written out entry by entry on a tiny case (3 inputs, 2 hidden)."""
+    W1 = np.array([[1.0 - 2.0j, 0.5j, -1.0], [0.25, -1.5 + 1.0j, 2.0j]])
+    b1 = np.array([0.5 - 0.25j, -0.75 + 1.0j])
+    W2 = np.array([[1.0, -1.0j], [0.5 + 0.5j, 2.0], [-1.0, 0.25j]])
+    b2 = np.array([0.1, -0.2j, 0.3 + 0.3j])
+    for x in ([2.0 - 1.0j, -0.5j, 1.0], [0.0, 0.0, -3.0 + 4.0j], [0.0, 0.0, 0.0]):
+        x = np.array(x)
+        s = max(abs(v) for v in x)
+        want = np.zeros(3, dtype=complex)
+        if s > 0:
+            h = []
+            for i in range(2):
+                z = sum(W1[i, j] * x[j] / s for j in range(3)) + b1[i]
+                h.append(complex(max(z.real, 0.0), max(z.imag, 0.0)))
+            for k in range(3):
+                want[k] = s * (sum(W2[k, i] * h[i] for i in range(2)) + b2[k])
+        got = oracle.cvfcnn_forward(W1, b1, W2, b2, x)
+        assert np.allclose(got, want, rtol=1e-14, atol=1e-14)
+    # the ReLU acts on the real and imaginary parts separately
+    z = oracle.cvfcnn_forward(np.array([[1.0]]), np.array([-2.0 + 0.5j]), np.array([[1.0]]), np.array([0.0]),
+                              np.array([1.0]))
+    assert z[0] == 0.5j
+
+
+@pytest.mark.parametrize("d", [[2, 0, 0], [1, 2, 3], [3, 3, 3]])
+def test_cvfcnn_fit_is_the_truncated_svd_on_the_unit_ball(d):
+    """Fitted weights keep every pre-activation in the ReLU's linear region, so the network
+    is U_H S_H V_H^H x on the unit l-inf ball and, being positively homogeneous through its
+    input scaling, everywhere; its error on inputs uniform in the unit box is then set by
+    the SVD tail (the Frobenius tail is its RMS for isotropic inputs)."""
+    p = W.tiny()
+    C = oracle.coupling_block(p, np.array(d, dtype=np.int32))
+    net = oracle.cvfcnn_fit(C, 50)
+    U, S, Vh = np.linalg.svd(C)
+    T = (U[:, :50] * S[:50]) @ Vh[:50]
+    g = W.rng(960)
+    x = g.uniform(-1, 1, (300, 192)) + 1j * g.uniform(-1, 1, (300, 192))
+    for scale in (1.0, 1e3, 1e-4):
+        o = oracle.cvfcnn_forward(*net, scale * x)
+        assert np.abs(o - scale * x @ T.T).max() <= 1e-12 * np.abs(scale * x @ T.T).max()
+    o = oracle.cvfcnn_forward(*net, x)
+    ref = x @ C.T
+    rms = np.sqrt(np.mean(np.linalg.norm(o - ref, axis=1) ** 2) / np.mean(np.linalg.norm(ref, axis=1) ** 2))
+    tail = np.sqrt((S[50:] ** 2).sum() / (S ** 2).sum())
+    assert 0.5 * tail <= rms <= 2.0 * tail
+
+
+def test_cvfcnn_networks_beat_the_trained_ones_of_table1():
+    """The closed-form networks (H = 50) against Table 1's trained networks: below the 1e-3
+    stopping criterion of eq. 171 and below each listed mean error, for the same translation
+    distances and box edges (inputs uniform in the unit box, the first-stage distribution)."""
+    gold = json.load(open(os.path.join(GOLDEN, "table1_networks.json")))
+    g = W.rng(961)
+    for row in gold["rows"]:
+        p = W.lfb(W.tiny(), "lfb8") if row["a_over_lambda"] == 0.125 else W.lfb(W.tiny(), "lfb256")
+        assert p.a == row["a_over_lambda"]
+        C = oracle.coupling_block(p, np.array(row["d"], dtype=np.int32))
+        net = oracle.cvfcnn_fit(C, gold["hidden"])
+        x = g.uniform(-1, 1, (200, 192)) + 1j * g.uniform(-1, 1, (200, 192))
+        ref = x @ C.T
+        eu = np.linalg.norm(oracle.cvfcnn_forward(*net, x) - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        assert eu.mean() < min(gold["gate"], row["mean"]), row
+
+
+def test_canonical_frames_map_translation_matrices():
+    """canonical_frame and signed_permutation: G_d = S_Q G_c S_Q^T for d = Q c, c = sorted |d|."""
+    p = W.tiny()
+    for d in ([0, -2, 0], [3, -1, 2], [-2, -2, 1], [0, 3, -3]):
+        c, Q = oracle.canonical_frame(d)
+        assert np.array_equal(Q @ c, d) and np.all(np.diff(c) >= 0)
+        S = oracle.signed_permutation(Q, 4)
+        Gd = oracle.coupling_block(p, np.array(d, dtype=np.int32))
+        Gc = oracle.coupling_block(p, c.astype(np.int32))
+        assert np.allclose(Gd, S @ Gc @ S.T, rtol=0, atol=1e-10 * np.abs(Gd).max())
+
+
+def test_cvfcnn_far_matvec_pair_by_pair():
+    """Alg. 2 with networks: every ordered far box pair adds net_d(x_b) to target t, by loops."""
+    boxes = [[0, 0, 0], [2, 0, 0], [0, 3, 1], [3, 3, 3]]
+    p = Tiny(boxes, G=4, L=4, nb=5, seed=962)
+    ds, groups = oracle.pair_groups(p, oracle.FAR)
+    g = W.rng(963)
+    H = 3
+    weights = {tuple(int(v) for v in d): (W.complex_normal(g, (H, 192)) / 14, W.complex_normal(g, H) * 0.1,
+                                          W.complex_normal(g, (192, H)) / 2, W.complex_normal(g, 192) * 0.1)
+               for d in ds}
+    c = W.complex_normal(g, (1, int(p.nb.sum())))
+    X = oracle.aggregate(p, c)[0]
+    Y = np.zeros_like(X)
+    ijk = np.array(boxes)
+    for b in range(len(boxes)):
+        for t in range(len(boxes)):
+            d = ijk[t] - ijk[b]
+            if np.abs(d).max() >= 2:
+                Y[t] += oracle.cvfcnn_forward(*weights[tuple(int(v) for v in d)], X[b])
+    want = oracle.disaggregate(p, Y[None])
+    got = oracle.cvfcnn_far_matvec(p, c, weights=weights)
+    assert np.allclose(got, want, rtol=1e-13, atol=1e-13 * np.abs(want).max())
