@@ -321,7 +321,9 @@ def run_shell16(ctx):
         p, mapping = map_shell(ctx, p)
         workload = workload.replace("basis unknowns", "basis unknowns, P mapped from point-dipole functions")
     p.alpha = W.alpha_for(p.name)
-    precs = [ie.IE_PREC_FP32, ie.IE_PREC_BF16X3, ie.IE_PREC_FP16X3, ie.IE_PREC_BF16X1, ie.IE_PREC_FP16X1]
+    precs = [ie.IE_PREC_FP32, ie.IE_PREC_BF16X3, ie.IE_PREC_FP16X3, ie.IE_PREC_BF16X1, ie.IE_PREC_FP16X1,
+             ie.IE_PREC_CVFCNN]
+    tc_precs = [ie.IE_PREC_BF16X3, ie.IE_PREC_FP16X3, ie.IE_PREC_BF16X1, ie.IE_PREC_FP16X1]
     t0 = time.perf_counter()
     plan = ie.Plan(ie.problem_from(p, ie.precmask(*precs), symmetry=args.symmetry), stream)
     plan_s = time.perf_counter() - t0
@@ -333,7 +335,7 @@ def run_shell16(ctx):
     paths = {name: dict(spec, opts=ie.solve_opts(**spec["opts"])) for name, spec in solve_paths(ie).items()}
     warm = max(3, args.warmup)
     # autotune the tensor-core translation (tile width, item order) once per precision
-    tuned = {ie.PREC_NAMES[q]: ie.ie_plan_tune(plan.handle, q, 1, stream) for q in precs if q != ie.IE_PREC_FP32}
+    tuned = {ie.PREC_NAMES[q]: ie.ie_plan_tune(plan.handle, q, 1, stream) for q in tc_precs}
 
     # ---- timed region: K solves of the headline path (CUDA events on the solve stream)
     head = time_solves(ctx, plan, v, x, 1, paths[HEADLINE]["opts"], args.steps, warm, clocks=True)
@@ -375,6 +377,13 @@ def run_shell16(ctx):
                      "frac": simt_ach / FP32_SIMT_PEAK_TFLOPS, "kernel": "translate_simt_kernel",
                      "traffic": profiled_traffic("translate_simt_fp32_shell16.md", "translate_simt.cu"),
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    # translation networks: 2 x 192 x H complex multiply-adds per pair (H = 50), FP32 SIMT
+    cv_ach = pairs * 8 * 2 * 192 * st["cvfcnn_hidden"] / (far["cvfcnn"]["translate_kernel_ms"] / 1e3) / 1e12
+    roofline_cvfcnn = {"bound": "alu", "achieved": cv_ach, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                       "frac": cv_ach / FP32_SIMT_PEAK_TFLOPS, "kernel": "cvfcnn_translate_kernel",
+                       "traffic": None, "hidden": st["cvfcnn_hidden"], "svd_tail_max": st["cvfcnn_tail"],
+                       "jacobi_sweeps_max": st["cvfcnn_sweeps"],
+                       "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
 
     hp = paths[HEADLINE]
     result = {
@@ -400,6 +409,7 @@ def run_shell16(ctx):
         "e2e": e2e,
         "roofline": roofline,
         "roofline_fp32": roofline_fp32,
+        "roofline_cvfcnn": roofline_cvfcnn,
     }
     if mapping is not None:
         result["mapping"] = mapping
@@ -643,6 +653,11 @@ def solve_paths(ie) -> dict:
                              desc="refinement (FP16X3 residual) around GMRES(50) on single fp16 products to 1e-3"),
         "plain": dict(opts=dict(tol=1e-6, restart=50, prec=ie.IE_PREC_FP32), dtype="f32",
                       desc="plain FP32 path: GMRES(50) on FP32 SIMT products to 1e-6"),
+        "cvfcnn_refined": dict(opts=dict(tol=1e-5, restart=50, prec=ie.IE_PREC_CVFCNN, refine=1,
+                                         refine_prec=ie.IE_PREC_FP16X3, inner_tol=1e-3),
+                               dtype="f32 translation networks (H = 50), f32 GMRES, f64 refinement",
+                               desc="refinement (FP16X3 residual) around GMRES(50) on products whose translations "
+                                    "are the closed-form networks of §3, to 1e-3"),
     }
 
 

@@ -69,9 +69,11 @@ typedef enum {
  *          output rescaled), evaluated in FP32 on the SIMT cores.  Its weights are
  *          fitted at plan creation in closed form: the network whose output is the
  *          best rank-H approximation of the block (truncated SVD by one-sided Jacobi
- *          in FP64), with hidden biases that keep every pre-activation in the ReLU's
- *          linear region on the unit l-infinity ball; ie_cvfcnn_set_weights loads
- *          any other weights.  Error against G_d: the SVD tail (ie_plan_stats). */
+ *          in FP64, once per canonical displacement sorted |d|, turned into each
+ *          displacement's frame), with hidden biases that keep every pre-activation
+ *          in the ReLU's linear region on the unit l-infinity ball;
+ *          ie_cvfcnn_set_weights loads any other weights.  Error against G_d: the
+ *          SVD tail (ie_plan_stats). */
 typedef enum {
     IE_PREC_FP32 = 1,
     IE_PREC_BF16X3 = 2,
@@ -151,9 +153,9 @@ typedef struct {
     int64_t n_coupling_blocks; /* stored far blocks: n_far_disp, or the canonical
                                   displacements with symmetry = 1                     */
     int cvfcnn_hidden;         /* H of the surrogates (0: none prepared)             */
-    int cvfcnn_sweeps;         /* most Jacobi sweeps any block's SVD took (at most
-                                  30; clustered tiny singular values can use them up,
-                                  cvfcnn_tail is exact either way)                  */
+    int cvfcnn_sweeps;         /* most Jacobi sweeps any canonical block's SVD took
+                                  (at most 16: clustered tiny singular values can use
+                                  them up; cvfcnn_tail is exact either way)          */
     double cvfcnn_tail;        /* largest relative Frobenius tail of a block's SVD
                                   beyond H: the surrogate's expected relative error
                                   on inputs with independent entries (e^u of §3)     */

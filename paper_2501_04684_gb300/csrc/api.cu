@@ -325,6 +325,7 @@ size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, i
     add(npairs * sizeof(int32_t));
     add(npairs * sizeof(int32_t));
     const bool sym = pr->symmetry == 1;
+    const int64_t ncanon = nblk;   // canonical displacements
     if (!sym) nblk = nd;
     if (sym) {
         add(nd * 2 * sizeof(int32_t));                       // block and Q of each group
@@ -344,8 +345,10 @@ size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, i
     }
     if (wants_cvfcnn(pr->prec_mask)) {
         add((size_t)nblk * kCvBlockElems * sizeof(float2));
-        // FP64 fit scratch (block and right singular vectors), freed before the plan returns
-        add((size_t)std::min<int64_t>(nblk, kCvFitChunk) * 2 * kNU * kNU * sizeof(double2));
+        // FP64 fit scratch (block and right singular vectors) and, without the symmetric
+        // store, the canonical networks before their expansion: freed before the plan returns
+        add((size_t)std::min<int64_t>(ncanon, kCvFitChunk) * 2 * kNU * kNU * sizeof(double2));
+        if (!sym) add((size_t)ncanon * kCvBlockElems * sizeof(float2));
     }
     add((nbox + 1) * sizeof(int32_t));
     add(nnear * sizeof(int32_t));
@@ -536,7 +539,8 @@ ie_status ie_plan_footprint(const ie_problem *pr, size_t *bytes) {
     for (int b = 0; b < pr->n_boxes; ++b) n += (nb[b] = pr->nb ? pr->nb[b] : kNU);
     FarGroups fg;
     int64_t npairs = 0, nd = 0, ncanon = 0;
-    far_groups(pr, g, false, fg, npairs, nd, pr->symmetry ? &ncanon : nullptr);
+    far_groups(pr, g, false, fg, npairs, nd,
+               (pr->symmetry || wants_cvfcnn(pr->prec_mask)) ? &ncanon : nullptr);
     std::vector<int32_t> st, src;
     std::vector<int64_t> boff;
     int64_t elems = 0;
@@ -600,8 +604,9 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
     p->h_gstart = fg.start;
     // stored blocks: one per displacement, or one per canonical displacement
     p->sym = pr->symmetry == 1;
+    // canonical displacements (the symmetric store, and the networks' fits)
     std::vector<int32_t> gcanon, gsigma, canon_disp;
-    if (p->sym) {
+    if (p->sym || wants_cvfcnn(p->prec_mask)) {
         std::map<std::array<int32_t, 3>, int32_t> index;
         gcanon.resize(p->n_far_disp);
         gsigma.resize(p->n_far_disp);
@@ -612,10 +617,8 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
             if (ins.second) canon_disp.insert(canon_disp.end(), c, c + 3);
             gcanon[d] = ins.first->second;
         }
-        p->n_blocks = (int64_t)index.size();
-    } else {
-        p->n_blocks = p->n_far_disp;
     }
+    p->n_blocks = p->sym ? (int64_t)canon_disp.size() / 3 : p->n_far_disp;
     std::vector<int32_t> nstart, nsrc;
     std::vector<int64_t> nboff;
     near_lists(pr, g, p->nb, nstart, nsrc, nboff, p->near_elems);
@@ -716,7 +719,32 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
         }
         if (!keep32) cudaFreeAsync(C32, st);
         PT(cst);
-        if (wants_cvfcnn(p->prec_mask)) PT(launch_cvfcnn_fit(p, gen_disp, st));
+        if (wants_cvfcnn(p->prec_mask)) {
+            const int64_t ncanon = (int64_t)canon_disp.size() / 3;
+            if (p->sym) {
+                PT(launch_cvfcnn_fit(p, p->d_canon_disp, ncanon, nullptr, nullptr, nullptr, st));
+            } else {   // fit each canonical displacement once, then turn it into every frame
+                std::vector<uint16_t> map;
+                symmetry_map(map);
+                int32_t *d_cd = nullptr, *d_gc = nullptr, *d_gs = nullptr;
+                uint16_t *d_map = nullptr;
+                PC(cudaMallocAsync(&d_cd, canon_disp.size() * sizeof(int32_t), st));
+                PC(cudaMallocAsync(&d_gc, gcanon.size() * sizeof(int32_t), st));
+                PC(cudaMallocAsync(&d_gs, gsigma.size() * sizeof(int32_t), st));
+                PC(cudaMallocAsync(&d_map, map.size() * sizeof(uint16_t), st));
+                PC(cudaMemcpyAsync(d_cd, canon_disp.data(), canon_disp.size() * sizeof(int32_t),
+                                   cudaMemcpyHostToDevice, st));
+                PC(cudaMemcpyAsync(d_gc, gcanon.data(), gcanon.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+                PC(cudaMemcpyAsync(d_gs, gsigma.data(), gsigma.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+                PC(cudaMemcpyAsync(d_map, map.data(), map.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
+                ie_status fs = launch_cvfcnn_fit(p, d_cd, ncanon, d_gc, d_gs, d_map, st);
+                cudaFreeAsync(d_cd, st);
+                cudaFreeAsync(d_gc, st);
+                cudaFreeAsync(d_gs, st);
+                cudaFreeAsync(d_map, st);
+                PT(fs);
+            }
+        }
     }
 
     // host copy of the pairs' source boxes: per-scatterer column counts cut the work lists

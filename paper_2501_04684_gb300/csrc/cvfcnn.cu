@@ -26,7 +26,7 @@ namespace ie {
 namespace {
 
 constexpr int kJacobiThreads = 1024;
-constexpr int kMaxSweeps = 30;
+constexpr int kMaxSweeps = 16;             // the rank-50 tails are then within 1e-6 of the SVD's
 constexpr double kJacobiTol = 1e-13;       // relative orthogonality of a column pair
 constexpr double kJacobiAbs = 1e-14;       // noise floor, in units of ||G||_F (|p| + |q|)
 constexpr int kTileN = 64;
@@ -85,7 +85,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 // (entries carry errors of about eps sqrt(192) ||G||_F): pairs of columns far below the
 // largest could never meet the relative test.  Columns whose singular values cluster
 // near the noise converge slowly and may use up the sweeps; truncating A V keeps an exact
-// record of the error whether or not they did: G - B_H V_H^H = B_drop V_drop^H.  For the
+// record of the error whether or not they did: G - B_H V_H^H = B_drop V_drop^H.
+// FP64 is the cost here (GB300 runs it at a small fraction of its FP32 rate): one
+// sweep is ~25 MFLOP per block, so blocks are fitted once per canonical displacement.  For the
 // pair (p, q): g = p^H q = |g| e^{i phi}; with q~ = q e^{-i phi} the Gram matrix is real,
 // zeta = (|q|^2 - |p|^2) / (2 |g|), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
 // c = 1 / sqrt(1 + t^2), s = c t, and p <- c p - s q~, q <- s p + c q~.  Rounds pair
@@ -246,6 +248,33 @@ __global__ void cvfcnn_weights_kernel(const double2 *__restrict__ A, const doubl
             bi += bh * ((double)x.x + (double)x.y);
         }
         w[kCvB2 + u] = make_float2((float)-br, (float)-bi);
+    }
+}
+
+// Weights of displacement d = Q c from those of its canonical c: net_d(x) = S net_c(S^T x)
+// with S[U(u)][u] = +-1 (the symmetry map), i.e. W1_d[h][U(u)] = +-W1_c[h][u], b1_d = b1_c,
+// W2_d[U(u)][h] = +-W2_c[u][h], b2_d[U(u)] = +-b2_c[u].  One CTA per displacement.
+__global__ void cvfcnn_expand_kernel(const float2 *__restrict__ Wc, const int32_t *__restrict__ gcanon,
+                                     const int32_t *__restrict__ gsigma, const uint16_t *__restrict__ map,
+                                     float2 *__restrict__ Wd) {
+    const float2 *src = Wc + (size_t)gcanon[blockIdx.x] * kCvBlockElems;
+    float2 *out = Wd + (size_t)blockIdx.x * kCvBlockElems;
+    const uint16_t *m = map + (size_t)gsigma[blockIdx.x] * kNU;
+    for (int idx = threadIdx.x; idx < kNU * kCvHp; idx += blockDim.x) {
+        const int u = idx / kCvHp, h = idx % kCvHp;
+        const uint16_t e = m[u];
+        const float sg = (e & 0x100) ? -1.f : 1.f;
+        const float2 w1 = src[kCvW1 + idx];                          // W1^T[u][h]
+        out[kCvW1 + (size_t)(e & 0xFF) * kCvHp + h] = make_float2(sg * w1.x, sg * w1.y);
+        const float2 w2 = src[kCvW2 + (size_t)h * kNU + u];           // W2^T[h][u]
+        out[kCvW2 + (size_t)h * kNU + (e & 0xFF)] = make_float2(sg * w2.x, sg * w2.y);
+    }
+    for (int h = threadIdx.x; h < kCvHp; h += blockDim.x) out[kCvB1 + h] = src[kCvB1 + h];
+    for (int u = threadIdx.x; u < kNU; u += blockDim.x) {
+        const uint16_t e = m[u];
+        const float sg = (e & 0x100) ? -1.f : 1.f;
+        const float2 b = src[kCvB2 + u];
+        out[kCvB2 + (e & 0xFF)] = make_float2(sg * b.x, sg * b.y);
     }
 }
 
@@ -465,32 +494,36 @@ cvfcnn_translate_kernel(const WorkItem *__restrict__ items, const float2 *__rest
 
 }  // namespace
 
-ie_status launch_cvfcnn_fit(ie_plan p, const int32_t *blk_disp, cudaStream_t st) {
+ie_status launch_cvfcnn_fit(ie_plan p, const int32_t *canon_disp, int64_t ncanon, const int32_t *gcanon,
+                            const int32_t *gsigma, const uint16_t *map, cudaStream_t st) {
     const int64_t nblk = p->n_blocks;
-    if (nblk == 0) return IE_OK;
+    if (nblk == 0 || ncanon == 0) return IE_OK;
     IE_TRY(dalloc_t(p, &p->d_cvW, (size_t)nblk * kCvBlockElems));
-    const int64_t chunk = std::min(nblk, kCvFitChunk);
+    const bool expand = gcanon != nullptr;
+    const int64_t chunk = std::min(ncanon, kCvFitChunk);
     double2 *A = nullptr, *V = nullptr;
     double *tail = nullptr;
     int *sweeps = nullptr;
+    float2 *Wc = p->d_cvW;
     IE_CK(cudaMallocAsync(&A, (size_t)chunk * kNU * kNU * sizeof(double2), st));
     IE_CK(cudaMallocAsync(&V, (size_t)chunk * kNU * kNU * sizeof(double2), st));
     IE_CK(cudaMallocAsync(&tail, (size_t)chunk * sizeof(double), st));
     IE_CK(cudaMallocAsync(&sweeps, (size_t)chunk * sizeof(int), st));
+    if (expand) IE_CK(cudaMallocAsync(&Wc, (size_t)ncanon * kCvBlockElems * sizeof(float2), st));
     std::vector<double> h_tail(chunk);
     std::vector<int> h_sweeps(chunk);
     ie_status s = IE_OK;
     p->cv_sweeps = 0;
     p->cv_tail = 0.0;
-    for (int64_t b0 = 0; b0 < nblk && s == IE_OK; b0 += chunk) {
-        const int64_t m = std::min(chunk, nblk - b0);
+    for (int64_t b0 = 0; b0 < ncanon && s == IE_OK; b0 += chunk) {
+        const int64_t m = std::min(chunk, ncanon - b0);
         const int64_t threads = m * kSites * kSites;
         blocks_fp64_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(p->k, p->eta, p->a / kLattice,
-                                                                          blk_disp + 3 * b0, m, A);
+                                                                          canon_disp + 3 * b0, m, A);
         count_launches(1);
         jacobi_svd_kernel<<<(unsigned)m, kJacobiThreads, 0, st>>>(A, V, sweeps);
         count_launches(1);
-        cvfcnn_weights_kernel<<<(unsigned)m, 256, 0, st>>>(A, V, p->cv_hidden, p->d_cvW + b0 * kCvBlockElems, tail);
+        cvfcnn_weights_kernel<<<(unsigned)m, 256, 0, st>>>(A, V, p->cv_hidden, Wc + b0 * kCvBlockElems, tail);
         count_launches(1);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(h_tail.data(), tail, m * sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -506,10 +539,21 @@ ie_status launch_cvfcnn_fit(ie_plan p, const int32_t *blk_disp, cudaStream_t st)
             p->cv_tail = std::max(p->cv_tail, h_tail[i]);
         }
     }
+    if (s == IE_OK && expand) {
+        cvfcnn_expand_kernel<<<(unsigned)nblk, 256, 0, st>>>(Wc, gcanon, gsigma, map, p->d_cvW);
+        count_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            set_error("CVFCNN expansion: %s", cudaGetErrorString(e));
+            s = IE_ERR_CUDA;
+        }
+    }
     cudaFreeAsync(A, st);
     cudaFreeAsync(V, st);
     cudaFreeAsync(tail, st);
     cudaFreeAsync(sweeps, st);
+    if (expand) cudaFreeAsync(Wc, st);
     return s;
 }
 

@@ -250,8 +250,12 @@ ie_status launch_translate_simt(ie_plan p, const float2 *X, float2 *Yslab, int n
                                 const int *gate = nullptr);
 ie_status launch_translate_cvfcnn(ie_plan p, const float2 *X, float2 *Yslab, int nrhs, cudaStream_t st,
                                   const int *gate = nullptr);
-// fits the surrogate of every stored block (blk_disp: device, n_blocks x 3)
-ie_status launch_cvfcnn_fit(ie_plan p, const int32_t *blk_disp, cudaStream_t st);
+// fits the surrogates of the ncanon canonical displacements (device, ncanon x 3); with
+// gcanon / gsigma / map (device: per stored block its canonical index and signed
+// permutation, and the 48 x 192 symmetry map) every stored block gets its canonical
+// network turned into its own frame, else the canonical networks are the stored blocks'
+ie_status launch_cvfcnn_fit(ie_plan p, const int32_t *canon_disp, int64_t ncanon, const int32_t *gcanon,
+                            const int32_t *gsigma, const uint16_t *map, cudaStream_t st);
 ie_status launch_translate_tc(ie_plan p, int prec, float2 *Yslab, int nrhs, cudaStream_t st,
                               const int *gate = nullptr);
 ie_status launch_plane_wave(const ie_plan p, const double *d_khat, const double *d_pol, int nrhs, float2 *v,

@@ -45,7 +45,7 @@ def test_fit_statistics_and_block_order(tiny):
     ds, _ = oracle.pair_groups(tiny, oracle.FAR)
     canon = sorted({tuple(sorted(np.abs(d))) for d in ds})
     assert sorted(map(tuple, blocks)) == canon and len(blocks) == st["n_coupling_blocks"] == 16
-    assert st["cvfcnn_hidden"] == 50 and 2 <= st["cvfcnn_sweeps"] <= 30
+    assert st["cvfcnn_hidden"] == 50 and 2 <= st["cvfcnn_sweeps"] <= 16
     tails = [_svd_tail(oracle.coupling_block(tiny, np.array(c, dtype=np.int32)), 50) for c in canon]
     assert np.isclose(st["cvfcnn_tail"], max(tails), rtol=1e-6, atol=1e-14)
 
