@@ -19,7 +19,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--grid", type=int, default=10)
     ap.add_argument("--radius", type=float, default=4.0)
-    ap.add_argument("--prec", default="bf16x3", help="comma list of fp32,bf16x3,fp16x3,bf16x1")
+    ap.add_argument("--prec", default="bf16x3", help="comma list of fp32,bf16x3,fp16x3,bf16x1,fp16x1,cvfcnn")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--symmetry", type=int, default=0, choices=[0, 1])
@@ -34,7 +34,7 @@ def main():
     precs = [names[s] for s in args.prec.split(",")]
     boxes = W.sphere_shell(args.grid, args.radius)
     p = W.make_problem("profile", args.grid, boxes, 32, seed_P=61, alpha=1.0)
-    mask = ie.precmask(ie.IE_PREC_FP32, *precs)
+    mask = ie.precmask(*precs)
     with ie.Plan(ie.problem_from(p, mask, args.nrhs, symmetry=args.symmetry)) as plan:
         st = plan.stats
         c = torch.from_numpy(W.coefficients(p, args.nrhs, 62).astype(np.complex64)).cuda()
