@@ -13,7 +13,8 @@
 // relative error on inputs with independent entries is the SVD's Frobenius tail.
 //
 // Inference: one CTA per work item of the FP32 path (a displacement group's run of at
-// most 64 columns): the column scales, GEMM 1 (64 x 64 x 192) with the bias and the
+// most 64 columns): the column scales, GEMM 1 (64 x 64 x 192, 4 x 4 complex register
+// tile of two row pairs and two column pairs, 16-byte shared loads) with the bias and the
 // ReLU in its epilogue into shared memory, GEMM 2 (192 x 64 x 64), the bias, the
 // rescale and the scatter-add into the far-field slabs (with the symmetry maps when
 // the store is symmetry-compressed).  1.92x fewer multiply-adds than G_c x at H = 50.
@@ -351,8 +352,8 @@ cvfcnn_translate_kernel(const WorkItem *__restrict__ items, const float2 *__rest
         }
         cp_commit();
     };
-    const int hm = tid >> 4;      // hidden rows hm + 16 i
-    const int hn = tid & 15;      // columns hn + 16 j
+    const int hm = tid >> 4;      // hidden rows {2hm, 2hm+1} + 32 i
+    const int hn = tid & 15;      // columns {2hn, 2hn+1} + 32 j
     float2 z[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -373,9 +374,17 @@ cvfcnn_translate_kernel(const WorkItem *__restrict__ items, const float2 *__rest
         for (int kk = 0; kk < kKC; ++kk) {
             float2 a[4], b[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = S.u.s1.W[buf][kk][hm + 16 * i];
+            for (int i = 0; i < 2; ++i) {
+                const float4 v = *reinterpret_cast<const float4 *>(&S.u.s1.W[buf][kk][2 * hm + 32 * i]);
+                a[2 * i] = make_float2(v.x, v.y);
+                a[2 * i + 1] = make_float2(v.z, v.w);
+            }
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = S.u.s1.X[buf][kk][hn + 16 * j];
+            for (int j = 0; j < 2; ++j) {
+                const float4 v = *reinterpret_cast<const float4 *>(&S.u.s1.X[buf][kk][2 * hn + 32 * j]);
+                b[2 * j] = make_float2(v.x, v.y);
+                b[2 * j + 1] = make_float2(v.z, v.w);
+            }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -391,11 +400,11 @@ cvfcnn_translate_kernel(const WorkItem *__restrict__ items, const float2 *__rest
     // bias and Cartesian ReLU: h = relu(z / s + b1)
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const int row = hm + 16 * i;
+        const int row = 2 * hm + 32 * (i >> 1) + (i & 1);
         const float2 b1 = Wb[kCvB1 + row];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int col = hn + 16 * j;
+            const int col = 2 * hn + 32 * (j >> 1) + (j & 1);
             const float iv = S.inv[col];
             float2 h = make_float2(fmaxf(fmaf(z[i][j].x, iv, b1.x), 0.f), fmaxf(fmaf(z[i][j].y, iv, b1.y), 0.f));
             if (col >= ncols) h = make_float2(0.f, 0.f);

@@ -93,6 +93,23 @@ def test_fitted_far_product(symmetry, tiny):
     assert tail < 1e-4
 
 
+@pytest.mark.parametrize("tag", ["lfb8", "lfb256"])
+def test_fitted_far_product_at_the_papers_box_edges(tag):
+    """The paper trained its networks for a = lambda/8 and lambda/256 (§3)."""
+    p = W.lfb(W.tiny(), tag)
+    c = W.coefficients(p, 1, 973)
+    ref_net = oracle.cvfcnn_far_matvec(p, c, H=50)
+    ref = oracle.far_matvec(p, c)
+    with _plan(p, [ie.IE_PREC_CVFCNN], symmetry=1) as plan:
+        y = empty((1, p.n))
+        ie.ie_matvec(plan.handle, ie.IE_FAR, ie.IE_PREC_CVFCNN, dev(c), y, 1)
+        got = host(y)
+        tail = plan.stats["cvfcnn_tail"]
+    assert rel_l2(got, ref_net) <= NET_TOL
+    assert rel_l2(got, ref) <= 2 * rel_l2(ref_net, ref) + NET_TOL
+    assert tail < 1e-4
+
+
 def test_surrogate_solve_with_refinement(tiny):
     """GMRES on surrogate products to 1e-3, FP64 residuals of FP16X3 products outside:
     the answer meets 1e-5 against the dense LU of the exact system."""
