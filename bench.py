@@ -115,15 +115,18 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ distributed
-def dist_setup(args):
+def dist_setup(args, backend: str = "nccl"):
+    """One process per GPU from the launcher's environment (replicas: no data collective;
+    the process group serves the barriers and the max over ranks only)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
     return world, rank, local
 
 
@@ -138,9 +141,15 @@ def max_over_ranks(x: float, world: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_rate(world: int, units_per_rank: int, slowest_ms: float) -> float:
+    """Whole-job throughput of `world` replicas that each processed `units_per_rank` units,
+    timed by the slowest rank."""
+    return world * units_per_rank / (slowest_ms / 1e3)
 
 
 # ------------------------------------------------------------------ reference arm (FP64 CPU oracle)
@@ -243,7 +252,7 @@ def time_solves(ctx, plan, v, x, nrhs, opts, steps, warmup, clocks=False):
     barrier(ctx.world)
     lat = [a.elapsed_time(b) for a, b in ev]
     total = max_over_ranks(sum(lat), ctx.world)
-    return dict(solves_per_s=ctx.world * steps / (total / 1e3), ms=total / steps,
+    return dict(solves_per_s=aggregate_rate(ctx.world, steps, total), ms=total / steps,
                 p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
                 iterations=infos[-1]["iterations"], matvecs=infos[-1]["matvecs"],
                 refinements=infos[-1]["refinements"], relres=infos[-1]["relres"],
@@ -274,7 +283,8 @@ def time_far(ctx, plan, c, nrhs, precs, reps, warmup=3):
         s2 = ie.ie_plan_stats_get(plan.handle)
         ie.ie_plan_profile(plan.handle, False)
         k_ms = s2["translate_ms"] / max(1, s2["translate_launches"])
-        out[ie.PREC_NAMES[prec]] = dict(matvecs_per_s=ctx.world * 1e3 / mv_ms, ms=mv_ms, translate_kernel_ms=k_ms)
+        out[ie.PREC_NAMES[prec]] = dict(matvecs_per_s=aggregate_rate(ctx.world, 1, mv_ms), ms=mv_ms,
+                                        translate_kernel_ms=k_ms)
     return out
 
 
@@ -361,7 +371,7 @@ def run_shell16(ctx):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
-    e2e = {"value": world * args.steps / (e2e_ms / 1e3), "unit": "solves/s",
+    e2e = {"value": aggregate_rate(world, args.steps, e2e_ms), "unit": "solves/s",
            "h2d_bytes_per_step": int(vh.numel() * vh.element_size()),
            "d2h_bytes_per_step": int(xh.numel() * xh.element_size())}
 
