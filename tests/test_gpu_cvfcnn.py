@@ -155,3 +155,23 @@ def test_weights_need_a_surrogate_plan(tiny):
             y = empty((1, tiny.n))
             ie.ie_matvec(plan.handle, ie.IE_FAR, ie.IE_PREC_CVFCNN, dev(W.coefficients(tiny, 1, 1)), y, 1)
         assert e.value.status == ie.IE_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("symmetry", [0, 1])
+def test_batch_of_scatterers_with_their_own_rhs_counts(symmetry):
+    """Four scatterers in one plan, each translating only its own right-hand sides: the
+    network kernel runs the FP32 path's work items (runs of pairs with one column count)."""
+    b = W.small_batch()
+    R = b.max_rhs
+    members = [W.coefficients(m, R, 980 + g) for g, m in enumerate(b.members)]
+    for g, m in enumerate(b.members):
+        members[g][b.nrhs[g]:] = 0.0                      # padding columns stay zero
+    refs = [oracle.cvfcnn_far_matvec(m, c[:b.nrhs[g]], H=50) for g, (m, c) in enumerate(zip(b.members, members))]
+    pr = ie.problem_from_batch(b, ie.precmask(ie.IE_PREC_CVFCNN), symmetry=symmetry, exact_rhs=True)
+    with ie.Plan(pr) as plan:
+        y = empty((R, b.n))
+        ie.ie_matvec(plan.handle, ie.IE_FAR, ie.IE_PREC_CVFCNN, dev(np.concatenate(members, axis=1)), y, R)
+        for g, got in enumerate(b.split(host(y))):
+            q = b.nrhs[g]
+            assert rel_l2(got[:q], refs[g]) <= NET_TOL, g
+            assert not np.any(got[q:]), g
