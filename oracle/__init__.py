@@ -83,7 +83,7 @@ def _load():
         L.or_coupling_block.argtypes = [d, d, d, i, p, p]
         L.or_coupling_blocks.argtypes = [d, d, d, i, i64, p, p]
         L.or_plane_wave.argtypes = [d, d, i, i, i64, p, i64, p, p, p]
-        L.or_point_dipole_far.argtypes = [d, d, i64, p, p, p, p, p, p, p]
+        L.or_point_dipole_far.argtypes = [d, d, i64, p, p, p, p, p, p, p, p]
         L.or_point_fields.argtypes = [d, d, i64, p, i64, p, p, p]
         L.or_num_threads.restype = i
         _lib = L
@@ -520,11 +520,13 @@ def inverse_map_fields(k, eta, a, L, n_samples, radius_rel, E, pos, mom) -> comp
     return total
 
 
-def point_dipole_far(p, fun_off, pos, mom, c) -> np.ndarray:
+def point_dipole_far(p, fun_off, pos, mom, c, targets=None) -> np.ndarray:
     """Far part of the original subdomain system for point-dipole basis functions (box b's
     functions are listed in box order, p.nb[b] of them; pos relative to each box centre):
     y_f = sum over dipoles d of f of mom_d . E(r_d), E the field of c_g-weighted dipoles of
-    every function g in a box at Chebyshev distance >= 2 (eq. 3-4 with point sources)."""
+    every function g in a box at Chebyshev distance >= 2 (eq. 3-4 with point sources).
+    targets: box slots whose functions are computed (the result then holds those rows,
+    in basis_rows order); None = all."""
     fun_off = np.ascontiguousarray(fun_off, dtype=np.int64)
     n_fun = len(fun_off) - 1
     fun_box = np.repeat(np.arange(p.n_boxes, dtype=np.int32), np.asarray(p.nb, dtype=np.int64))
@@ -537,9 +539,14 @@ def point_dipole_far(p, fun_off, pos, mom, c) -> np.ndarray:
     m = _c128(np.asarray(mom).reshape(-1, 3))
     cc = _c128(np.asarray(c).reshape(-1))
     out = np.zeros(n_fun, dtype=np.complex128)
+    want = None
+    if targets is not None:
+        rows = basis_rows(p, targets)
+        want = np.zeros(n_fun, dtype=np.uint8)
+        want[rows] = 1
     _load().or_point_dipole_far(p.k, p.eta, n_fun, _ptr(fun_off), _ptr(fun_box), _ptr(ijk), _ptr(absolute),
-                                _ptr(m), _ptr(cc), _ptr(out))
-    return out
+                                _ptr(m), _ptr(cc), None if want is None else _ptr(want), _ptr(out))
+    return out if targets is None else out[basis_rows(p, targets)]
 
 
 # ---------------------------------------------------------------- §3 translation networks

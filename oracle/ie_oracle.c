@@ -209,10 +209,12 @@ void or_plane_wave(double k, double a, int L, int G, int64_t nbox, const int32_t
  * fun_off[f] .. fun_off[f+1]-1 at absolute positions pos and complex moments mom.
  *   out[f] = sum over dipoles d of f of  mom_d . sum over dipoles e of functions g whose
  *            box is at Chebyshev distance >= 2 from f's box of  D(r_d - r_e) (c_g mom_e)
- * c, out: [n_fun] complex.
+ * c, out: [n_fun] complex.  want (n_fun flags, or NULL for all): only the flagged outputs
+ * are computed, the others are set to 0.
  */
 void or_point_dipole_far(double k, double eta, int64_t n_fun, const int64_t *fun_off, const int32_t *fun_box,
-                         const int32_t *ijk, const double *pos, const double *mom, const double *c, double *out) {
+                         const int32_t *ijk, const double *pos, const double *mom, const double *c,
+                         const uint8_t *want, double *out) {
     int64_t nd = fun_off[n_fun];
     double *w = (double *)malloc(sizeof(double) * 6 * (size_t)(nd > 0 ? nd : 1));
     int32_t *dbox = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nd > 0 ? nd : 1));
@@ -229,6 +231,11 @@ void or_point_dipole_far(double k, double eta, int64_t n_fun, const int64_t *fun
     for (int64_t f = 0; f < n_fun; ++f) {
         const int32_t *tf = ijk + 3 * fun_box[f];
         double acc_r = 0.0, acc_i = 0.0;
+        if (want && !want[f]) {
+            out[2 * f] = 0.0;
+            out[2 * f + 1] = 0.0;
+            continue;
+        }
         for (int64_t d = fun_off[f]; d < fun_off[f + 1]; ++d) {
             double E[6] = {0, 0, 0, 0, 0, 0};
             for (int64_t e = 0; e < nd; ++e) {
