@@ -391,7 +391,9 @@ def run_shell16(ctx):
     cv_ach = pairs * 8 * 2 * 192 * st["cvfcnn_hidden"] / (far["cvfcnn"]["translate_kernel_ms"] / 1e3) / 1e12
     roofline_cvfcnn = {"bound": "alu", "achieved": cv_ach, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
                        "frac": cv_ach / FP32_SIMT_PEAK_TFLOPS, "kernel": "cvfcnn_translate_kernel",
-                       "traffic": profiled_traffic("cvfcnn_translate_fp32_shell16.md", "cvfcnn.cu"),
+                       "traffic": profiled_traffic("cvfcnn_translate_fp32_shell16.md",
+                                                           "cvfcnn.cu:struct SmemCv {",
+                                                           "cvfcnn.cu:cvfcnn_translate_kernel(const WorkItem"),
                        "hidden": st["cvfcnn_hidden"], "svd_tail_max": st["cvfcnn_tail"],
                        "jacobi_sweeps_max": st["cvfcnn_sweeps"],
                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}

@@ -728,20 +728,29 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
                 symmetry_map(map);
                 int32_t *d_cd = nullptr, *d_gc = nullptr, *d_gs = nullptr;
                 uint16_t *d_map = nullptr;
-                PC(cudaMallocAsync(&d_cd, canon_disp.size() * sizeof(int32_t), st));
-                PC(cudaMallocAsync(&d_gc, gcanon.size() * sizeof(int32_t), st));
-                PC(cudaMallocAsync(&d_gs, gsigma.size() * sizeof(int32_t), st));
-                PC(cudaMallocAsync(&d_map, map.size() * sizeof(uint16_t), st));
-                PC(cudaMemcpyAsync(d_cd, canon_disp.data(), canon_disp.size() * sizeof(int32_t),
-                                   cudaMemcpyHostToDevice, st));
-                PC(cudaMemcpyAsync(d_gc, gcanon.data(), gcanon.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-                PC(cudaMemcpyAsync(d_gs, gsigma.data(), gsigma.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-                PC(cudaMemcpyAsync(d_map, map.data(), map.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st));
-                ie_status fs = launch_cvfcnn_fit(p, d_cd, ncanon, d_gc, d_gs, d_map, st);
-                cudaFreeAsync(d_cd, st);
-                cudaFreeAsync(d_gc, st);
-                cudaFreeAsync(d_gs, st);
-                cudaFreeAsync(d_map, st);
+                cudaError_t ce = cudaMallocAsync(&d_cd, canon_disp.size() * sizeof(int32_t), st);
+                if (ce == cudaSuccess) ce = cudaMallocAsync(&d_gc, gcanon.size() * sizeof(int32_t), st);
+                if (ce == cudaSuccess) ce = cudaMallocAsync(&d_gs, gsigma.size() * sizeof(int32_t), st);
+                if (ce == cudaSuccess) ce = cudaMallocAsync(&d_map, map.size() * sizeof(uint16_t), st);
+                if (ce == cudaSuccess)
+                    ce = cudaMemcpyAsync(d_cd, canon_disp.data(), canon_disp.size() * sizeof(int32_t),
+                                         cudaMemcpyHostToDevice, st);
+                if (ce == cudaSuccess)
+                    ce = cudaMemcpyAsync(d_gc, gcanon.data(), gcanon.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+                if (ce == cudaSuccess)
+                    ce = cudaMemcpyAsync(d_gs, gsigma.data(), gsigma.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+                if (ce == cudaSuccess)
+                    ce = cudaMemcpyAsync(d_map, map.data(), map.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st);
+                ie_status fs = IE_OK;
+                if (ce == cudaSuccess) {
+                    fs = launch_cvfcnn_fit(p, d_cd, ncanon, d_gc, d_gs, d_map, st);
+                } else {
+                    cudaGetLastError();
+                    set_error("CVFCNN fit set-up: %s", cudaGetErrorString(ce));
+                    fs = IE_ERR_CUDA;
+                }
+                for (void *ptr : {(void *)d_cd, (void *)d_gc, (void *)d_gs, (void *)d_map})
+                    if (ptr) cudaFreeAsync(ptr, st);
                 PT(fs);
             }
         }

@@ -513,15 +513,21 @@ ie_status launch_cvfcnn_fit(ie_plan p, const int32_t *canon_disp, int64_t ncanon
     double2 *A = nullptr, *V = nullptr;
     double *tail = nullptr;
     int *sweeps = nullptr;
-    float2 *Wc = p->d_cvW;
-    IE_CK(cudaMallocAsync(&A, (size_t)chunk * kNU * kNU * sizeof(double2), st));
-    IE_CK(cudaMallocAsync(&V, (size_t)chunk * kNU * kNU * sizeof(double2), st));
-    IE_CK(cudaMallocAsync(&tail, (size_t)chunk * sizeof(double), st));
-    IE_CK(cudaMallocAsync(&sweeps, (size_t)chunk * sizeof(int), st));
-    if (expand) IE_CK(cudaMallocAsync(&Wc, (size_t)ncanon * kCvBlockElems * sizeof(float2), st));
+    float2 *Wc = nullptr;
+    cudaError_t ae = cudaMallocAsync(&A, (size_t)chunk * kNU * kNU * sizeof(double2), st);
+    if (ae == cudaSuccess) ae = cudaMallocAsync(&V, (size_t)chunk * kNU * kNU * sizeof(double2), st);
+    if (ae == cudaSuccess) ae = cudaMallocAsync(&tail, (size_t)chunk * sizeof(double), st);
+    if (ae == cudaSuccess) ae = cudaMallocAsync(&sweeps, (size_t)chunk * sizeof(int), st);
+    if (ae == cudaSuccess && expand) ae = cudaMallocAsync(&Wc, (size_t)ncanon * kCvBlockElems * sizeof(float2), st);
+    float2 *Wfit = expand ? Wc : p->d_cvW;
     std::vector<double> h_tail(chunk);
     std::vector<int> h_sweeps(chunk);
     ie_status s = IE_OK;
+    if (ae != cudaSuccess) {
+        cudaGetLastError();
+        set_error("CVFCNN fit scratch: %s", cudaGetErrorString(ae));
+        s = ae == cudaErrorMemoryAllocation ? IE_ERR_OOM : IE_ERR_CUDA;
+    }
     p->cv_sweeps = 0;
     p->cv_tail = 0.0;
     for (int64_t b0 = 0; b0 < ncanon && s == IE_OK; b0 += chunk) {
@@ -532,7 +538,7 @@ ie_status launch_cvfcnn_fit(ie_plan p, const int32_t *canon_disp, int64_t ncanon
         count_launches(1);
         jacobi_svd_kernel<<<(unsigned)m, kJacobiThreads, 0, st>>>(A, V, sweeps);
         count_launches(1);
-        cvfcnn_weights_kernel<<<(unsigned)m, 256, 0, st>>>(A, V, p->cv_hidden, Wc + b0 * kCvBlockElems, tail);
+        cvfcnn_weights_kernel<<<(unsigned)m, 256, 0, st>>>(A, V, p->cv_hidden, Wfit + b0 * kCvBlockElems, tail);
         count_launches(1);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(h_tail.data(), tail, m * sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -558,11 +564,8 @@ ie_status launch_cvfcnn_fit(ie_plan p, const int32_t *canon_disp, int64_t ncanon
             s = IE_ERR_CUDA;
         }
     }
-    cudaFreeAsync(A, st);
-    cudaFreeAsync(V, st);
-    cudaFreeAsync(tail, st);
-    cudaFreeAsync(sweeps, st);
-    if (expand) cudaFreeAsync(Wc, st);
+    for (void *ptr : {(void *)A, (void *)V, (void *)tail, (void *)sweeps, (void *)Wc})
+        if (ptr) cudaFreeAsync(ptr, st);
     return s;
 }
 
