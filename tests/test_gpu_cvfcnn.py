@@ -175,3 +175,18 @@ def test_batch_of_scatterers_with_their_own_rhs_counts(symmetry):
             q = b.nrhs[g]
             assert rel_l2(got[:q], refs[g]) <= NET_TOL, g
             assert not np.any(got[q:]), g
+
+
+@pytest.mark.parametrize("symmetry", [0, 1])
+def test_footprint_covers_the_surrogate_plan(symmetry):
+    """ie_plan_footprint (host only) bounds what a plan with the networks holds on the
+    device (it also counts the fit's scratch, freed before the plan returns)."""
+    p = W.shell16()
+    p.alpha = W.alpha_for("shell16")
+    pr = ie.problem_from(p, ie.precmask(ie.IE_PREC_FP32, ie.IE_PREC_CVFCNN), symmetry=symmetry)
+    fp = ie.ie_plan_footprint(pr)
+    with ie.Plan(pr) as plan:
+        held = plan.stats["device_bytes"]
+    assert held <= fp
+    nblk = 473 if symmetry else 16540
+    assert held >= nblk * 198656           # the networks themselves
