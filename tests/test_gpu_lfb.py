@@ -1,4 +1,4 @@
-"""Low-frequency regime: box edge lambda/8 and lambda/256 (§3, §6).
+"""Low-frequency regime: box edge lambda/8 and lambda/256 (§3, §5).
 
 At lambda/256 every interaction is quasi-static.  The reactive (imaginary) part of the
 dyad exceeds its radiative (real) part by about 3/(kR)^3, 6e4 at the closest far site

@@ -24,7 +24,7 @@ discretisation, §5):
            1..4 plane waves each (seed 51).
   *_lfb8, *_lfb256
            the same geometry and seeds with box edge a = lambda/8 or lambda/256
-           (the paper's low-frequency regime, §3 and §6).  The closest far site
+           (the paper's low-frequency regime, §3 and §5).  The closest far site
            pairs then have kR = 0.98 or 0.031; at lambda/256 a shell16 object is
            1/16 wavelength across, so every interaction is quasi-static and the
            1/(kR)^2 terms of the dyad dominate.
