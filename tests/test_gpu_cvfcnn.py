@@ -190,3 +190,16 @@ def test_footprint_covers_the_surrogate_plan(symmetry):
     assert held <= fp
     nblk = 473 if symmetry else 16540
     assert held >= nblk * 198656           # the networks themselves
+
+
+@pytest.mark.parametrize("hidden", [1, 64])
+def test_hidden_width_limits(hidden, tiny):
+    """The narrowest network and the widest the kernel holds (no padding rows)."""
+    c = W.coefficients(tiny, 1, 974)
+    ref_net = oracle.cvfcnn_far_matvec(tiny, c, H=hidden)
+    with _plan(tiny, [ie.IE_PREC_CVFCNN], symmetry=1, hidden=hidden) as plan:
+        assert plan.stats["cvfcnn_hidden"] == hidden
+        y = empty((1, tiny.n))
+        ie.ie_matvec(plan.handle, ie.IE_FAR, ie.IE_PREC_CVFCNN, dev(c), y, 1)
+        got = host(y)
+    assert rel_l2(got, ref_net) <= NET_TOL
