@@ -192,9 +192,13 @@ def test_footprint_covers_the_surrogate_plan(symmetry):
     assert held >= nblk * 198656           # the networks themselves
 
 
-@pytest.mark.parametrize("hidden", [1, 64])
+@pytest.mark.parametrize("hidden", [2, 64])
 def test_hidden_width_limits(hidden, tiny):
-    """The narrowest network and the widest the kernel holds (no padding rows)."""
+    """A narrow network and the widest the kernel holds (no padding rows).  Width 1 is left
+    out on purpose: blocks of axis and diagonal displacements are symmetric under rotations
+    about d, so their two largest singular values are equal and a rank-1 network is not
+    unique (any vector of that plane is correct); 2 is the narrowest width whose truncation
+    is unique on this grid (relative gap 0.2 or more)."""
     c = W.coefficients(tiny, 1, 974)
     ref_net = oracle.cvfcnn_far_matvec(tiny, c, H=hidden)
     with _plan(tiny, [ie.IE_PREC_CVFCNN], symmetry=1, hidden=hidden) as plan:
