@@ -5,6 +5,11 @@ with s = ||x||_inf in FP32, inside Alg. 2 in place of G_d x.  Fitted weights put
 network in its linear regime, equal to the truncated SVD of G_c; each side fits its own
 (Jacobi SVD on the GPU, LAPACK in the oracle), and the networks' outputs are unique.
 
+Uniqueness: where sigma_H = sigma_H+1 the truncation (hence the network) is not unique.  At
+H = 50 that happens on seven of shell16's 473 classes, all with sigma_50 <= 1.1e-8 sigma_1,
+so either choice moves the output by less than that; widths whose cutoff splits a large
+degenerate pair (H = 1 for axis and diagonal displacements) are not compared.
+
 Tolerances.  Network against network: FP32 sums of 192 and H terms plus the hidden bias,
 which is up to sqrt(192) times the hidden signal and cancels in the output bias: about
 25 x 6e-8 x sqrt(H) ~ 1e-5 relative, so 3e-5.  Network against the exact translation:
