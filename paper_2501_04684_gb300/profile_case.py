@@ -5,6 +5,9 @@ a few GB, runs `--reps` far-zone products in each requested precision and exits.
 Example (the translation kernel of one BF16X3 product):
 
   python -m paper_2501_04684_gb300.profile_case --grid 10 --radius 4 --prec bf16x3
+
+With --prec cvfcnn the plan fits the translation networks (FP64 Jacobi SVDs); --map N also
+runs the mapping construction for N boxes' worth of seeded point-dipole functions.
 """
 from __future__ import annotations
 
@@ -23,6 +26,8 @@ def main():
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--symmetry", type=int, default=0, choices=[0, 1])
+    ap.add_argument("--map", type=int, default=0,
+                    help="also map this many boxes' worth of seeded point-dipole functions (ie_map_basis)")
     args = ap.parse_args()
     import numpy as np
     import torch
@@ -43,6 +48,9 @@ def main():
             for _ in range(args.reps):
                 ie.ie_matvec(plan.handle, ie.IE_FAR, prec, c, y, args.nrhs)
         torch.cuda.synchronize()
+        if args.map:
+            fun_off, pos, mom = W.point_dipole_basis(p.nb[:args.map], 63, a=p.a)
+            ie.ie_map_basis(p.k, p.eta, p.a, fun_off, pos, mom, tikhonov=W.MAPPED_TIKHONOV)
         print(f"profile case: {st['n_boxes']} boxes, {st['n_far_pairs']} far pairs, {st['n_far_disp']} groups "
               f"on {st['n_coupling_blocks']} stored blocks, "
               f"{st['device_bytes'] / 1e9:.2f} GB on the device; precisions {args.prec} x {args.reps}")
