@@ -468,15 +468,12 @@ def test_mapping_reproduces_a_uniform_dipole(a):
 
 
 def test_mapping_superposition_over_the_dipoles_of_a_function():
+    """A function made of three dipoles maps to the sum of the rows of its dipoles alone."""
     a = W.BOX_EDGE
-    fun_off, pos, mom = W.point_dipole_basis([3], 910, a=a, max_dipoles=3)
-    fun_off = np.array([0, 3], dtype=np.int64)
-    pos, mom = pos[:3], mom[:3]
-    if len(pos) < 3:
-        pos = np.vstack([pos, [[0.01, -0.02, 0.03]] * (3 - len(pos))])
-        mom = np.vstack([mom, [[1, 1j, 0]] * (3 - len(mom))])
-    whole, _ = oracle.map_basis(K, ETA, a, 4, 128, 1.5, fun_off, pos, mom)
-    parts, _ = oracle.map_basis(K, ETA, a, 4, 128, 1.5, np.arange(4, dtype=np.int64), pos, mom)
+    singles, pos, mom = W.point_dipole_basis([3], 910, a=a, max_dipoles=1)   # three one-dipole functions
+    assert list(singles) == [0, 1, 2, 3]
+    whole, _ = oracle.map_basis(K, ETA, a, 4, 128, 1.5, np.array([0, 3], dtype=np.int64), pos, mom)
+    parts, _ = oracle.map_basis(K, ETA, a, 4, 128, 1.5, singles, pos, mom)
     assert np.linalg.norm(whole[0] - parts.sum(0)) <= 1e-10 * np.linalg.norm(whole[0])
 
 
