@@ -391,7 +391,8 @@ ie_status ie_plan_blocks(ie_plan plan, int32_t *disp);
  * complex64 (re, im interleaved), per stored block in ie_plan_blocks order, H the
  * plan's cvfcnn_hidden:  W1 [blocks][H][192], b1 [blocks][H], W2 [blocks][192][H],
  * b2 [blocks][192].  The network of block c maps x to s (W2 relu(W1 x / s + b1) + b2),
- * s = max_u |x_u| (0 for x = 0); with symmetry = 1 displacement d = Q c applies it in
+ * relu(z) = max(Re z, 0) + j max(Im z, 0) elementwise, s = max_u |x_u| (0 for x = 0);
+ * with symmetry = 1 displacement d = Q c applies it in
  * the frame of c (input through S_Q^T, output through S_Q).  Synchronises stream. */
 ie_status ie_cvfcnn_set_weights(ie_plan plan, const float *W1, const float *b1, const float *W2, const float *b2,
                                 void *stream);
