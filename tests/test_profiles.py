@@ -1,0 +1,25 @@
+"""The committed ncu summaries: short text files, each giving the full command that made it
+(with --clock-control none), and the kernel summaries recording the digest of the kernel
+code they were taken on (bench.py reports their DRAM traffic only while it matches)."""
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+KERNEL_SUMMARIES = ("translate_tc_fp16x3_shell16.md", "translate_simt_fp32_shell16.md",
+                    "cvfcnn_translate_fp32_shell16.md")
+
+
+def test_profiles_are_short_text_with_their_commands():
+    d = os.path.join(ROOT, "profiles")
+    for name in os.listdir(d):
+        assert name.endswith((".md", ".txt")), name
+        text = open(os.path.join(d, name)).read()
+        assert len(text) < 16_000, name
+        assert "ncu " in text and "--clock-control none" in text, name
+
+
+def test_kernel_summaries_record_code_digest_and_traffic():
+    for name in KERNEL_SUMMARIES:
+        text = open(os.path.join(ROOT, "profiles", name)).read()
+        assert re.search(r"^kernel_code_sha256_16: [0-9a-f]{16}$", text, re.M), name
+        assert re.search(r"^traffic_bytes_per_launch: [0-9]+$", text, re.M), name
