@@ -31,3 +31,9 @@ def test_identity_tiny_and_mapped_alphas():
     assert p.P is None and np.all(p.nb == W.NU) and p.n == 64 * W.NU
     for name in ("tiny_mapped", "shell16_mapped"):
         assert W.alpha_for(name) > 0
+
+
+def test_every_bench_variant_has_its_frozen_alpha():
+    """bench.py --lfb lfb8|lfb256 and --mapped solve systems whose alpha make_alpha.py froze."""
+    for name in ["shell16", "shell32"] + [f"shell16_{t}" for t in W.LFB_EDGES] + ["shell16_mapped"]:
+        assert W.alpha_for(name) > 0, name

@@ -40,6 +40,7 @@ BUILDERS = {
     "shell32": lambda: W.shell32(),
     "tiny_lfb8": lambda: W.lfb(W.tiny(), "lfb8"),
     "tiny_lfb256": lambda: W.lfb(W.tiny(), "lfb256"),
+    "shell16_lfb8": lambda: W.lfb(W.shell16(), "lfb8"),
     "shell16_lfb256": lambda: W.lfb(W.shell16(), "lfb256"),
     "tiny_mapped": lambda: mapped(W.tiny()),
     "shell16_mapped": lambda: mapped(W.shell16()),
