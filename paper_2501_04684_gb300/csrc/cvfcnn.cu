@@ -4,13 +4,16 @@
 // by s = ||x||_inf, the hidden layer is z = W1 x / s + b1 with the Cartesian ReLU
 // max(Re z, 0) + j max(Im z, 0), the output s (W2 h + b2) replaces G_c x in Alg. 2.
 //
-// Weights (plan creation): the block is regenerated in FP64, its SVD G = U S V^H is
-// computed by one-sided Jacobi (one CTA per block, Hestenes rotations on the columns,
-// round-robin pairing), and the network is set to its linear regime on the unit
+// Weights (plan creation), once per canonical displacement c = sorted |d|: the block is
+// regenerated in FP64, its SVD G = U S V^H is computed by one-sided Jacobi (one CTA per
+// block, Hestenes rotations on the columns, round-robin pairing), and the network is set
+// to its linear regime on the unit
 // l-inf ball: W1 = V_H^H, W2 = U_H S_H, b1_h = beta_h (1 + j) with beta_h the l1 norm
 // of row h of W1 (so Re and Im of W1 x/s + b1 stay >= 0), b2 = -W2 b1.  The output is
 // then U_H S_H V_H^H x: the best rank-H approximation of G_c (Eckart-Young), whose
-// relative error on inputs with independent entries is the SVD's Frobenius tail.
+// relative error on inputs with independent entries is the SVD's Frobenius tail.  With
+// the symmetric store the canonical networks are the stored ones; with the full store
+// each displacement d = Q c gets the canonical network turned into its frame.
 //
 // Inference: one CTA per work item of the FP32 path (a displacement group's run of at
 // most 64 columns): the column scales, GEMM 1 (64 x 64 x 192, 4 x 4 complex register
