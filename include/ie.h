@@ -236,11 +236,11 @@ ie_status ie_disaggregate(ie_plan plan, const void *Y, void *r, int nrhs, void *
  * counterpart; it serves callers that cannot allocate device memory at call time,
  * e.g. code whose device memory belongs to another allocator's pool, or a latency-
  * critical loop where cudaMalloc / cudaFree could block or synchronise the device).
- * Same arithmetic and result as ie_translate; it calls no allocator.  Its scratch is
- * a fixed 32 MiB device area inside libie (held by every GPU that loads the library
- * until exit) that must hold 8 x nrhs x n_boxes x 192 complex64 partial sums plus
- * the group offsets; larger requests return IE_ERR_INVALID with the sizes in
- * ie_last_error().  The first call on a device looks the area up and sets the kernel
+ * Same arithmetic and result as ie_translate; it calls no allocator and copies nothing from host memory (the
+ * displacement-group offsets it reads were put on the device with the plan).  Its
+ * scratch is a fixed 32 MiB device area inside libie (held by every GPU that loads the
+ * library until exit) that must hold 8 x nrhs x n_boxes x 192 complex64 partial sums;
+ * larger requests return IE_ERR_INVALID with the sizes in ie_last_error().  The first call on a device looks the area up and sets the kernel
  * up on that device (make it before any stream capture).  Every call reuses the same
  * area, so calls that overlap in time on the GPU (any streams, any plans) race; the
  * partial sums are cleared by each call.  X, Y: device complex64 [nrhs][n_boxes][192].

@@ -322,6 +322,7 @@ size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, i
     add((nbox + 1) * sizeof(int64_t));
     add(nbox * 3 * sizeof(int32_t));
     add(nd * 3 * sizeof(int32_t));
+    add((nd + 1) * sizeof(int64_t));
     add(npairs * sizeof(int32_t));
     add(npairs * sizeof(int32_t));
     const bool sym = pr->symmetry == 1;
@@ -669,9 +670,12 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
     // far groups and coupling blocks
     if (p->n_far_disp) {
         PT(dalloc_t(p, &p->d_disp, fg.disp.size()));
+        PT(dalloc_t(p, &p->d_gstart, fg.start.size()));
         PT(dalloc_t(p, &p->d_src, fg.src.size()));
         PT(dalloc_t(p, &p->d_dst, fg.dst.size()));
         PC(cudaMemcpyAsync(p->d_disp, fg.disp.data(), fg.disp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        PC(cudaMemcpyAsync(p->d_gstart, p->h_gstart.data(), p->h_gstart.size() * sizeof(int64_t),
+                           cudaMemcpyHostToDevice, st));
         PC(cudaMemcpyAsync(p->d_src, fg.src.data(), fg.src.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         PC(cudaMemcpyAsync(p->d_dst, fg.dst.data(), fg.dst.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
         const int32_t *gen_disp = p->d_disp;

@@ -160,6 +160,7 @@ struct ie_plan_s {
     int64_t n_far_disp = 0, n_far_pairs = 0;
     std::vector<int32_t> h_disp;       // n_far_disp x 3
     std::vector<int64_t> h_gstart;     // n_far_disp + 1 (pair offsets)
+    int64_t *d_gstart = nullptr;       // n_far_disp + 1, device copy of h_gstart
     int32_t *d_disp = nullptr;         // n_far_disp x 3
     int32_t *d_src = nullptr, *d_dst = nullptr;   // [n_far_pairs], sorted by displacement
     float2 *d_Csimt = nullptr;         // [n_far_disp][192 (k)][192 (m)] complex64

@@ -271,9 +271,8 @@ extern "C" ie_status ie_translate_noalloc(ie_plan p, const void *X, void *Y, int
         return set_error("ie_translate_noalloc runs the FP32 translation over a full block store; this plan has "
                          "no FP32 store or a symmetry-compressed one"),
                IE_ERR_UNSUPPORTED;
-    size_t off_bytes = ((size_t)(p->n_far_disp + 1) * sizeof(int64_t) + 255) / 256 * 256;
     size_t stride = (size_t)nrhs * p->nbox * kNU;                 // float2 per slab
-    size_t need = off_bytes + (size_t)kSlabs * stride * sizeof(float2);
+    size_t need = (size_t)kSlabs * stride * sizeof(float2);
     if (need > kNoAllocScratchBytes)
         return set_error("ie_translate_noalloc needs %zu bytes of scratch for %d boxes x %d rhs; the fixed area "
                          "holds %zu bytes (use ie_translate)", need, p->nbox, nrhs, kNoAllocScratchBytes),
@@ -286,15 +285,13 @@ extern "C" ie_status ie_translate_noalloc(ie_plan p, const void *X, void *Y, int
     void *base = nullptr;
     IE_TRY(noalloc_scratch(&base));
     cudaStream_t st = (cudaStream_t)stream;
-    int64_t *d_gstart = reinterpret_cast<int64_t *>(base);
-    float2 *slabs = reinterpret_cast<float2 *>(static_cast<unsigned char *>(base) + off_bytes);
+    float2 *slabs = reinterpret_cast<float2 *>(base);
     // the area keeps the previous call's contents: the slabs must start at zero
     IE_TRY(launch_zero(slabs, (size_t)kSlabs * stride * sizeof(float2), st));
     if (p->n_far_disp > 0) {
-        IE_CK(cudaMemcpyAsync(d_gstart, p->h_gstart.data(), (size_t)(p->n_far_disp + 1) * sizeof(int64_t),
-                              cudaMemcpyHostToDevice, st));
+        // group offsets: the plan's device copy, uploaded once when the plan was built
         translate_simt_grouped_kernel<<<dim3((unsigned)p->n_far_disp, (unsigned)runs), kThreads, sizeof(SmemSimt),
-                                        st>>>(d_gstart, p->d_Csimt, p->d_src, p->d_dst, (const float2 *)X, slabs,
+                                        st>>>(p->d_gstart, p->d_Csimt, p->d_src, p->d_dst, (const float2 *)X, slabs,
                                               stride, p->nbox, nrhs, per);
         IE_CK_LAUNCH();
     }
