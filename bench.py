@@ -1,13 +1,20 @@
 #!/usr/bin/env python
 """Benchmark of the group-by-group far-zone solver on one workload.
 
-A step is one full GMRES solve of the 16^3 sphere-shell scatterer (1,264 boxes,
-40,448 basis unknowns, plane-wave excitation): every GMRES iteration runs the
-mapping (Alg. 1), the displacement-grouped translation (Alg. 2), the inverse
-mapping (Alg. 3), the stored near product and the Arnoldi/Givens update on the
-GPU.  Coupling blocks are generated once per plan (amortised, timed separately).
+Default (the headline line): the 32^3 sphere-shell scatterer (5,000 boxes, 160,000
+basis unknowns, 24.9 M far box pairs, plane-wave excitation).  A step is one full
+solve to a relative residual of 1e-5 in the mixed form: GMRES(50) on FP16X3 tensor-
+core products inside an outer FP64 refinement loop.  Every GMRES iteration runs the
+mapping (Alg. 1), the displacement-grouped translation (Alg. 2), the inverse mapping
+(Alg. 3), the stored near product and the Arnoldi/Givens update on the GPU.  The
+same solve in plain FP32 (FP32 SIMT products) and the other mixed forms are timed
+on the same plan; far-zone products/s per precision, the translation kernel's
+roofline, the FP64 CPU oracle on a box subsample and a bounded serving run (config
+5) go into the same JSON line.  Coupling blocks are generated once per plan
+(amortised, timed separately).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload shell32|shell16|batch64|serve]
 
 N > 1 runs under torchrun: every rank solves its own replica (no collective on the
 data path; scaling "weak"), timing = max over ranks.  Rank 0 prints one JSON line.
@@ -31,6 +38,12 @@ METRIC = "far-zone matvecs/s + GMRES solves/s (p50/p99) mixed vs plain FP32, sam
 WORKLOAD = ("shell16: 16^3 grid of a=lambda/4 boxes, sphere shell r=7 boxes (1,264 boxes, 40,448 basis unknowns, "
             "242,688 dipole unknowns, 1,575,248 far pairs in 16,540 displacement groups), nb=32, "
             "x-polarised plane wave along +z, GMRES(50)")
+WORKLOAD32 = ("shell32: 32^3 grid of a=lambda/4 boxes, sphere shell r=14 boxes (5,000 boxes, 160,000 basis unknowns, "
+              "960,000 dipole unknowns, 24,910,952 far pairs in 112,160 displacement groups), nb=32, "
+              "x-polarised plane wave along +z, GMRES(50), rel. residual 1e-5")
+HEAD32 = "mixed_fp16x3"          # the headline path of the shell32 line
+CPU_SAMPLE_BOXES = 64            # target boxes of the oracle's timed sample (cpu_baseline)
+REF_SAMPLE_BOXES = 8             # target boxes per step of the reference arm
 FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 
@@ -40,9 +53,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="shell16", choices=["shell16", "shell32", "batch64", "serve"],
-                    help="shell16 is the headline line; the others measure the precision, batching and "
-                         "serving workloads")
+    ap.add_argument("--workload", default="shell32", choices=["shell32", "shell16", "batch64", "serve"],
+                    help="shell32 is the headline line (with a bounded serving record); the others measure "
+                         "the plain-path shell, batching and serving workloads on their own")
+    ap.add_argument("--no-serve", action="store_true", help="shell32: leave out the bounded serving record")
     ap.add_argument("--lfb", default=None, choices=["lfb8", "lfb256"],
                     help="shell16 only: the same geometry with box edge lambda/8 or lambda/256 "
                          "(low-frequency regime)")
@@ -52,6 +66,8 @@ def parse():
     ap.add_argument("--symmetry", type=int, default=0, choices=[0, 1],
                     help="1: symmetry-compressed coupling store (one block per sorted |d|)")
     ap.add_argument("--requests", type=int, default=12, help="serve: requests per run")
+    ap.add_argument("--record-requests", type=int, default=6,
+                    help="shell32: requests of the bounded serving record")
     ap.add_argument("--serve-load", type=float, nargs="+", default=[0.5, 0.9],
                     help="serve: offered loads as fractions of the plain form's capacity")
     ap.add_argument("--serve-batch", type=int, default=4, help="serve: most requests merged into one plan")
@@ -153,42 +169,75 @@ def aggregate_rate(world: int, units_per_rank: int, slowest_ms: float) -> float:
 
 
 # ------------------------------------------------------------------ reference arm (FP64 CPU oracle)
+def shell32_config(symmetry: int = 0, world: int = 1) -> dict:
+    """`config` of the headline line, shared by both arms."""
+    return {"workload": WORKLOAD32, "path": HEAD32,
+            "path_desc": ("outer FP64 refinement (residual r = v - Z x from FP16X3 products, differences and norms "
+                          "in FP64) around GMRES(50) on FP16X3 tcgen05 products (fp16 hi+lo split, FP32 "
+                          "accumulate, FP32 Krylov vectors, FP64 dots and Givens) to 5e-6; stop at 1e-5"),
+            "tol": 1e-5, "nrhs": 1, "symmetry": symmetry,
+            "l2": "no flush needed: each product streams >= 33 GB of coupling images (> 129 MB L2)",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
+def oracle_sample_time(p, nboxes: int, seed_c: int, seed_sub: int, reps: int = 1):
+    """Wall time of the FP64 brute-force oracle product (near + far) on `nboxes` seeded
+    target boxes; the median of `reps` runs."""
+    import oracle
+    import workloads as W
+    c = W.coefficients(p, 1, seed_c)
+    targets = W.subsample_boxes(p, nboxes, seed_sub)
+    oracle.build()
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.operator(p, c, "full", targets=targets)
+        times.append(time.perf_counter() - t0)
+    return statistics.median(times), len(targets), times
+
+
 def run_reference(args):
+    """The FP64 CPU oracle on the headline workload: every step is the brute-force product
+    on REF_SAMPLE_BOXES seeded target boxes (the work that is timed); `value` scales that
+    to whole solves (full product x the products of the oracle's own GMRES)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import numpy as np
-
     import oracle
     import workloads as W
-    p = W.shell16()
-    p.alpha = W.alpha_for("shell16")
-    c = W.coefficients(p, 1, W.SEED_C["shell16"])
-    targets = W.subsample_boxes(p, 8, W.SEED_SUBSAMPLE["shell16"])
-    iters = oracle_products("shell16", HEADLINE_TOL)
-    if iters is None:
-        print(json.dumps({"impl": "reference", "unavailable": "workloads/oracle_solve.json has no shell16 entry "
-                                                               "(run workloads/make_oracle_solve.py shell16)"}))
+    name = args.workload if args.workload in ("shell16", "shell32") else "shell32"
+    p = W.shell32() if name == "shell32" else W.shell16()
+    p.alpha = W.alpha_for(name)
+    tol = 1e-5 if name == "shell32" else HEADLINE_TOL
+    prods = oracle_products(name, tol)
+    if prods is None:
+        print(json.dumps({"impl": "reference", "unavailable": f"workloads/oracle_solve.json has no {name} entry "
+                                                               f"(run workloads/make_oracle_solve.py {name})"}))
         return
     oracle.build()
+    c = W.coefficients(p, 1, W.SEED_C[name])
+    targets = W.subsample_boxes(p, REF_SAMPLE_BOXES, W.SEED_SUBSAMPLE[name])
     for _ in range(args.warmup):
-        oracle.operator(p, c, "full", targets=targets[:1])
+        oracle.operator(p, c, "full", targets=targets)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
         oracle.operator(p, c, "full", targets=targets)
         times.append(time.perf_counter() - t0)
-    t_sample = statistics.median(times)
-    t_matvec = t_sample * p.n_boxes / len(targets)
-    solves_per_s = 1.0 / (iters * t_matvec)
-    sample = (f"brute-force FP64 oracle product (near + far, site pair by site pair) on {len(targets)} of "
-              f"{p.n_boxes} target boxes, scaled to a full product x {iters} products (the oracle's own "
-              f"GMRES(50) to the same tolerance)")
+    t_step = statistics.median(times)
+    t_solve = t_step * p.n_boxes / len(targets) * prods
+    solves_per_s = 1.0 / t_solve
+    sample = (f"each step: brute-force FP64 oracle product (near + far, site pair by site pair) on {len(targets)} of "
+              f"{p.n_boxes} target boxes ({1e3 * t_step:.0f} ms); value extrapolated: x {p.n_boxes / len(targets):.0f} "
+              f"to a full product, x {prods} products (the oracle's own GMRES(50) on this system to {tol:g})")
+    config = shell32_config() if name == "shell32" else {"workload": WORKLOAD}
     line = {"impl": "reference", "metric": METRIC, "value": solves_per_s, "unit": "solves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / solves_per_s,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD},
+            "config": config,
+            "value_basis": "extrapolated from the timed sample steps (ms_per_step is the sample's own time)",
+            "extrapolated_solve_s": t_solve,
             "cpu_baseline": {"value": solves_per_s, "unit": "solves/s", "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": solves_per_s, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -252,7 +301,7 @@ def time_solves(ctx, plan, v, x, nrhs, opts, steps, warmup, clocks=False):
     barrier(ctx.world)
     lat = [a.elapsed_time(b) for a, b in ev]
     total = max_over_ranks(sum(lat), ctx.world)
-    return dict(solves_per_s=aggregate_rate(ctx.world, steps, total), ms=total / steps,
+    return dict(solves_per_s=aggregate_rate(ctx.world, steps, total), ms=total / steps, steps=steps,
                 p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
                 iterations=infos[-1]["iterations"], matvecs=infos[-1]["matvecs"],
                 refinements=infos[-1]["refinements"], relres=infos[-1]["relres"],
@@ -365,23 +414,7 @@ def run_shell16(ctx):
     far |= time_far(ctx, plan_cv, c, 1, [ie.IE_PREC_CVFCNN], max(5, args.steps))
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
-    vh = v.cpu().pin_memory()
-    xh = torch.zeros_like(vh).pin_memory()
-    e0, e1 = ctx.ev(), ctx.ev()
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        v.copy_(vh, non_blocking=True)
-        s, info = ie.ie_solve(plan.handle, v, x, 1, paths[HEADLINE]["opts"], stream)
-        if s != ie.IE_OK:
-            raise RuntimeError(f"solve did not converge: {info}")
-        xh.copy_(x, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
-    e2e = {"value": aggregate_rate(world, args.steps, e2e_ms), "unit": "solves/s",
-           "h2d_bytes_per_step": int(vh.numel() * vh.element_size()),
-           "d2h_bytes_per_step": int(xh.numel() * xh.element_size())}
+    e2e = time_e2e(ctx, plan, v, x, paths[HEADLINE]["opts"], args.steps)
 
     # ---- roofline of the dominant kernel of the headline path
     pairs = st["n_far_pairs"]
@@ -435,7 +468,8 @@ def run_shell16(ctx):
     if mapping is not None:
         result["mapping"] = mapping
     if ctx.rank == 0 and world == 1:
-        result["cpu_baseline"] = cpu_baseline(p, oracle_products(p.name, HEADLINE_TOL) or head["matvecs"])
+        result["cpu_baseline"] = cpu_baseline(p, "shell16", oracle_products(p.name, HEADLINE_TOL) or head["matvecs"],
+                                              "the oracle's own GMRES(50) to the same tolerance")
     plan.close()
     plan_cv.close()
     return result
@@ -469,55 +503,121 @@ def map_shell(ctx, p):
                             "note": "whole call: host copies of 124 MB of P and the one-off QR included"}}
 
 
+def shell32_paths(ie) -> dict:
+    """Solve forms of the headline line (all to a relative residual of 1e-5); HEAD32 is
+    the value's step, "plain" the FP32 comparison."""
+    return {
+        "mixed_fp16x3": dict(opts=ie.solve_opts(tol=1e-5, prec=ie.IE_PREC_FP16X3, refine=1,
+                                                refine_prec=ie.IE_PREC_FP16X3, inner_tol=5e-6),
+                             dtype="fp16x3 tensor products (fp16 hi+lo split, f32 accumulate), f32 GMRES, f64 "
+                                   "refinement residual"),
+        "fp16x3_gmres": dict(opts=ie.solve_opts(tol=1e-5, prec=ie.IE_PREC_FP16X3),
+                             dtype="fp16x3 tensor products, f32 GMRES (residual recomputed with fp16x3 products at "
+                                   "each restart)"),
+        "mixed_bf16x3": dict(opts=ie.solve_opts(tol=1e-5, prec=ie.IE_PREC_BF16X3, refine=1,
+                                                refine_prec=ie.IE_PREC_FP16X3, inner_tol=1e-3),
+                             dtype="bf16x3 inner GMRES to 1e-3, f64 refinement on fp16x3 residuals"),
+        "mixed_fp16x1": dict(opts=ie.solve_opts(tol=1e-5, prec=ie.IE_PREC_FP16X1, refine=1,
+                                                refine_prec=ie.IE_PREC_FP16X3, inner_tol=1e-3),
+                             dtype="single fp16 products in the inner GMRES to 1e-3, f64 refinement on fp16x3 "
+                                   "residuals"),
+        "plain": dict(opts=ie.solve_opts(tol=1e-5, prec=ie.IE_PREC_FP32),
+                      dtype="f32 (FP32 SIMT products, f32 GMRES, f64 dots)"),
+    }
+
+
 def run_shell32(ctx):
-    """Precision workload: 32^3 grid, radius-14 shell (5,000 boxes); mixed and plain
-    solves to 1e-5, far products per precision."""
+    """Headline: the 32^3 shell (5,000 boxes) solved to 1e-5 in the mixed form and in
+    plain FP32 on one plan; far products per precision; roofline; oracle sample; a
+    bounded serving record."""
     args, ie, W, torch, np = ctx.args, ctx.ie, ctx.W, ctx.torch, ctx.np
+    world, stream = ctx.world, ctx.stream
     p = W.shell32()
     p.alpha = W.alpha_for("shell32")
-    precs = [ie.IE_PREC_FP32, ie.IE_PREC_BF16X3, ie.IE_PREC_FP16X3, ie.IE_PREC_FP16X1]
+    precs = [ie.IE_PREC_FP32, ie.IE_PREC_BF16X3, ie.IE_PREC_FP16X3, ie.IE_PREC_BF16X1, ie.IE_PREC_FP16X1]
     t0 = time.perf_counter()
-    plan = ie.Plan(ie.problem_from(p, ie.precmask(*precs), symmetry=args.symmetry), ctx.stream)
+    plan = ie.Plan(ie.problem_from(p, ie.precmask(*precs), symmetry=args.symmetry), stream)
     plan_s = time.perf_counter() - t0
     st = plan.stats
     kh, pol = W.plane_wave_spec(1)
     v = torch.zeros((1, p.n), dtype=torch.complex64, device=ctx.dev)
-    ie.ie_rhs_plane_wave(plan.handle, kh, pol, v, ctx.stream)
+    ie.ie_rhs_plane_wave(plan.handle, kh, pol, v, stream)
     x = torch.zeros_like(v)
-    tuned = {ie.PREC_NAMES[q]: ie.ie_plan_tune(plan.handle, q, 1, ctx.stream) for q in precs if q != ie.IE_PREC_FP32}
-    paths = {
-        "fp16x3": ie.solve_opts(tol=1e-5, prec=ie.IE_PREC_FP16X3),
-        "mixed_refine": ie.solve_opts(tol=1e-5, prec=ie.IE_PREC_BF16X3, refine=1, refine_prec=ie.IE_PREC_FP16X3,
-                                      inner_tol=1e-3),
-        "mixed_fp16x1": ie.solve_opts(tol=1e-5, prec=ie.IE_PREC_FP16X1, refine=1, refine_prec=ie.IE_PREC_FP16X3,
-                                      inner_tol=1e-3),
-        "plain": ie.solve_opts(tol=1e-5, prec=ie.IE_PREC_FP32),
-    }
-    warm = max(1, args.warmup)
-    res = {name: time_solves(ctx, plan, v, x, 1, o, args.steps, warm, clocks=(name == "fp16x3"))
-           for name, o in paths.items()}
+    tuned = {ie.PREC_NAMES[q]: ie.ie_plan_tune(plan.handle, q, 1, stream) for q in precs if q != ie.IE_PREC_FP32}
+    paths = shell32_paths(ie)
+    warm = max(3, args.warmup)
+    # ---- timed region: K solves of the headline path (CUDA events on the solve stream)
+    head = time_solves(ctx, plan, v, x, 1, paths[HEAD32]["opts"], args.steps, warm, clocks=True)
+    # the comparison forms: the plain path with the same K, the others with at most 5 steps
+    others = {}
+    for name, path in paths.items():
+        if name == HEAD32:
+            continue
+        k = args.steps if name == "plain" else min(args.steps, 5)
+        others[name] = time_solves(ctx, plan, v, x, 1, path["opts"], k, 1 if name == "plain" else 2)
+    # ---- far-zone products per precision and the translation kernel's own time
     c = torch.from_numpy(W.coefficients(p, 1, W.SEED_C["shell32"]).astype(np.complex64)).to(ctx.dev)
-    far = time_far(ctx, plan, c, 1, precs, max(3, args.steps))
+    far = time_far(ctx, plan, c, 1, precs, max(3, min(args.steps, 10)))
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = time_e2e(ctx, plan, v, x, paths[HEAD32]["opts"], args.steps)
     pairs = st["n_far_pairs"]
-    head = res["fp16x3"]
-    out = {
-        "metric": METRIC, "value": head["solves_per_s"], "unit": "solves/s", "n_gpus": ctx.world,
+    roofline = tc_roofline(pairs, far["fp16x3"]["translate_kernel_ms"], 3, "translate_tc_fp16x3_shell32.md",
+                           "translate_tc_kernel<fp16,x3>")
+    simt_ach = pairs * 8 * 192 * 192 / (far["fp32"]["translate_kernel_ms"] / 1e3) / 1e12
+    roofline_fp32 = {"bound": "alu", "achieved": simt_ach, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": simt_ach / FP32_SIMT_PEAK_TFLOPS, "kernel": "translate_simt_kernel",
+                     "traffic": None, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+    keys = ("solves_per_s", "p50_ms", "p99_ms", "iterations", "matvecs", "refinements", "relres")
+    result = {
+        "metric": METRIC, "value": head["solves_per_s"], "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": warm, "ms_per_step": head["ms"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "fp16x3 tensor products, f32 GMRES",
-        "data": "synthetic",
-        "config": {"workload": ("shell32: 32^3 grid, sphere shell r=14 boxes (5,000 boxes, 160,000 basis unknowns, "
-                                "24,910,952 far pairs in 112,160 displacement groups), nb=32, x-polarised plane "
-                                "wave along +z, tol 1e-5"),
-                   "l2": "no flush needed: each product streams >= 33 GB of coupling blocks"},
-        "vs_plain_fp32": head["solves_per_s"] / res["plain"]["solves_per_s"],
-        "paths": {k: {q: r[q] for q in ("solves_per_s", "p50_ms", "p99_ms", "iterations", "matvecs", "refinements",
-                                         "relres")} for k, r in res.items()},
-        "far_matvecs": far, "tuned": tuned, "plan_seconds": plan_s, "device_bytes": st["device_bytes"],
+        "scaling": "weak", "vs_baseline": None, "dtype": paths[HEAD32]["dtype"], "data": "synthetic",
+        "config": shell32_config(args.symmetry, world),
+        "solve": {k: head[k] for k in keys if k != "solves_per_s"},
+        "vs_plain_fp32": head["solves_per_s"] / others["plain"]["solves_per_s"],
+        "paths": {name: {k: r[k] for k in keys} | {"dtype": paths[name]["dtype"], "steps": r["steps"]}
+                  for name, r in others.items()},
+        "far_matvecs": far,
+        "far_vs_plain_fp32": {q: far[q]["matvecs_per_s"] / far["fp32"]["matvecs_per_s"] for q in far},
+        "tuned": tuned, "plan_seconds": plan_s, "device_bytes": st["device_bytes"],
         "gpu_launches": int(head["launches"]), "clocks": head["clocks"],
-        "roofline": tc_roofline(pairs, far["fp16x3"]["translate_kernel_ms"], 3, None, "translate_tc_kernel<fp16,x3>"),
+        "e2e": e2e, "roofline": roofline, "roofline_fp32": roofline_fp32,
     }
     plan.close()
-    return out
+    del v, x, c
+    torch.cuda.empty_cache()
+    if ctx.rank == 0 and world == 1:
+        prods = oracle_products("shell32", 1e-5)
+        basis = "the oracle's own GMRES(50) on this system to 1e-5"
+        if prods is None:
+            prods, basis = others["plain"]["matvecs"], "the plain FP32 GPU solve's products (no oracle record)"
+        result["cpu_baseline"] = cpu_baseline(p, "shell32", prods, basis)
+    if not args.no_serve:
+        result["serve"] = serve_record(ctx)
+    return result
+
+
+def time_e2e(ctx, plan, v, x, opts, steps):
+    """The headline solve through the C ABI with the right-hand side copied in from
+    pinned host memory and the solution copied back, inside the timed region."""
+    ie, torch = ctx.ie, ctx.torch
+    vh = v.cpu().pin_memory()
+    xh = torch.zeros_like(vh).pin_memory()
+    e0, e1 = ctx.ev(), ctx.ev()
+    torch.cuda.synchronize()
+    e0.record(ctx.stream)
+    for _ in range(steps):
+        v.copy_(vh, non_blocking=True)
+        s, info = ie.ie_solve(plan.handle, v, x, 1, opts, ctx.stream)
+        if s != ie.IE_OK:
+            raise RuntimeError(f"solve did not converge: {info}")
+        xh.copy_(x, non_blocking=True)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), ctx.world)
+    return {"value": aggregate_rate(ctx.world, steps, ms), "unit": "solves/s",
+            "h2d_bytes_per_step": int(vh.numel() * vh.element_size()),
+            "d2h_bytes_per_step": int(xh.numel() * xh.element_size())}
 
 
 def run_batch64(ctx):
@@ -581,55 +681,95 @@ def run_batch64(ctx):
     return out
 
 
-def run_serve(ctx):
-    """Serving workload: Poisson arrivals of scattering solves (200..20,000 boxes log-
-    uniform, 1..4 plane waves), admitted by device footprint; p50/p99 from arrival to
-    completion for the mixed and the plain FP32 forms."""
-    args, ie, W, torch, np = ctx.args, ctx.ie, ctx.W, ctx.torch, ctx.np
-    from paper_2501_04684_gb300 import serve as S
-    reqs = W.serve_requests(count=args.requests, rate_hz=1.0)
+def serve_setup(ctx, count: int):
+    """The seeded serving requests (Poisson arrivals at 1 Hz, seed 51) and their problems."""
+    W = ctx.W
+    reqs = W.serve_requests(count=count, rate_hz=1.0)
     problems = []
     for r in reqs:
         nb = r["nb"]
         problems.append(W.Problem(name=f"req{len(problems)}", G=r["G"], box_ijk=r["box_ijk"], nb=nb,
                                   P=W.random_P(W.rng(r["seed_P"]), nb), alpha=W.batch_alpha(nb)))
-    free, total = torch.cuda.mem_get_info()
-    budget = int(free * 0.9)
-    forms = {
+    return reqs, problems
+
+
+def serve_forms(ie) -> dict:
+    return {
         "mixed": ([ie.IE_PREC_FP16X3], ie.solve_opts(tol=1e-5, prec=ie.IE_PREC_FP16X3)),
         "plain": ([ie.IE_PREC_FP32], ie.solve_opts(tol=1e-5, prec=ie.IE_PREC_FP32)),
     }
 
+
+def serve_run(ctx, reqs, problems, form, rate, batch, budget, symmetry, foot):
+    """One serving run: the seeded arrivals replayed at `rate` (x the 1 Hz process), every
+    request solved to 1e-5 in `form`; latency from submission to completion."""
+    ie, np = ctx.ie, ctx.np
+    from paper_2501_04684_gb300 import serve as S
+    precs, opts = serve_forms(ie)[form]
+    srv = S.Server(precs, opts, budget, workers=ctx.args.serve_workers, batch=batch, symmetry=symmetry)
+    gaps = np.diff([0.0] + [q["t_arrival"] for q in reqs])
+    todo = [S.Request(rid=i, problem=pr, khat=q["khat"], pol=q["pol"]) for i, (q, pr) in
+            enumerate(zip(reqs, problems))]
+    for r in todo:          # footprints are part of the request's description: taken before the clock
+        key = (form, r.rid)
+        if key not in foot:
+            foot[key] = srv.footprint_of(r, 4)
+        r.footprint = foot[key]
+    try:
+        t_begin = time.perf_counter()
+        for i, r in enumerate(todo):
+            time.sleep(max(0.0, gaps[i] / rate))
+            srv.submit(r)
+        done = srv.drain(len(reqs))
+        wall = time.perf_counter() - t_begin
+    finally:
+        srv.close()
+    bad = [r for r in done if r.status != ie.IE_OK]
+    lat = [r.latency for r in done if r.status == ie.IE_OK]
+    pc = S.percentiles(lat)
+    return {"rate_hz": rate, "batch": batch, "completed": len(lat), "failed": len(bad),
+            "errors": sorted({r.error or ie.lib().ie_status_str(r.status).decode() for r in bad})[:3],
+            "solves_per_s": len(lat) / wall, "p50_s": pc["p50"], "p99_s": pc["p99"],
+            "mean_service_s": float(np.mean([r.t_done - r.t_start for r in done])),
+            "peak_device_bytes": srv.peak_used, "wall_s": wall}
+
+
+def serve_record(ctx):
+    """Bounded serving record of the headline line (config 5): the first
+    --record-requests seeded Poisson arrivals, replayed back to back (capacity) in the mixed
+    and the plain form, then at --serve-load[-1] x the plain capacity."""
+    args, torch = ctx.args, ctx.torch
+    reqs, problems = serve_setup(ctx, args.record_requests)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(free * 0.9)
+    foot = {}
+    sym = 1
+    cap = {form: serve_run(ctx, reqs, problems, form, 1e9, 1, budget, sym, foot) for form in ("mixed", "plain")}
+    load = args.serve_load[-1]
+    rate = load * cap["plain"]["solves_per_s"] / max(1e-9, len(reqs) / max(1e-9, reqs[-1]["t_arrival"]))
+    loaded = {form: serve_run(ctx, reqs, problems, form, rate, 1, budget, sym, foot) for form in ("mixed", "plain")}
+    return {"workload": (f"{len(reqs)} Poisson arrivals (seed 51) of sphere-shell scatterers of 200..20,000 boxes "
+                         f"(log-uniform), nb=32, 1..4 plane waves each, tol 1e-5, symmetry-compressed stores"),
+            "capacity_solves_per_s": {f: cap[f]["solves_per_s"] for f in cap},
+            "load_x_plain_capacity": load,
+            "p50_s": {f: loaded[f]["p50_s"] for f in loaded}, "p99_s": {f: loaded[f]["p99_s"] for f in loaded},
+            "solves_per_s": {f: loaded[f]["solves_per_s"] for f in loaded},
+            "runs": {"capacity": cap, "loaded": loaded}}
+
+
+def run_serve(ctx):
+    """Serving workload: Poisson arrivals of scattering solves (200..20,000 boxes log-
+    uniform, 1..4 plane waves), admitted by device footprint; p50/p99 from arrival to
+    completion for the mixed and the plain FP32 forms."""
+    args, ie, torch = ctx.args, ctx.ie, ctx.torch
+    reqs, problems = serve_setup(ctx, args.requests)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(free * 0.9)
+    forms = serve_forms(ie)
     foot = {}
 
     def run(form, rate, batch):
-        precs, opts = forms[form]
-        srv = S.Server(precs, opts, budget, workers=args.serve_workers, batch=batch, symmetry=args.symmetry)
-        gaps = np.diff([0.0] + [q["t_arrival"] for q in reqs])      # seeded arrival process at 1 Hz
-        todo = [S.Request(rid=i, problem=pr, khat=q["khat"], pol=q["pol"]) for i, (q, pr) in
-                enumerate(zip(reqs, problems))]
-        for r in todo:          # footprints are part of the request's description: taken before the clock
-            key = (form, r.rid)
-            if key not in foot:
-                foot[key] = srv.footprint_of(r, 4)
-            r.footprint = foot[key]
-        try:
-            t_begin = time.perf_counter()
-            for i, r in enumerate(todo):
-                time.sleep(max(0.0, gaps[i] / rate))
-                srv.submit(r)
-            done = srv.drain(len(reqs))
-            wall = time.perf_counter() - t_begin
-        finally:
-            srv.close()
-        bad = [r for r in done if r.status != ie.IE_OK]
-        lat = [r.latency for r in done if r.status == ie.IE_OK]
-        pc = S.percentiles(lat)
-        return {"rate_hz": rate, "batch": batch, "completed": len(lat), "failed": len(bad),
-                "errors": sorted({r.error or ie.lib().ie_status_str(r.status).decode() for r in bad})[:3],
-                "solves_per_s": len(lat) / wall, "p50_s": pc["p50"], "p99_s": pc["p99"],
-                "mean_service_s": float(np.mean([r.t_done - r.t_start for r in done])),
-                "peak_device_bytes": srv.peak_used, "wall_s": wall}
+        return serve_run(ctx, reqs, problems, form, rate, batch, budget, args.symmetry, foot)
 
     # capacity: requests back to back (every arrival at once); the offered loads are
     # fractions of the plain form's capacity and both forms see the same arrivals
@@ -749,22 +889,18 @@ def measured_peaks() -> dict:
         return {"bf16": 1900.0, "bf16_sustained": 1700.0, "hbm": 6800.0, "source": "of fallback"}
 
 
-def cpu_baseline(p, iters: int) -> dict:
-    """The FP64 oracle as it stands, on a bounded sample of the same workload."""
+def cpu_baseline(p, name: str, products: int, basis: str, boxes: int | None = None) -> dict:
+    """The FP64 oracle as it stands, on a bounded sample of the same workload: the brute-
+    force product on a seeded subsample of target boxes, timed, then scaled to a solve."""
     import oracle
     import workloads as W
-    c = W.coefficients(p, 1, W.SEED_C["shell16"])
-    targets = W.subsample_boxes(p, 8, W.SEED_SUBSAMPLE["shell16"])
-    oracle.build()
-    t0 = time.perf_counter()
-    oracle.operator(p, c, "full", targets=targets)
-    t = time.perf_counter() - t0
-    t_matvec = t * p.n_boxes / len(targets)
-    v = 1.0 / (max(1, iters) * t_matvec)
+    boxes = boxes or (CPU_SAMPLE_BOXES if name == "shell32" else 8)
+    t, nt, _ = oracle_sample_time(p, boxes, W.SEED_C[name], W.SEED_SUBSAMPLE[name])
+    t_matvec = t * p.n_boxes / nt
+    v = 1.0 / (max(1, products) * t_matvec)
     return {"value": v, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": (f"brute-force FP64 product (near + far) on {len(targets)} of {p.n_boxes} target boxes "
-                       f"({t:.1f} s), scaled to a full product x {iters} products (the oracle's own GMRES(50) "
-                       f"to the same tolerance)")}
+            "sample": (f"brute-force FP64 product (near + far) on {nt} of {p.n_boxes} target boxes ({t:.1f} s), "
+                       f"extrapolated to a full product x {products} products ({basis})")}
 
 
 if __name__ == "__main__":

@@ -284,9 +284,12 @@ typedef struct {
     int matvecs;         /* operator applications (all precisions)                      */
     int refinements;     /* outer refinement steps taken                                */
     int converged;       /* 1 when every right-hand side met tol                        */
-    double relres;       /* max over right-hand sides of the final relative residual:
-                            the recurrence estimate without refinement, the FP64
-                            refinement residual with it                                 */
+    double relres;       /* max over right-hand sides of the final relative residual
+                            ||v - Z c|| / ||v||, recomputed from c (not the Arnoldi
+                            recurrence): without refinement at the end of the last
+                            restart cycle with a `prec` product (FP32 difference, FP64
+                            norms); with refinement the FP64 residual of the last outer
+                            step (`refine_prec` product, FP64 difference and norms)     */
     double seconds;      /* host wall time of the call                                  */
 } ie_solve_info;
 

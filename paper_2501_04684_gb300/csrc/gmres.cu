@@ -470,7 +470,7 @@ __global__ void ref_residual_kernel(const float2 *__restrict__ v, const float2 *
         int64_t e = e0 + threadIdx.x + t * kDotThreads;
         if (e >= e1) continue;
         int64_t i = (int64_t)r * n + e;
-        float2 a = v[i], b = Wv[i];
+        float2 a = v[i], b = Wv ? Wv[i] : make_float2(0.f, 0.f);
         double rx = (double)a.x - (double)b.x, ry = (double)a.y - (double)b.y;
         rout[i] = make_float2((float)rx, (float)ry);
         q += rx * rx + ry * ry;
@@ -994,12 +994,19 @@ ie_status ie_solve(ie_plan p, const void *v, void *c, int nrhs, const ie_solve_o
         int outer = 0, inner_iters = 0, mv = 0;
         double worst = 1;
         ie_status e = IE_OK;
+        bool reuse = false;     // the inner solver's last product is Z c in refine_prec
         while (e == IE_OK) {
-            // r = v - Z x  (FP64 difference of the product)
-            e = apply(p, IE_FULL, o.refine_prec, (const float2 *)c, Wz, nrhs, st);
-            mv++;
-            if (e != IE_OK) break;
-            ref_residual_kernel<<<dim3(s->C, nrhs), kDotThreads, 0, st>>>((const float2 *)v, Wz, rv, sg, nblk, part);
+            // r = v - Z x  (FP64 difference of the product); x = 0 on the first step, so r = v
+            const float2 *Zc = nullptr;
+            if (reuse) {
+                Zc = s->W;
+            } else if (outer > 0) {
+                e = apply(p, IE_FULL, o.refine_prec, (const float2 *)c, Wz, nrhs, st);
+                mv++;
+                if (e != IE_OK) break;
+                Zc = Wz;
+            }
+            ref_residual_kernel<<<dim3(s->C, nrhs), kDotThreads, 0, st>>>((const float2 *)v, Zc, rv, sg, nblk, part);
             count_launches(1);
             if (cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double2), cudaMemcpyDeviceToHost, st) !=
                     cudaSuccess ||
@@ -1024,6 +1031,10 @@ ie_status ie_solve(ie_plan p, const void *v, void *c, int nrhs, const ie_solve_o
             mv += ii.matvecs;
             ref_accumulate_kernel<<<vec_grid(total), 256, 0, st>>>(x64, d, (float2 *)c, total, 0);
             count_launches(1);
+            // After the first inner solve x = 0 + d exactly (c = d), and the inner solver's
+            // restart product W = Z d was taken with the last update of d: when it used the
+            // refinement's precision, the next residual reuses it instead of a new product.
+            reuse = outer == 0 && ii.iterations > 0 && io.prec == o.refine_prec;
             outer++;
         }
         cudaFreeAsync(x64, st);
