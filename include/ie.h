@@ -183,11 +183,11 @@ ie_status ie_plan_stats_get(ie_plan plan, ie_plan_stats *out);
 ie_status ie_plan_profile(ie_plan plan, int enable);
 
 /* Autotuner of the tensor-core translation (no counterpart in the paper): for calls with
- * this nrhs, times the translation of precision `prec` with tile widths of 128, 112, 96
- * and 64 columns and two work-item orders (largest first; displacement order, which runs
+ * this nrhs, times the translation of precision `prec` with tile widths of 96, 80, 64
+ * and 48 columns and two work-item orders (largest first; displacement order, which runs
  * the tiles of one group on neighbouring CTAs together) and keeps the fastest for the
  * plan.  Synchronises `stream`; overwrites the plan's scratch.  info (may be NULL): the
- * chosen tile width and order, its time per launch and that of the default (128, 1).
+ * chosen tile width and order, its time per launch and that of the default (96, 1).
  * Errors: IE_ERR_INVALID, IE_ERR_UNSUPPORTED (FP32 or a precision not in the plan). */
 typedef struct {
     int tile_columns;      /* complex columns per work item chosen                       */

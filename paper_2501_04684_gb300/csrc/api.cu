@@ -372,12 +372,12 @@ size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, i
 }  // namespace
 
 // Work list of one translation kernel for `nrhs`: every displacement group cut into
-// runs of at most (tile columns / nrhs) pairs; the tensor-core list repeats each run
-// for its three M-blocks and, in order 1, keeps displacement order, so that the tiles
-// of one group (which share the group's coupling images) run at the same time on
-// neighbouring CTAs of the persistent kernel's static round-robin; order 0 sorts runs by
-// size (largest first).  The tensor-core tile width and order come from ie_plan_tune
-// (default: the full 128 columns, order 1, the fastest on the shells measured).
+// runs of at most (tile columns / nrhs) pairs (the tensor-core kernel runs the three
+// M-blocks of a run inside one item).  In order 1 the tensor-core list keeps
+// displacement order, so that the tiles of one group (which share the group's coupling
+// images) run at the same time on neighbouring CTAs of the persistent kernel's static
+// round-robin; order 0 sorts runs by size (largest first).  The tensor-core tile width
+// and order come from ie_plan_tune (default: the full tile width, order 1).
 ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out) {
     auto &cache = tc ? p->tc_work : p->simt_work;
     int cols = tc ? tc_tile_columns() : simt_tile_columns(), order = 1;
@@ -402,13 +402,7 @@ ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out) {
         return std::min(nrhs, (int)p->gnrhs[p->box_group[p->h_src[pair]]]);
     };
     std::vector<WorkItem> items;
-    auto emit = [&](int64_t d, int64_t q, int np, int nr) {
-        if (tc) {
-            for (int mb = 0; mb < 3; ++mb) items.push_back({(int32_t)d, (int32_t)q, np, mb, nr});
-        } else {
-            items.push_back({(int32_t)d, (int32_t)q, np, 0, nr});
-        }
-    };
+    auto emit = [&](int64_t d, int64_t q, int np, int nr) { items.push_back({(int32_t)d, (int32_t)q, np, 0, nr}); };
     for (int64_t d = 0; d < p->n_far_disp; ++d) {
         int64_t s = p->h_gstart[d], e = p->h_gstart[d + 1];
         // runs of pairs with the same column count (pairs of one scatterer are contiguous)
@@ -816,7 +810,7 @@ ie_status ie_plan_tune(ie_plan p, int prec, int nrhs, ie_tune_info *info, void *
     cudaEvent_t ev[2] = {nullptr, nullptr};
     IE_CK(cudaEventCreate(&ev[0]));
     IE_CK(cudaEventCreate(&ev[1]));
-    const int cands[] = {128, 112, 96, 64};
+    const int cands[] = {96, 80, 64, 48};
     std::pair<int, int> best{tc_tile_columns(), 1};
     double best_ms = 1e30, default_ms = 0;
     int tried = 0;

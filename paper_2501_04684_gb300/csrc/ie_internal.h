@@ -119,7 +119,7 @@ struct WorkItem {
     int32_t disp;        // index of the displacement (coupling block)
     int32_t pair0;       // first pair (global index into src/dst)
     int32_t npairs;      // pairs in this item (x nrhs columns)
-    int32_t mb;          // tensor-core M-block (0..2); unused by the FP32 path
+    int32_t mb;          // unused (0)
     int32_t nr;          // right-hand-side columns of each pair (the call's nrhs, or fewer for
                          // scatterers with fewer right-hand sides)
 };

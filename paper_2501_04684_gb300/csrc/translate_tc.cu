@@ -7,37 +7,44 @@
 // The product A B^T then holds Gr xr, Gr xi, Gi xr, Gi xi in adjacent TMEM lanes /
 // columns, and the epilogue forms y = (Gr xr - Gi xi) + j (Gr xi + Gi xr) with one lane
 // exchange.  Split precision: every operand is hi + lo in 16 bits (bf16 or fp16), and
-// D = Ahi Bhi + Ahi Blo + Alo Bhi is accumulated in FP32 (BF16X1: Ahi Bhi only).
+// D = Ahi Bhi + Ahi Blo + Alo Bhi is accumulated in FP32 (X1 forms: Ahi Bhi only).
 //
-// Work item = (displacement, M-block of 128 real rows, run of <= 128 complex columns).
-// Persistent CTAs walk the size-sorted item list round-robin.  576 threads, roles:
-//   warps 0-7  producers.  Per item, thread t < columns owns column t: the pair's boxes,
-//              the block and input copy (symmetric store) are fetched one item ahead,
-//              the fp16 scales at that item's third stage, the work item two ahead, so
-//              no dependent global load stalls a stage.  The column's gather base goes
-//              to shared memory for the copies; its target offset and scale go to a
-//              4-deep ring for the epilogue, released through the `staged` mbarrier.
-//              Per K-chunk of 32 (a stage): one thread bulk-copies the two pre-swizzled
-//              8 KB A images (TMA engine, complete_tx on `full`); every (column, hi/lo)
-//              chunk of B is one 128-byte line of the chunk-major input (re and im rows
-//              adjacent), copied by 8 lanes with 16-byte cp.async into the 64-byte-
-//              swizzled K-major layout (chunk c of row n at c ^ ((n / 2) mod 4)); the
-//              copy addresses are computed once per item.  Threads arrive on `landed`
-//              when their copies complete (cp.async.mbarrier.arrive.noinc).
-//   warp 9     signaller (one thread): per stage, waits for `landed`, issues the proxy
-//              fence that makes the gathered rows visible to the tensor core, arrives on
-//              `full`.  48 KB stages, 4-deep ring.
-//   warp 8     MMA issuer (one thread): tcgen05.mma M=128, N<=256, K=16 with
-//              descriptors derived from one base, into one of two TMEM accumulators
-//              (2 x 256 columns); the next work item is prefetched.
-//   warps 10-17 epilogue (two warps per TMEM lane quarter, alternating 16-column chunks,
-//              two chunks per TMEM wait): lanes 2m' and 2m'+1 (Re and Im rows of complex
-//              row m') exchange two values per column pair, then each adds one complex
-//              result (fp16 rescaled) with an 8-byte red.global.add into the slab d mod 8,
-//              at the mapped row with the map's sign for the symmetric store.
-// Every wait is bounded and each role decides on a timeout uniformly (lane-0 wait +
-// shuffle, or a named barrier + abort flag), so no lane is ever left at a barrier; a
-// timeout sets the device error word, drains the CTA's copies, frees TMEM, returns.
+// Work item = (displacement, run of <= 96 complex columns).  The item's gathered inputs
+// B (192 real rows x K = 192, hi and lo) stay in shared memory while the three M-blocks
+// of 128 real rows of A stream past them, so every input line is gathered once per
+// column tile (not once per M-block) and every M-block's product is one TMEM
+// accumulator of N <= 192 columns; two accumulators alternate, so the epilogue of one
+// M-block overlaps the MMAs of the next.  Persistent CTAs walk the items round-robin.
+// 480 threads, roles:
+//   warp 0     A producer (one thread): per (M-block, K-chunk of 32) one bulk copy of
+//              the pre-swizzled hi (and lo) images into a 4-deep ring (TMA engine,
+//              complete_tx on `afull`).
+//   warp 1     MMA issuer (one thread): tcgen05.mma M=128, N<=192, K=16, three products
+//              (hi*hi, hi*lo, lo*hi) per K-step for X3; commits free each A stage, free
+//              each B chunk after the last M-block used it, and hand each accumulator to
+//              the epilogue.
+//   warp 2     signaller (one thread): per B chunk, waits for its gathers (`blanded`),
+//              issues the proxy fence that makes rows written by cp.async visible to the
+//              tensor core, arrives on `bfull`.
+//   warps 3-6  B gatherers.  Per item thread t < columns owns column t: the pair's boxes,
+//              the block and input copy (symmetric store) are loaded one item ahead, the
+//              fp16 scales halfway through the item before, so no dependent global load
+//              stalls a chunk.  The column's gather base goes to shared memory; its target
+//              offset and scale go to a 4-deep ring for the epilogue (`staged`).  Per
+//              K-chunk, once the previous item's last M-block has released it (`bfree`),
+//              every (column, hi/lo) line of the chunk-major input (128 bytes: re and im
+//              rows) is copied by 8 lanes with 16-byte cp.async into the 64-byte-swizzled
+//              K-major layout (chunk c of row n at c ^ ((n / 2) mod 4)), at addresses
+//              computed once per item; the threads arrive on `blanded`.
+//   warps 7-14 epilogue (two warps per TMEM lane quarter, alternating 32-column chunks):
+//              lanes 2m' and 2m'+1 (Re and Im rows of complex row m') exchange two values
+//              per column pair, then each adds one complex result (fp16 rescaled) with an
+//              8-byte red.global.add into the slab d mod 8, at the mapped row with the
+//              map's sign for the symmetric store.
+// Every wait is bounded: a role that gives up raises the CTA's abort flag and the device
+// error word.  The A producer then waits (bounded) for its armed stages' bytes (`afull`
+// depends on nothing else), the gatherers for their cp.async, the MMA thread for its
+// issued MMAs; every role reaches the final barrier, which frees TMEM.
 #include <algorithm>
 
 #include "ie_internal.h"
@@ -45,25 +52,30 @@
 namespace ie {
 namespace {
 
-constexpr int kTcTileCols = 128;                 // complex columns per work item (N <= 256)
-constexpr int kStages = 4;
-constexpr int kAcc = 2;                          // TMEM accumulators of 256 columns
-constexpr int kProducers = 256;
-constexpr int kProdWarps = kProducers / 32;
-constexpr int kMmaWarp = kProdWarps, kSigWarp = kProdWarps + 1;
-constexpr int kLines = 2 * kTcTileCols / (kProducers / 8);      // B lines per producer thread and stage (<=)
-constexpr int kEpilogue = 256;
-constexpr int kThreadsTc = kProducers + 32 + 32 + kEpilogue;  // producers, MMA, signaller, epilogue
-constexpr int kEpiFirst = kProducers + 64;                    // first epilogue thread
+constexpr int kTcTileCols = 96;                  // complex columns per work item (N <= 192)
+constexpr int kN = 2 * kTcTileCols;              // real B rows of a full item
+constexpr int kAStages = 4;
+constexpr int kAcc = 2;                          // TMEM accumulators (256-column slots)
+constexpr int kGathWarps = 4;
+constexpr int kGath = 32 * kGathWarps;
+constexpr int kEpiWarps = 8;
+constexpr int kWarpGath0 = 3, kWarpEpi0 = kWarpGath0 + kGathWarps;
+constexpr int kThreadsTc = 32 * (kWarpEpi0 + kEpiWarps);        // 480
+constexpr int kLines = (2 * kTcTileCols) / (kGath / 8);         // B lines per gatherer thread and chunk (<=)
 constexpr int kImgBytes = 128 * kTcK * 2;        // 8 KB A image
-constexpr int kBBytes = 256 * kTcK * 2;          // 16 KB B plane (256 rows x 64 B)
-constexpr int kStageBytes = 2 * kImgBytes + 2 * kBBytes;     // 48 KB
-constexpr int kRing = 4;                         // epilogue metadata buffers (producers stay < 3 items ahead)
-constexpr int kEpiBytes = kRing * kTcTileCols * (8 + 4) + kRing * 16;   // column offsets + scales + item header
-constexpr int kColBytes = 2 * kTcTileCols * 8;                 // gather base pointer of each column, 2 items
-constexpr int kSmemBytes = kStages * kStageBytes + kEpiBytes + kColBytes + 512 /*barriers*/ + 1024 /*alignment*/;
+constexpr int kAStageBytes = 2 * kImgBytes;      // hi + lo
+constexpr int kBPlane = kN * kTcK * 2;           // 12 KB: one chunk, one of hi / lo (192 rows x 64 B)
+constexpr int kBChunkBytes = 2 * kBPlane;
+constexpr int kBBytes = kTcKChunks * kBChunkBytes;              // 144 KB
+constexpr int kRing = 4;                         // epilogue metadata buffers
+constexpr int kEpiBytes = kRing * kTcTileCols * 8 + kRing * 16; // column offset + scale, item header
+constexpr int kColBytes = 2 * kTcTileCols * 8;                  // gather base of each column, 2 items
+constexpr int kSmemBytes = kAStages * kAStageBytes + kBBytes + kEpiBytes + kColBytes + 512 /*barriers*/ +
+                           1024 /*alignment*/;
 constexpr uint32_t kTmemCols = 512;
 constexpr long long kWaitCycles = 1ll << 31;     // bounded waits give up after ~1 s of SM clock
+static_assert(kAStages * kAStageBytes % 1024 == 0 && kBChunkBytes % 1024 == 0, "operand tiles 1 KB aligned");
+static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -108,8 +120,7 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatil
     if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag) ? 1 : 0;
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
-__device__ __forceinline__ void named_sync_epilogue() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
-__device__ __forceinline__ void named_sync_producers() { asm volatile("bar.sync 2, %0;" ::"n"(kProducers) : "memory"); }
+__device__ __forceinline__ void named_sync_gatherers() { asm volatile("bar.sync 1, %0;" ::"n"(kGath) : "memory"); }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
@@ -159,24 +170,49 @@ __device__ __forceinline__ void umma(uint32_t dtmem, uint64_t adesc, uint64_t bd
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
         : "memory");
 }
+// The same with A kept in the collector buffer for the next MMA (fill), or read from it
+// for the last time (lastuse).
+__device__ __forceinline__ void umma_fill(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_last(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
 __device__ __forceinline__ void umma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t r[16]) {
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t r[32]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+__device__ __forceinline__ void red_add_v2(float *addr, float a, float b) {
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(addr), "f"(a), "f"(b) : "memory");
+}
+
 struct TcArgs {
     const WorkItem *items;
     int64_t n_items;
-    const uint16_t *C;          // [disp][36 images]
-    const int32_t *Cexp;        // [disp] or null
+    const uint16_t *C;          // [block][36 images]
+    const int32_t *Cexp;        // [block] or null
     const int32_t *Xexp;        // [col]
     const uint16_t *Xtc;        // [hl][col][chunk][reim][32]
     int64_t plane;              // elements per hl plane of Xtc
@@ -199,35 +235,45 @@ translate_tc_kernel(const TcArgs a) {
     if (a.gate && *a.gate == 0) return;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    int64_t *ep_off = reinterpret_cast<int64_t *>(smem + kStages * kStageBytes);      // [kRing][128]
-    float *ep_scale = reinterpret_cast<float *>(ep_off + kRing * kTcTileCols);          // [kRing][128]
-    int4 *ep_head = reinterpret_cast<int4 *>(ep_scale + kRing * kTcTileCols);           // [kRing] ncols, disp, mb
-    const uint16_t **colptr = reinterpret_cast<const uint16_t **>(ep_head + kRing);    // [2][128]
-    uint64_t *full = reinterpret_cast<uint64_t *>(colptr + 2 * kTcTileCols);            // [kStages]
-    uint64_t *empty = full + kStages;                                                    // [kStages]
-    uint64_t *landed = empty + kStages;                                                  // [kStages]
-    uint64_t *accfull = landed + kStages;                                                // [kAcc]
+    unsigned char *sAbase = smem;                                                        // [kAStages][16 KB]
+    unsigned char *sBbase = smem + kAStages * kAStageBytes;                              // [6][hi, lo][12 KB]
+    int32_t *ep_off = reinterpret_cast<int32_t *>(sBbase + kBBytes);                    // [kRing][96]
+    float *ep_scale = reinterpret_cast<float *>(ep_off + kRing * kTcTileCols);          // [kRing][96]
+    int4 *ep_head = reinterpret_cast<int4 *>(ep_scale + kRing * kTcTileCols);           // [kRing] ncols, disp, sig
+    const uint16_t **colptr = reinterpret_cast<const uint16_t **>(ep_head + kRing);    // [2][96]
+    uint64_t *afull = reinterpret_cast<uint64_t *>(colptr + 2 * kTcTileCols);           // [kAStages]
+    uint64_t *aempty = afull + kAStages;                                                 // [kAStages]
+    uint64_t *blanded = aempty + kAStages;                                               // [6]
+    uint64_t *bfull = blanded + kTcKChunks;                                              // [6]
+    uint64_t *bfree = bfull + kTcKChunks;                                                // [6]
+    uint64_t *accfull = bfree + kTcKChunks;                                              // [kAcc]
     uint64_t *accempty = accfull + kAcc;                                                 // [kAcc]
     uint64_t *staged = accempty + kAcc;                                                  // [kRing]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(staged + kRing);
+    uint64_t *mdone = staged + kRing;                                                    // [1]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(mdone + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(smem_u32(&full[s]), 2);               // signaller + the A copies' expect_tx arrive
-            mbar_init(smem_u32(&empty[s]), 1);
-            mbar_init(smem_u32(&landed[s]), kProducers);
+        for (int s = 0; s < kAStages; ++s) {
+            mbar_init(smem_u32(&afull[s]), 1);              // the A producer's expect_tx arrive
+            mbar_init(smem_u32(&aempty[s]), 1);
+        }
+        for (int k = 0; k < kTcKChunks; ++k) {
+            mbar_init(smem_u32(&blanded[k]), kGath);
+            mbar_init(smem_u32(&bfull[k]), 1);
+            mbar_init(smem_u32(&bfree[k]), 1);
         }
         for (int b = 0; b < kAcc; ++b) {
             mbar_init(smem_u32(&accfull[b]), 1);
-            mbar_init(smem_u32(&accempty[b]), kEpilogue);
+            mbar_init(smem_u32(&accempty[b]), kEpiWarps);
         }
-        for (int b = 0; b < kRing; ++b) mbar_init(smem_u32(&staged[b]), kProducers);
+        for (int b = 0; b < kRing; ++b) mbar_init(smem_u32(&staged[b]), kGath);
+        mbar_init(smem_u32(&mdone[0]), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == kMmaWarp) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -238,28 +284,155 @@ translate_tc_kernel(const TcArgs a) {
     const uint32_t tmem_base = *tmem_slot;
 
     const int64_t first = blockIdx.x, step = gridDim.x;
-    if (warp < kProdWarps) {
-        // ---------------- producers (warps 0-7)
-        const int tid = threadIdx.x;
-        int64_t armed[kStages];
-        for (int s = 0; s < kStages; ++s) armed[s] = -1;
+    if (warp == 0) {
+        // ---------------- A producer (lane 0)
+        if (lane == 0) {
+            bool ok = true;
+            int64_t g = 0;                  // A stages issued
+            int64_t i = first;
+            int blk = 0;
+            if (i < a.n_items) {
+                const int d0 = a.items[i].disp;
+                blk = a.gcanon ? __ldg(a.gcanon + d0) : d0;
+            }
+            for (; i < a.n_items && ok; i += step) {
+                // the next item's block, in flight during this item
+                int blk_n = 0;
+                if (i + step < a.n_items) {
+                    const int dn = a.items[i + step].disp;
+                    blk_n = a.gcanon ? __ldg(a.gcanon + dn) : dn;
+                }
+                const uint16_t *Cd = a.C + (int64_t)blk * kTcDispElems;
+                for (int q = 0; q < 3 * kTcKChunks; ++q, ++g) {      // q = mb * 6 + kc
+                    const int s = (int)(g % kAStages);
+                    const uint32_t ph = (uint32_t)((g / kAStages) & 1);
+                    if (!mbar_wait(smem_u32(&aempty[s]), ph ^ 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fb = smem_u32(&afull[s]);
+                    mbar_arrive_expect_tx(fb, X3 ? 2 * kImgBytes : kImgBytes);
+                    // images of (mb, kc) are (mb * 6 + kc) * 2 + hl: hi and lo adjacent
+                    bulk_g2s(smem_u32(sAbase + s * kAStageBytes), Cd + (int64_t)(2 * q) * kTcImageElems,
+                             X3 ? 2 * kImgBytes : kImgBytes, fb);
+                }
+                blk = blk_n;
+            }
+            if (!ok) {
+                atomicExch(a.err, 1);
+                // drain: the last stages armed complete once their bytes land (no other role involved)
+                for (int64_t gg = g > kAStages ? g - kAStages : 0; gg < g; ++gg) {
+                    const uint32_t ph = (uint32_t)((gg / kAStages) & 1);
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(smem_u32(&afull[gg % kAStages]), ph) && clock64() - t0 < kWaitCycles) {
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---------------- MMA issuer (lane 0)
+        if (lane == 0) {
+            const uint64_t da = sw64_desc(smem_u32(sAbase));      // A stage s: + s * kAStageBytes / 16
+            const uint64_t db = sw64_desc(smem_u32(sBbase));      // B chunk kc: + kc * kBChunkBytes / 16
+            int64_t il = 0, g = 0;
+            bool ok = true, issued = false;
+            WorkItem nxt = first < a.n_items ? a.items[first] : WorkItem{0, 0, 0, 0, 1};
+            for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
+                const WorkItem it = nxt;
+                if (i + step < a.n_items) nxt = a.items[i + step];   // in flight during this item
+                const int ncols = it.npairs * it.nr;
+                const int nmma = (2 * ncols + 15) & ~15;
+                const uint32_t idesc = f16_idesc(nmma, FP16);
+                const uint32_t bph = (uint32_t)(il & 1);
+                for (int mb = 0; mb < 3 && ok; ++mb) {
+                    const int64_t qa = il * 3 + mb;          // accumulator use
+                    const int buf = (int)(qa % kAcc);
+                    if (!mbar_wait<false>(smem_u32(&accempty[buf]), (uint32_t)(((qa / kAcc) & 1) ^ 1), abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t dt = tmem_base + (uint32_t)(buf * 256);
+                    for (int kc = 0; kc < kTcKChunks; ++kc, ++g) {
+                        const int s = (int)(g % kAStages);
+                        if (!mbar_wait<false>(smem_u32(&afull[s]), (uint32_t)((g / kAStages) & 1), abort_flag) ||
+                            (mb == 0 && !mbar_wait<false>(smem_u32(&bfull[kc]), bph, abort_flag))) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        // descriptors of this K-chunk; +2 advances the start address by 32 B (K = 16)
+                        const uint64_t ah = da + (uint64_t)(s * (kAStageBytes >> 4));
+                        const uint64_t al = ah + (uint64_t)(kImgBytes >> 4);
+                        const uint64_t bh = db + (uint64_t)(kc * (kBChunkBytes >> 4));
+                        const uint64_t bl = bh + (uint64_t)(kBPlane >> 4);
+                        // X3: hi*hi then hi*lo keep A (hi) in the collector buffer, so it is
+                        // read from shared memory once for the two products
+                        if (X3) {
+                            umma_fill(dt, ah, bh, idesc, kc ? 1u : 0u);
+                            umma_last(dt, ah, bl, idesc, 1u);
+                            umma(dt, al, bh, idesc, 1u);
+                            umma_fill(dt, ah + 2, bh + 2, idesc, 1u);
+                            umma_last(dt, ah + 2, bl + 2, idesc, 1u);
+                            umma(dt, al + 2, bh + 2, idesc, 1u);
+                        } else {
+                            umma(dt, ah, bh, idesc, kc ? 1u : 0u);
+                            umma(dt, ah + 2, bh + 2, idesc, 1u);
+                        }
+                        issued = true;
+                        umma_commit(smem_u32(&aempty[s]));
+                        if (mb == 2) umma_commit(smem_u32(&bfree[kc]));
+                        if (kc == kTcKChunks - 1) umma_commit(smem_u32(&accfull[buf]));
+                    }
+                }
+            }
+            if (!ok) {
+                atomicExch(a.err, 1);
+                // the MMAs already issued still read shared memory and TMEM: wait for them
+                if (issued) {
+                    umma_commit(smem_u32(&mdone[0]));
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(smem_u32(&mdone[0]), 0) && clock64() - t0 < kWaitCycles) {
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 2) {
+        // ---------------- signaller (lane 0)
+        if (lane == 0) {
+            int64_t il = 0;
+            bool ok = true;
+            for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
+                for (int kc = 0; kc < kTcKChunks; ++kc) {
+                    if (!mbar_wait<false>(smem_u32(&blanded[kc]), (uint32_t)(il & 1), abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_proxy_async();     // gathered rows (generic proxy) -> tensor core (async proxy)
+                    mbar_arrive(smem_u32(&bfull[kc]));
+                }
+            }
+            if (!ok) atomicExch(a.err, 1);
+        }
+        __syncwarp();
+    } else if (warp < kWarpEpi0) {
+        // ---------------- B gatherers (warps 3-6)
+        const int tid = threadIdx.x - 32 * kWarpGath0;       // 0 .. kGath-1
         bool ok = true;
         // Per item, thread t owns column t: its gather base (input copy, rhs, source box)
-        // and the epilogue's target offset and fp16 scale.  No dependent global load may
-        // stall a stage, so the metadata of an item is fetched in steps over the items
-        // before it: the work item two items ahead; its pair's boxes and the block and
-        // input copy at the start of the item before; the fp16 scales at that item's
-        // third stage; the result is published at its end.
+        // and the epilogue's target offset and fp16 scale.  The metadata of an item is
+        // fetched over the item before it (boxes and copy at its start, fp16 scales at
+        // its third chunk), so no dependent global load stalls a chunk.
         struct Meta {
-            int src, dst, rr, blk, sig, ed, xe, ncols, disp, mb;
+            int src, dst, rr, sig, ed, xe, ncols, disp;
         };
         auto meta_issue = [&](const WorkItem &w, bool valid) {
-            Meta m{0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+            Meta m{0, 0, 0, 0, 0, 0, 0, 0};
             if (!valid) return m;
             m.ncols = w.npairs * w.nr;
             m.disp = w.disp;
-            m.mb = w.mb;
-            m.blk = a.gcanon ? __ldg(a.gcanon + w.disp) : w.disp;
             m.sig = a.gcanon ? __ldg(a.gsigma + w.disp) : 0;
             if (tid >= m.ncols) return m;
             int p;
@@ -275,51 +448,47 @@ translate_tc_kernel(const TcArgs a) {
         };
         auto meta_scales = [&](Meta &m) {
             if (FP16 && tid < m.ncols) {
-                m.ed = __ldg(a.Cexp + m.blk);
+                const int blk = a.gcanon ? __ldg(a.gcanon + m.disp) : m.disp;
+                m.ed = __ldg(a.Cexp + blk);
                 m.xe = __ldg(a.Xexp + (int64_t)m.rr * a.nbox + m.src);
             }
         };
-        // publish item il's column data: gather bases (producers) and the epilogue ring
+        // publish item il's column data: gather bases and the epilogue ring
         auto publish = [&](const Meta &m, int64_t il) {
             const bool on = tid < m.ncols;
             const int rb = (int)(il % kRing);
             if (tid < kTcTileCols) {
                 colptr[(il & 1) * kTcTileCols + tid] =
                     on ? a.Xtc + (int64_t)m.sig * a.sig_stride + ((int64_t)m.rr * a.nbox + m.src) * (2 * kNU) : nullptr;
-                ep_off[rb * kTcTileCols + tid] = on ? ((int64_t)m.rr * a.nbox + m.dst) * (2 * kNU) : 0;
+                ep_off[rb * kTcTileCols + tid] = on ? (m.rr * a.nbox + m.dst) * kNU : 0;
                 ep_scale[rb * kTcTileCols + tid] = (FP16 && on) ? ldexpf(1.f, m.ed + m.xe) : 1.f;
             }
-            if (tid == 0) ep_head[rb] = make_int4(m.ncols, m.disp, m.mb, m.sig);
+            if (tid == 0) ep_head[rb] = make_int4(m.ncols, m.disp, m.sig, 0);
             mbar_arrive(smem_u32(&staged[rb]));      // release: the epilogue reads after its wait
         };
-        WorkItem w_cur = a.items[first];
         WorkItem w_nxt = first + step < a.n_items ? a.items[first + step] : WorkItem{0, 0, 0, 0, 1};
-        Meta m_cur = meta_issue(w_cur, true);
+        Meta m_cur = meta_issue(a.items[first], true);
         meta_scales(m_cur);
         publish(m_cur, 0);
-        named_sync_producers();
-        // line layout of a stage: each (column, hi/lo) K-chunk is 128 contiguous bytes
+        named_sync_gatherers();
+        // line layout of a chunk: each (column, hi/lo) K-chunk is 128 contiguous bytes
         // (re 32 + im 32 values), fetched by 8 lanes: lanes 0-3 the re row, 4-7 the im row
         const int sub = tid & 7, lg = tid >> 3, part = sub >> 2, c = sub & 3;
-        int64_t g = 0;                 // stages issued by this CTA
         int64_t il = 0;
         for (int64_t i = first; i < a.n_items; i += step, ++il) {
-            const WorkItem it = w_cur;
-            const int blk = m_cur.blk;
             const bool has_next = i + step < a.n_items;
             const WorkItem w_nn = i + 2 * step < a.n_items ? a.items[i + 2 * step] : WorkItem{0, 0, 0, 0, 1};
             Meta m_nxt = meta_issue(w_nxt, has_next);
-            const int ncols = it.npairs * it.nr;
+            const int ncols = m_cur.ncols;
             const int nl = X3 ? 2 * ncols : ncols;
             const uint16_t *const *cols = colptr + (il & 1) * kTcTileCols;
-            const uint16_t *Cd = a.C + (int64_t)blk * kTcDispElems;
-            // this thread's lines of the item (<= kLines): offset inside a stage and source
-            // of K-chunk 0, computed once per item; a stage then costs one add per copy
+            // this thread's lines of the item (<= kLines): offset inside a chunk and source
+            // of K-chunk 0, computed once per item; a chunk then costs one add per copy
             uint32_t loff[kLines];
             const uint16_t *lsrc[kLines];
 #pragma unroll
             for (int k = 0; k < kLines; ++k) {
-                const int L = lg + (kProducers / 8) * k;
+                const int L = lg + (kGath / 8) * k;
                 lsrc[k] = nullptr;
                 loff[k] = 0;
                 if (L < nl) {
@@ -327,207 +496,105 @@ translate_tc_kernel(const TcArgs a) {
                     const int hl = X3 ? (L & 1) : 0;
                     const int n = 2 * j + part;
                     loff[k] = (uint32_t)((n >> 3) * 512 + (n & 7) * 64 + ((c ^ ((n >> 1) & 3)) << 4)) +
-                              (hl ? (uint32_t)kBBytes : 0u);
+                              (hl ? (uint32_t)kBPlane : 0u);
                     lsrc[k] = cols[j] + (hl ? a.plane : 0) + part * kTcK + c * 8;
                 }
             }
-            for (int kc = 0; kc < kTcKChunks && ok; ++kc, ++g) {
-                const int s = (int)(g % kStages);
-                const uint32_t ph = (uint32_t)((g / kStages) & 1);
+            for (int kc = 0; kc < kTcKChunks && ok; ++kc) {
                 if (kc == 2) meta_scales(m_nxt);
-                if (!warp_wait(smem_u32(&empty[s]), ph ^ 1, abort_flag)) {
+                // the previous item's last M-block has finished with this chunk
+                if (!warp_wait(smem_u32(&bfree[kc]), (uint32_t)((il & 1) ^ 1), abort_flag)) {
                     ok = false;
                     break;
                 }
-                unsigned char *st = smem + s * kStageBytes;
-                const uint32_t sA = smem_u32(st), sB = smem_u32(st + 2 * kImgBytes);
-                const uint32_t fb = smem_u32(&full[s]);
-                if (tid == 0) {
-                    mbar_arrive_expect_tx(fb, X3 ? 2 * kImgBytes : kImgBytes);
-                    armed[s] = g;
-                    const uint16_t *img = Cd + (int64_t)((it.mb * kTcKChunks + kc) * 2) * kTcImageElems;
-                    bulk_g2s(sA, img, kImgBytes, fb);
-                    if (X3) bulk_g2s(sA + kImgBytes, img + kTcImageElems, kImgBytes, fb);
-                }
+                const uint32_t sB = smem_u32(sBbase + kc * kBChunkBytes);
 #pragma unroll
                 for (int k = 0; k < kLines; ++k)
                     if (lsrc[k]) cp_async16(sB + loff[k], lsrc[k] + kc * (2 * kTcK));
-                cp_async_arrive_noinc(smem_u32(&landed[s]));
+                cp_async_arrive_noinc(smem_u32(&blanded[kc]));
             }
-            // every producer warp reaches this once per item, also after a timeout
+            // every gatherer warp reaches this once per item, also after a timeout
             if (ok && has_next) publish(m_nxt, il + 1);
-            named_sync_producers();
+            named_sync_gatherers();
             if (*abort_flag) ok = false;
             if (!ok) break;
-            w_cur = w_nxt;
             w_nxt = w_nn;
             m_cur = m_nxt;
         }
         cp_async_wait_all();
-        if (!ok) {
-            if (tid == 0) {
-                atomicExch(a.err, 1);
-                // drain: every stage this CTA armed completes once its bulk bytes land
-                for (int s = 0; s < kStages; ++s) {
-                    if (armed[s] < 0) continue;
-                    const uint32_t ph = (uint32_t)((armed[s] / kStages) & 1);
-                    const long long t0 = clock64();
-                    while (!mbar_try_wait(smem_u32(&full[s]), ph) && clock64() - t0 < kWaitCycles) __nanosleep(64);
-                }
-            }
-        }
-    } else if (warp == kMmaWarp) {
-        // ---------------- MMA issuer (lane 0)
-        if (lane == 0) {
-            const uint64_t d0 = sw64_desc(smem_u32(smem));   // stage s: + s * kStageBytes / 16
-            int64_t il = 0;
-            bool ok = true;
-            WorkItem nxt = first < a.n_items ? a.items[first] : WorkItem{0, 0, 0, 0, 1};
-            for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
-                const WorkItem it = nxt;
-                if (i + step < a.n_items) nxt = a.items[i + step];   // in flight during this item
-                const int ncols = it.npairs * it.nr;
-                const int nmma = (2 * ncols + 15) & ~15;
-                const uint32_t idesc = f16_idesc(nmma, FP16);
-                const int buf = (int)(il % kAcc);
-                const uint32_t aph = (uint32_t)((il / kAcc) & 1);
-                if (!mbar_wait<false>(smem_u32(&accempty[buf]), aph ^ 1, abort_flag)) {
+        if (!ok && tid == 0) atomicExch(a.err, 1);
+    } else {
+        // ---------------- epilogue warps 7-14 (TMEM lane quarter = warp mod 4)
+        const int q = warp & 3;
+        const int half = (warp - kWarpEpi0) >> 2;          // which alternate 32-column chunks
+        const int64_t slab_f = (int64_t)a.slab_stride * 2;
+        const bool odd = lane & 1;
+        int64_t il = 0;
+        bool ok = true;
+        for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
+            const int rb = (int)(il % kRing);
+            if (!warp_wait(smem_u32(&staged[rb]), (uint32_t)((il / kRing) & 1), abort_flag)) break;
+            const int4 hd = ep_head[rb];
+            const int ncols = hd.x, disp = hd.y, sig = hd.z;
+            const int32_t *offs = ep_off + rb * kTcTileCols;
+            const float *scl = ep_scale + rb * kTcTileCols;
+            float *Yslab = a.Yslab + (int64_t)(disp % kSlabs) * slab_f;
+            for (int mb = 0; mb < 3; ++mb) {
+                const int64_t qa = il * 3 + mb;
+                const int buf = (int)(qa % kAcc);
+                if (!warp_wait(smem_u32(&accfull[buf]), (uint32_t)((qa / kAcc) & 1), abort_flag)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t dt = tmem_base + (uint32_t)(buf * 256);
-                for (int kc = 0; kc < kTcKChunks; ++kc) {
-                    const int64_t g = il * kTcKChunks + kc;
-                    const int s = (int)(g % kStages);
-                    const uint32_t ph = (uint32_t)((g / kStages) & 1);
-                    if (!mbar_wait<false>(smem_u32(&full[s]), ph, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    // descriptors of this stage; +2 advances the start address by 32 B (K = 16)
-                    const uint64_t ah = d0 + (uint64_t)(s * (kStageBytes >> 4));
-                    const uint64_t bh = ah + (uint64_t)((2 * kImgBytes) >> 4);
-                    const uint64_t al = ah + (uint64_t)(kImgBytes >> 4), bl = bh + (uint64_t)(kBBytes >> 4);
-                    umma(dt, ah, bh, idesc, kc ? 1u : 0u);
-                    if (X3) {
-                        umma(dt, ah, bl, idesc, 1u);
-                        umma(dt, al, bh, idesc, 1u);
-                    }
-                    umma(dt, ah + 2, bh + 2, idesc, 1u);
-                    if (X3) {
-                        umma(dt, ah + 2, bl + 2, idesc, 1u);
-                        umma(dt, al + 2, bh + 2, idesc, 1u);
-                    }
-                    umma_commit(smem_u32(&empty[s]));
-                    if (kc == kTcKChunks - 1) umma_commit(smem_u32(&accfull[buf]));
+                const int m0 = 64 * mb + 16 * q;       // first complex row of this warp
+                // float offset of this lane's complex row (the mapped row for the symmetric store)
+                int row_f = 2 * (m0 + (lane >> 1));
+                float sgn = 1.f;
+                if (a.gcanon) {
+                    const uint16_t e = __ldg(a.symmap + sig * kNU + m0 + (lane >> 1));
+                    row_f = 2 * (e & 0xFF);
+                    sgn = (e & 0x100) ? -1.f : 1.f;
                 }
-            }
-            if (!ok) atomicExch(a.err, 1);
-        }
-    } else if (warp == kSigWarp) {
-        // ---------------- signaller (lane 0)
-        if (lane == 0) {
-            int64_t g = 0;
-            for (int64_t i = first; i < a.n_items; i += step) {
-                bool ok = true;
-                for (int kc = 0; kc < kTcKChunks; ++kc, ++g) {
-                    const int s = (int)(g % kStages);
-                    const uint32_t ph = (uint32_t)((g / kStages) & 1);
-                    if (!mbar_wait<false>(smem_u32(&landed[s]), ph, abort_flag)) {
-                        ok = false;
-                        break;
-                    }
-                    fence_proxy_async();     // gathered rows (generic proxy) -> tensor core (async proxy)
-                    mbar_arrive(smem_u32(&full[s]));
-                }
-                if (!ok) {
-                    atomicExch(a.err, 1);
-                    break;
-                }
-            }
-        }
-    } else {
-        // ---------------- epilogue warps 6-13 (TMEM lane quarter = warp mod 4)
-        const int q = warp & 3;
-        const int half = (warp - kEpiFirst / 32) >> 2;     // which alternate 8-column chunks
-        const int64_t slab_f = (int64_t)a.slab_stride * 2;
-        int64_t il = 0;
-        for (int64_t i = first; i < a.n_items; i += step, ++il) {
-            const int buf = (int)(il % kAcc);
-            const uint32_t aph = (uint32_t)((il / kAcc) & 1);
-            const int rb = (int)(il % kRing);
-            bool ok = true;
-            if (lane == 0) {
-                ok = mbar_wait(smem_u32(&staged[rb]), (uint32_t)((il / kRing) & 1), abort_flag) &&
-                     mbar_wait(smem_u32(&accfull[buf]), aph, abort_flag);
-            }
-            named_sync_epilogue();               // makes the abort decision uniform
-            if (*abort_flag) break;
-            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-            if (!ok) break;
-            tc_fence_after();
-            const int4 hd = ep_head[rb];
-            const int ncols = hd.x, disp = hd.y, mb = hd.z, sig = hd.w;
-            const int64_t *offs = ep_off + rb * kTcTileCols;
-            const float *scl = ep_scale + rb * kTcTileCols;
-            const int m0 = 64 * mb + 16 * q;       // first complex row of this warp
-            float *Ys = a.Yslab + (int64_t)(disp % kSlabs) * slab_f + 2 * m0 + lane;
-            float sgn = 1.f;
-            if (a.gcanon) {                        // output row of this lane in the frame of d
-                const uint16_t e = __ldg(a.symmap + sig * kNU + m0 + (lane >> 1));
-                Ys = a.Yslab + (int64_t)(disp % kSlabs) * slab_f + 2 * (e & 0xFF) + (lane & 1);
-                sgn = (e & 0x100) ? -1.f : 1.f;
-            }
-            const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256);
-            // two 16-column chunks per TMEM wait (this warp's chunks are 32 columns apart).
-            // Lanes 2m', 2m'+1 hold Re G and Im G rows of complex row m'; per pair of
-            // columns (k, k+1) they exchange two values, then the even lane owns the
-            // complex result of column k and the odd lane that of column k+1, added with
-            // one 8-byte reduction each.
-            const bool odd = lane & 1;
-            float *Yrow = Ys - (lane & 1);               // float offset of complex row m' (or U(m'))
-            for (int c0 = 16 * half; c0 < 2 * ncols; c0 += 64) {
-                uint32_t r[32];
-                const bool two = c0 + 32 < 2 * ncols;   // warp-uniform
-                tmem_ld16_nowait(tbase + (uint32_t)c0, r);
-                if (two) {
-                    tmem_ld16_nowait(tbase + (uint32_t)(c0 + 32), r + 16);
-                } else {
+                float *Yrow = Yslab + row_f;
+                const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256);
+                // 32 TMEM columns = 16 complex columns per load.  Lanes 2m', 2m'+1 hold the Re G
+                // and Im G rows of complex row m'; per pair of columns (k, k+1) they exchange
+                // two values, then the even lane owns the complex result of column k and the
+                // odd lane that of column k+1.
+                for (int c0 = 32 * half; c0 < 2 * ncols; c0 += 64) {
+                    uint32_t r[32];
+                    tmem_ld32(tbase + (uint32_t)c0, r);
+                    tmem_wait_ld();
+                    const int jb = c0 >> 1;
 #pragma unroll
-                    for (int k = 16; k < 32; ++k) r[k] = 0u;
-                }
-                tmem_wait_ld();
-                const int jb = c0 >> 1;
-#pragma unroll
-                for (int pk = 0; pk < 8; ++pk) {
-                    const int k = 2 * pk;                // columns k, k+1 of the 16 (k even)
-                    const float a0 = __uint_as_float(r[2 * k]), a1 = __uint_as_float(r[2 * k + 1]);
-                    const float b0 = __uint_as_float(r[2 * k + 2]), b1 = __uint_as_float(r[2 * k + 3]);
-                    // even lane (Re G row) sends column k+1's values, odd lane (Im G row) column k's
-                    const float g0 = __shfl_xor_sync(0xffffffffu, odd ? a0 : b0, 1);
-                    const float g1 = __shfl_xor_sync(0xffffffffu, odd ? a1 : b1, 1);
-                    // even: y_k = (Gr xr - Gi xi, Gi xr + Gr xi) with Gi from the partner
-                    // odd:  y_{k+1} with Gr from the partner
-                    float re = odd ? g0 - b1 : a0 - g1;
-                    float im = odd ? b0 + g1 : g0 + a1;
-                    const int kk = k + (odd ? 1 : 0);
-                    const int j = jb + (kk & 7) + 16 * (kk >> 3);
-                    if (j < ncols) {
-                        float sc = sgn;
-                        if (FP16) sc *= scl[j];
-                        atomicAdd(reinterpret_cast<float2 *>(Yrow + offs[j]), make_float2(sc * re, sc * im));
+                    for (int pk = 0; pk < 8; ++pk) {
+                        const float a0 = __uint_as_float(r[4 * pk]), a1 = __uint_as_float(r[4 * pk + 1]);
+                        const float b0 = __uint_as_float(r[4 * pk + 2]), b1 = __uint_as_float(r[4 * pk + 3]);
+                        // even lane (Re G row) sends column k+1's values, odd lane (Im G row) column k's
+                        const float g0 = __shfl_xor_sync(0xffffffffu, odd ? a0 : b0, 1);
+                        const float g1 = __shfl_xor_sync(0xffffffffu, odd ? a1 : b1, 1);
+                        // even: y_k = (Gr xr - Gi xi, Gi xr + Gr xi) with Gi from the partner
+                        // odd:  y_{k+1} with Gr from the partner
+                        const float re = odd ? g0 - b1 : a0 - g1;
+                        const float im = odd ? b0 + g1 : g0 + a1;
+                        const int j = jb + 2 * pk + (odd ? 1 : 0);
+                        if (j < ncols) {
+                            float sc = sgn;
+                            if (FP16) sc *= scl[j];
+                            red_add_v2(Yrow + 2 * (int64_t)offs[j], sc * re, sc * im);
+                        }
                     }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&accempty[buf]));
             }
-            tc_fence_before();
-            mbar_arrive(smem_u32(&accempty[buf]));
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == kMmaWarp) {
+    if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols));
     }
@@ -585,6 +652,8 @@ ie_status launch_translate_tc(ie_plan p, int prec, float2 *Yslab, int nrhs, cuda
     const bool fp16 = is_fp16(prec);
     const uint16_t *C = fp16 ? p->d_Cfp16 : p->d_Cbf16;
     if (!C) return set_error("tensor-core coupling store for precision %d not built", prec), IE_ERR_UNSUPPORTED;
+    if ((int64_t)p->max_rhs * p->nbox * kNU > (int64_t)INT32_MAX)
+        return set_error("plan too large for the tensor-core translation's 32-bit offsets"), IE_ERR_UNSUPPORTED;
     WorkList *wl = nullptr;
     IE_TRY(work_list(p, true, nrhs, &wl));
     if (wl->n == 0) return IE_OK;
