@@ -66,21 +66,24 @@ typedef enum {
  *  CVFCNN  the translation surrogate of §3: per stored block a complex network
  *          192 -> H -> 192 (input scaled by its l-infinity norm, one hidden layer
  *          with the Cartesian ReLU max(Re z, 0) + j max(Im z, 0), linear output,
- *          output rescaled), evaluated in FP32 on the SIMT cores.  Its weights are
- *          fitted at plan creation in closed form: the network whose output is the
- *          best rank-H approximation of the block (truncated SVD by one-sided Jacobi
- *          in FP64, once per canonical displacement sorted |d|, turned into each
- *          displacement's frame), with hidden biases that keep every pre-activation
- *          in the ReLU's linear region on the unit l-infinity ball;
- *          ie_cvfcnn_set_weights loads any other weights.  Error against G_d: the
- *          SVD tail (ie_plan_stats). */
+ *          output rescaled), evaluated on the tcgen05 tensor cores: both layers are
+ *          fp16 GEMMs with FP32 accumulation, the hidden activations staying in shared
+ *          memory between them.  Weights: fitted at plan creation in closed form (the
+ *          network whose output is the best rank-H approximation of the block:
+ *          truncated SVD by one-sided Jacobi in FP64, once per canonical displacement
+ *          sorted |d|, turned into each displacement's frame, with hidden biases that
+ *          keep every pre-activation in the ReLU's linear region on the unit
+ *          l-infinity ball); ie_cvfcnn_train replaces them by networks trained as in §3
+ *          (first stage), ie_cvfcnn_set_weights by any others.
+ *  CVFCNN_FP32  the same networks evaluated in FP32 on the SIMT cores. */
 typedef enum {
     IE_PREC_FP32 = 1,
     IE_PREC_BF16X3 = 2,
     IE_PREC_FP16X3 = 3,
     IE_PREC_BF16X1 = 4,
     IE_PREC_FP16X1 = 5,
-    IE_PREC_CVFCNN = 6
+    IE_PREC_CVFCNN = 6,
+    IE_PREC_CVFCNN_FP32 = 7
 } ie_prec;
 #define IE_PRECMASK(p) (1u << (unsigned)(p))
 
@@ -390,7 +393,7 @@ ie_status ie_map_basis(const ie_mapping_spec *spec, int64_t n_fun, const int64_t
  * n_coupling_blocks x 3. */
 ie_status ie_plan_blocks(ie_plan plan, int32_t *disp);
 
-/* Replace the fitted surrogate weights (plan prepared with IE_PREC_CVFCNN).  HOST
+/* Replace the fitted surrogate weights (plan prepared with IE_PREC_CVFCNN or CVFCNN_FP32).  HOST
  * complex64 (re, im interleaved), per stored block in ie_plan_blocks order, H the
  * plan's cvfcnn_hidden:  W1 [blocks][H][192], b1 [blocks][H], W2 [blocks][192][H],
  * b2 [blocks][192].  The network of block c maps x to s (W2 relu(W1 x / s + b1) + b2),
@@ -399,6 +402,45 @@ ie_status ie_plan_blocks(ie_plan plan, int32_t *disp);
  * the frame of c (input through S_Q^T, output through S_Q).  Synchronises stream. */
 ie_status ie_cvfcnn_set_weights(ie_plan plan, const float *W1, const float *b1, const float *W2, const float *b2,
                                 void *stream);
+
+/* Read the plan's current surrogate weights back (closed-form, trained or set) into HOST
+ * buffers of the ie_cvfcnn_set_weights layout, which the caller owns.  Synchronises
+ * stream.  Errors: IE_ERR_INVALID (null buffer), IE_ERR_UNSUPPORTED (no surrogates). */
+ie_status ie_cvfcnn_get_weights(ie_plan plan, float *W1, float *b1, float *W2, float *b2, void *stream);
+
+/* Training of the networks (§3, first stage; replaces the closed-form weights).  One
+ * network per canonical displacement c = sorted |d| of the plan's far groups, width the
+ * plan's cvfcnn_hidden, trained from random weights (complex normal, variance 1/192 for
+ * W1 and 1/H for W2, zero biases) with Adam (beta 0.9 / 0.999, step size lr on a cosine
+ * decay to 2% of it over max_steps) on the mean square error between the network and
+ * the DGFA product G_c x (eq. 13) for batches of 32 x minibatches inputs whose real and imaginary
+ * parts are uniform in [-1, 1], normalised by their l-infinity norm as the network's
+ * input is.  Every eval_every steps e^u of eq. 171 (mean relative l2 error of the
+ * outputs) is measured on a fixed test set of 64 such inputs; a network's training ends
+ * once e^u < tol (the paper: 1e-3) or after max_steps.  The inputs come from a counter-
+ * based generator (splitmix64 of seed, network, step, index), so a training run is
+ * reproducible.  The paper's second stage needs RWG-mapped surface data and is not run.
+ * Synchronises `stream`.  info (may be NULL) reports the networks trained, how many
+ * reached tol, the largest and the mean final e^u, the most steps taken and the time.
+ * Errors: IE_ERR_UNSUPPORTED (plan without surrogates), IE_ERR_INVALID, IE_ERR_OOM. */
+typedef struct {
+    int max_steps;         /* Adam steps per network (default 8000)                        */
+    int minibatches;       /* minibatches of 32 inputs per step (default 4: 128 inputs)    */
+    int eval_every;        /* steps between e^u checks (default 250; 0: only at the end)   */
+    double lr;             /* Adam step size (default 4e-3)                                 */
+    double tol;            /* e^u at which a network's training stops (default 1e-3)       */
+    uint64_t seed;         /* generator seed                                               */
+} ie_cvfcnn_train_opts;
+typedef struct {
+    int64_t networks;      /* networks trained (canonical displacements)                   */
+    int64_t converged;     /* networks whose final e^u < tol                               */
+    double eu_max, eu_mean;/* final e^u over the networks                                  */
+    int steps_max;         /* most Adam steps any network took                             */
+    double seconds;        /* host wall time of the call                                   */
+} ie_cvfcnn_train_info;
+void ie_cvfcnn_train_opts_default(ie_cvfcnn_train_opts *o);
+ie_status ie_cvfcnn_train(ie_plan plan, const ie_cvfcnn_train_opts *opts, ie_cvfcnn_train_info *info,
+                          void *stream);
 
 /* ---- diagnostics -------------------------------------------------------------- */
 const char *ie_status_str(ie_status s);

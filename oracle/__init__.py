@@ -600,11 +600,12 @@ def canonical_frame(d):
     return c, Q
 
 
-def cvfcnn_far_matvec(p, c, H: int = 50, weights=None, targets=None) -> np.ndarray:
+def cvfcnn_far_matvec(p, c, H: int = 50, weights=None, targets=None, frames: bool = False) -> np.ndarray:
     """Z^F c with Alg. 2's translation E_t += G_d x_b replaced by the network of d.
     weights None: each canonical c = sorted |d| gets cvfcnn_fit(G_c, H), applied to
     displacement d = Q c in the frame of c: y = S_Q net_c(S_Q^T x).  weights: a dict
-    from displacement tuples to (W1, b1, W2, b2), applied directly."""
+    from displacement tuples to (W1, b1, W2, b2), applied directly; with frames=True
+    its keys are canonical c and each d = Q c uses net_c in the frame of c as above."""
     X = aggregate(p, c)
     nrhs = X.shape[0]
     ds, groups = pair_groups(p, FAR)
@@ -619,8 +620,11 @@ def cvfcnn_far_matvec(p, c, H: int = 50, weights=None, targets=None) -> np.ndarr
             src, dst = src[keep], dst[keep]
         if len(src) == 0:
             continue
-        if weights is not None:
+        if weights is not None and not frames:
             net, S = weights[tuple(int(v) for v in d)], None
+        elif weights is not None:
+            cc, Q = canonical_frame(d)
+            net, S = weights[tuple(int(v) for v in cc)], signed_permutation(Q, p.lattice)
         else:
             cc, Q = canonical_frame(d)
             key = tuple(int(v) for v in cc)

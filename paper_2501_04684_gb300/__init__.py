@@ -20,9 +20,10 @@ LIB_PATH = os.path.join(_HERE, "_build", "libie.so")
 
 IE_OK, IE_ERR_INVALID, IE_ERR_OOM, IE_ERR_CUDA, IE_ERR_NOT_CONVERGED, IE_ERR_TIMEOUT, IE_ERR_UNSUPPORTED = range(7)
 IE_PREC_FP32, IE_PREC_BF16X3, IE_PREC_FP16X3, IE_PREC_BF16X1, IE_PREC_FP16X1, IE_PREC_CVFCNN = 1, 2, 3, 4, 5, 6
+IE_PREC_CVFCNN_FP32 = 7
 IE_FAR, IE_NEAR, IE_FULL = 1, 2, 3
 PREC_NAMES = {IE_PREC_FP32: "fp32", IE_PREC_BF16X3: "bf16x3", IE_PREC_FP16X3: "fp16x3", IE_PREC_BF16X1: "bf16x1",
-              IE_PREC_FP16X1: "fp16x1", IE_PREC_CVFCNN: "cvfcnn"}
+              IE_PREC_FP16X1: "fp16x1", IE_PREC_CVFCNN: "cvfcnn", IE_PREC_CVFCNN_FP32: "cvfcnn_fp32"}
 NU = 192                      # dipole unknowns per box (4^3 lattice x 3 orientations)
 
 EXPORTED = [
@@ -31,7 +32,9 @@ EXPORTED = [
     "ie_solve_opts_default", "ie_solve", "ie_solver_create", "ie_solver_footprint", "ie_solver_start",
     "ie_solver_advance", "ie_solver_poll", "ie_solver_destroy", "ie_status_str", "ie_last_error", "ie_version",
     "ie_plan_profile", "ie_kernel_launches", "ie_translate_noalloc", "ie_plan_check", "ie_diag_bounded_wait",
-    "ie_plan_tune", "ie_map_basis", "ie_plan_blocks", "ie_cvfcnn_set_weights",
+    "ie_plan_tune", "ie_map_basis", "ie_plan_blocks", "ie_cvfcnn_set_weights", "ie_cvfcnn_get_weights",
+    "ie_cvfcnn_train",
+    "ie_cvfcnn_train_opts_default",
 ]
 
 
@@ -64,6 +67,17 @@ class ie_plan_stats(ctypes.Structure):
 class ie_tune_info(ctypes.Structure):
     _fields_ = [("tile_columns", ctypes.c_int), ("order", ctypes.c_int), ("ms", ctypes.c_double),
                 ("default_ms", ctypes.c_double), ("candidates", ctypes.c_int)]
+
+
+class ie_cvfcnn_train_opts(ctypes.Structure):
+    _fields_ = [("max_steps", ctypes.c_int), ("minibatches", ctypes.c_int), ("eval_every", ctypes.c_int),
+                ("lr", ctypes.c_double),
+                ("tol", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class ie_cvfcnn_train_info(ctypes.Structure):
+    _fields_ = [("networks", ctypes.c_int64), ("converged", ctypes.c_int64), ("eu_max", ctypes.c_double),
+                ("eu_mean", ctypes.c_double), ("steps_max", ctypes.c_int), ("seconds", ctypes.c_double)]
 
 
 class ie_mapping_spec(ctypes.Structure):
@@ -129,6 +143,10 @@ def lib() -> ctypes.CDLL:
     L.ie_map_basis.argtypes = [P(ie_mapping_spec), ctypes.c_int64, vp, vp, vp, vp, vp, vp]
     L.ie_plan_blocks.argtypes = [vp, vp]
     L.ie_cvfcnn_set_weights.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.ie_cvfcnn_get_weights.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.ie_cvfcnn_train_opts_default.argtypes = [P(ie_cvfcnn_train_opts)]
+    L.ie_cvfcnn_train_opts_default.restype = None
+    L.ie_cvfcnn_train.argtypes = [vp, P(ie_cvfcnn_train_opts), P(ie_cvfcnn_train_info), vp]
     for name in EXPORTED:          # every declared symbol must resolve
         getattr(L, name)
     _lib = L
@@ -348,6 +366,17 @@ def ie_cvfcnn_set_weights(plan, W1, b1, W2, b2, stream=None):
            "ie_cvfcnn_set_weights")
 
 
+def ie_cvfcnn_get_weights(plan, stream=None):
+    """The plan's current surrogate weights (W1, b1, W2, b2), complex64, in the shapes
+    ie_cvfcnn_set_weights takes."""
+    st = ie_plan_stats_get(plan)
+    nblk, H = int(st["n_coupling_blocks"]), int(st["cvfcnn_hidden"])
+    arrs = [np.zeros(shp, dtype=np.complex64) for shp in [(nblk, H, NU), (nblk, H), (nblk, NU, H), (nblk, NU)]]
+    _check(lib().ie_cvfcnn_get_weights(plan, *[a.ctypes.data for a in arrs], _stream(stream)),
+           "ie_cvfcnn_get_weights")
+    return tuple(arrs)
+
+
 def ie_rhs_plane_wave(plan, khat, pol, v, stream=None):
     """khat, pol: (nrhs, 3), or (n_groups, nrhs, 3) for a batched plan; v: [nrhs][n]."""
     n, _, groups = _dims(plan)
@@ -425,6 +454,23 @@ def ie_plan_tune(plan, prec, nrhs, stream=None) -> dict:
     """Autotunes the tensor-core translation of `prec` for calls with nrhs columns."""
     info = ie_tune_info()
     _check(lib().ie_plan_tune(plan, prec, nrhs, ctypes.byref(info), _stream(stream)), "ie_plan_tune")
+    return {f: getattr(info, f) for f, _ in info._fields_}
+
+
+def cvfcnn_train_opts(**kw) -> ie_cvfcnn_train_opts:
+    """ie_cvfcnn_train_opts with the library's defaults, fields overridden by kw."""
+    o = ie_cvfcnn_train_opts()
+    lib().ie_cvfcnn_train_opts_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def ie_cvfcnn_train(plan, opts: ie_cvfcnn_train_opts | None = None, stream=None) -> dict:
+    """Trains the plan's translation networks (first stage of §3); returns the training info."""
+    info = ie_cvfcnn_train_info()
+    _check(lib().ie_cvfcnn_train(plan, ctypes.byref(opts) if opts is not None else None, ctypes.byref(info),
+                                 _stream(stream)), "ie_cvfcnn_train")
     return {f: getattr(info, f) for f, _ in info._fields_}
 
 

@@ -48,11 +48,13 @@ ie_status dalloc(ie_plan p, void **ptr, size_t bytes) {
 ie_status prepare_translate_simt();
 ie_status prepare_translate_tc();
 ie_status prepare_translate_cvfcnn();
+ie_status prepare_cvfcnn_tc();
 
 ie_status prepare_kernels() {
     IE_TRY(prepare_translate_simt());
     IE_TRY(prepare_translate_tc());
     IE_TRY(prepare_translate_cvfcnn());
+    IE_TRY(prepare_cvfcnn_tc());
     return IE_OK;
 }
 
@@ -66,9 +68,13 @@ bool wants_bf16(unsigned mask) {
     return mask & (IE_PRECMASK(IE_PREC_BF16X3) | IE_PRECMASK(IE_PREC_BF16X1));
 }
 bool wants_fp16(unsigned mask) { return mask & (IE_PRECMASK(IE_PREC_FP16X3) | IE_PRECMASK(IE_PREC_FP16X1)); }
-bool wants_cvfcnn(unsigned mask) { return mask & IE_PRECMASK(IE_PREC_CVFCNN); }
-// FP32 translation inputs are read by the FP32 and the CVFCNN kernels
-bool wants_x32(unsigned mask) { return mask & (IE_PRECMASK(IE_PREC_FP32) | IE_PRECMASK(IE_PREC_CVFCNN)); }
+// networks on the tensor cores (fp16 images) and / or on the SIMT cores (FP32)
+bool wants_cvfcnn_tc(unsigned mask) { return mask & IE_PRECMASK(IE_PREC_CVFCNN); }
+bool wants_cvfcnn(unsigned mask) { return mask & (IE_PRECMASK(IE_PREC_CVFCNN) | IE_PRECMASK(IE_PREC_CVFCNN_FP32)); }
+// FP32 translation inputs are read by the FP32 block and network kernels
+bool wants_x32(unsigned mask) { return mask & (IE_PRECMASK(IE_PREC_FP32) | IE_PRECMASK(IE_PREC_CVFCNN_FP32)); }
+// split 16-bit translation inputs are read by the tensor-core block and network kernels
+bool wants_split(unsigned mask) { return wants_tc(mask) || wants_cvfcnn_tc(mask); }
 constexpr int kCvDefaultHidden = 50;   // the paper's H
 
 ie_status validate(const ie_problem *pr) {
@@ -82,7 +88,8 @@ ie_status validate(const ie_problem *pr) {
     if (!(pr->k > 0) || !(pr->box_edge > 0) || !(pr->eta > 0))
         return set_error("k, eta and box_edge must be positive"), IE_ERR_INVALID;
     unsigned known = IE_PRECMASK(IE_PREC_FP32) | IE_PRECMASK(IE_PREC_BF16X3) | IE_PRECMASK(IE_PREC_FP16X3) |
-                     IE_PRECMASK(IE_PREC_BF16X1) | IE_PRECMASK(IE_PREC_FP16X1) | IE_PRECMASK(IE_PREC_CVFCNN);
+                     IE_PRECMASK(IE_PREC_BF16X1) | IE_PRECMASK(IE_PREC_FP16X1) | IE_PRECMASK(IE_PREC_CVFCNN) |
+                     IE_PRECMASK(IE_PREC_CVFCNN_FP32);
     if (pr->prec_mask == 0 || (pr->prec_mask & ~known)) return set_error("bad prec_mask"), IE_ERR_INVALID;
     if (wants_cvfcnn(pr->prec_mask) && (pr->cvfcnn_hidden < 0 || pr->cvfcnn_hidden > kCvHp))
         return set_error("cvfcnn_hidden %d outside [0, %d]", pr->cvfcnn_hidden, kCvHp), IE_ERR_INVALID;
@@ -346,6 +353,10 @@ size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, i
     }
     if (wants_cvfcnn(pr->prec_mask)) {
         add((size_t)nblk * kCvBlockElems * sizeof(float2));
+        if (wants_cvfcnn_tc(pr->prec_mask)) {   // fp16 images and scales of every network
+            add((size_t)nblk * cvfcnn_image_elems() * sizeof(uint16_t));
+            add((size_t)nblk * 2 * sizeof(int32_t));
+        }
         // FP64 fit scratch (block and right singular vectors) and, without the symmetric
         // store, the canonical networks before their expansion: freed before the plan returns
         add((size_t)std::min<int64_t>(ncanon, kCvFitChunk) * 2 * kNU * kNU * sizeof(double2));
@@ -358,9 +369,10 @@ size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, i
     size_t col = (size_t)pr->max_rhs * nbox;
     add(col * kNU * sizeof(float2));                       // X
     add((size_t)kSlabs * col * kNU * sizeof(float2));      // slabs
-    if (wants_tc(pr->prec_mask)) {
+    if (wants_split(pr->prec_mask)) {
         add((sym ? kSym : 1) * 2 * col * 2 * kNU * sizeof(uint16_t));
         add(col * sizeof(int32_t));
+        add(col * sizeof(float));
     }
     add(sizeof(int) * 4);
     add((size_t)pr->max_rhs * n * sizeof(float2));         // tmp
@@ -378,12 +390,13 @@ size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, i
 // images) run at the same time on neighbouring CTAs of the persistent kernel's static
 // round-robin; order 0 sorts runs by size (largest first).  The tensor-core tile width
 // and order come from ie_plan_tune (default: the full tile width, order 1).
-ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out) {
+ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out, int max_cols) {
     auto &cache = tc ? p->tc_work : p->simt_work;
     int cols = tc ? tc_tile_columns() : simt_tile_columns(), order = 1;
     if (tc) {
         auto t = p->tc_tuned.find(nrhs);
         if (t != p->tc_tuned.end()) cols = t->second.first, order = t->second.second;
+        if (max_cols > 0) cols = std::min(cols, max_cols);
     }
     const int key = tc ? (nrhs * 1024 + cols) * 2 + order : nrhs;
     auto it = cache.find(key);
@@ -396,6 +409,8 @@ ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out) {
         return IE_OK;
     }
     if (nrhs > cols) return set_error("nrhs %d exceeds the tile width %d", nrhs, cols), IE_ERR_INVALID;
+    if (g_capture_depth > 0)      // building a list allocates and copies synchronously
+        return set_error("work list (nrhs %d, %d columns) missing at stream capture", nrhs, cols), IE_ERR_INVALID;
     // right-hand-side columns of a pair: the call's nrhs, or fewer for a scatterer that has fewer
     auto nr_of = [&](int64_t pair) {
         if (p->gnrhs.empty()) return nrhs;
@@ -434,6 +449,15 @@ ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out) {
     return IE_OK;
 }
 
+ie_status work_list_for(ie_plan p, int prec, int nrhs, WorkList **out) {
+    if (prec == IE_PREC_FP32 || prec == IE_PREC_CVFCNN_FP32) return work_list(p, false, nrhs, out);
+    if (prec == IE_PREC_CVFCNN) return work_list(p, true, nrhs, out, cvfcnn_tc_tile_columns());
+    return work_list(p, true, nrhs, out);
+}
+
+int canon_of_disp(const int32_t d[3], int32_t c[3]) { return canon_of(d, c); }
+void symmetry_map_host(std::vector<uint16_t> &map) { symmetry_map(map); }
+
 ie_status translate_timed(ie_plan p, int prec, const float2 *X, float2 *Yslab, int nrhs, cudaStream_t st,
                           const int *gate) {
     bool timed = false;
@@ -445,8 +469,10 @@ ie_status translate_timed(ie_plan p, int prec, const float2 *X, float2 *Yslab, i
     if (timed) IE_CK(cudaEventRecord(p->prof_ev[0], st));
     if (prec == IE_PREC_FP32)
         IE_TRY(launch_translate_simt(p, X, Yslab, nrhs, st, gate));
-    else if (prec == IE_PREC_CVFCNN)
+    else if (prec == IE_PREC_CVFCNN_FP32)
         IE_TRY(launch_translate_cvfcnn(p, X, Yslab, nrhs, st, gate));
+    else if (prec == IE_PREC_CVFCNN)
+        IE_TRY(launch_translate_cvfcnn_tc(p, Yslab, nrhs, st, gate));
     else
         IE_TRY(launch_translate_tc(p, prec, Yslab, nrhs, st, gate));
     if (timed) {
@@ -465,7 +491,7 @@ ie_status far_product(ie_plan p, int prec, const float2 *c, float2 *y, int nrhs,
     size_t stride = slab_stride(p);
     IE_TRY(launch_aggregate(p, c, p->d_X, nrhs, st, gate));
     IE_TRY(launch_zero_slabs(p->d_Yslab, kSlabs, stride, (size_t)nrhs * p->nbox * kNU, st, gate));
-    if (is_tc(prec)) IE_TRY(launch_split_tc(p, p->d_X, nrhs, is_fp16(prec), st, gate));
+    if (uses_split(prec)) IE_TRY(launch_split_tc(p, p->d_X, nrhs, is_fp16(prec), st, gate));
     IE_TRY(translate_timed(p, prec, p->d_X, p->d_Yslab, nrhs, st, gate));
     IE_TRY(launch_disaggregate(p, p->d_Yslab, kSlabs, stride, y, nrhs, accumulate, st, gate));
     return IE_OK;
@@ -494,7 +520,7 @@ ie_status apply(ie_plan p, int which, int prec, const float2 *c, float2 *y, int 
 using namespace ie;
 
 static ie_status check_prec(ie_plan p, int prec) {
-    if (prec < IE_PREC_FP32 || prec > IE_PREC_CVFCNN) return set_error("unknown precision %d", prec), IE_ERR_INVALID;
+    if (prec < IE_PREC_FP32 || prec > IE_PREC_CVFCNN_FP32) return set_error("unknown precision %d", prec), IE_ERR_INVALID;
     if (!(p->prec_mask & IE_PRECMASK(prec)))
         return set_error("precision %d not prepared by this plan", prec), IE_ERR_UNSUPPORTED;
     return IE_OK;
@@ -751,6 +777,11 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
                     if (ptr) cudaFreeAsync(ptr, st);
                 PT(fs);
             }
+            if (wants_cvfcnn_tc(p->prec_mask)) {
+                PT(dalloc_t(p, &p->d_cvimg, (size_t)p->n_blocks * cvfcnn_image_elems()));
+                PT(dalloc_t(p, &p->d_cvexp, (size_t)p->n_blocks * 2));
+                PT(build_cvfcnn_images(p, st));
+            }
         }
     }
 
@@ -776,9 +807,10 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
     size_t col = (size_t)p->max_rhs * p->nbox;
     PT(dalloc_t(p, &p->d_X, col * kNU));
     PT(dalloc_t(p, &p->d_Yslab, (size_t)kSlabs * col * kNU));
-    if (wants_tc(p->prec_mask)) {
+    if (wants_split(p->prec_mask)) {
         PT(dalloc_t(p, &p->d_Xtc, (size_t)(p->sym ? kSym : 1) * 2 * col * 2 * kNU));
         PT(dalloc_t(p, &p->d_Xexp, col));
+        PT(dalloc_t(p, &p->d_Xinf, col));
     }
     if (p->sym && wants_x32(p->prec_mask)) PT(dalloc_t(p, &p->d_Xsym, (size_t)kSym * col * kNU));
     PT(dalloc_t(p, &p->d_err, 4));
@@ -934,7 +966,7 @@ ie_status ie_translate(ie_plan p, int prec, const void *X, void *Y, int nrhs, vo
     cudaStream_t st = (cudaStream_t)stream;
     size_t stride = slab_stride(p);
     IE_TRY(launch_zero_slabs(p->d_Yslab, kSlabs, stride, (size_t)nrhs * p->nbox * kNU, st));
-    if (is_tc(prec)) IE_TRY(launch_split_tc(p, (const float2 *)X, nrhs, is_fp16(prec), st));
+    if (uses_split(prec)) IE_TRY(launch_split_tc(p, (const float2 *)X, nrhs, is_fp16(prec), st));
     IE_TRY(translate_timed(p, prec, (const float2 *)X, p->d_Yslab, nrhs, st, nullptr));
     return launch_sum_slabs(p, p->d_Yslab, kSlabs, stride, (float2 *)Y, nrhs, st);
 }

@@ -572,6 +572,13 @@ ie_status launch_cvfcnn_fit(ie_plan p, const int32_t *canon_disp, int64_t ncanon
     return s;
 }
 
+void launch_cvfcnn_expand(const float2 *Wc, const int32_t *gcanon, const int32_t *gsigma, const uint16_t *map,
+                          int64_t nblk, float2 *Wd, cudaStream_t st) {
+    if (nblk <= 0) return;
+    cvfcnn_expand_kernel<<<(unsigned)nblk, 256, 0, st>>>(Wc, gcanon, gsigma, map, Wd);
+    count_launches(1);
+}
+
 ie_status prepare_translate_cvfcnn() {
     IE_CK(cudaFuncSetAttribute(cvfcnn_translate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)sizeof(SmemCv)));
@@ -580,10 +587,10 @@ ie_status prepare_translate_cvfcnn() {
 
 ie_status launch_translate_cvfcnn(ie_plan p, const float2 *X, float2 *Yslab, int nrhs, cudaStream_t st,
                                   const int *gate) {
-    if (!(p->prec_mask & IE_PRECMASK(IE_PREC_CVFCNN)))
-        return set_error("the plan holds no CVFCNN surrogates"), IE_ERR_UNSUPPORTED;
+    if (!(p->prec_mask & IE_PRECMASK(IE_PREC_CVFCNN_FP32)))
+        return set_error("the plan holds no FP32 CVFCNN surrogates"), IE_ERR_UNSUPPORTED;
     WorkList *wl = nullptr;
-    IE_TRY(work_list(p, false, nrhs, &wl));
+    IE_TRY(work_list_for(p, IE_PREC_CVFCNN_FP32, nrhs, &wl));
     if (wl->n == 0) return IE_OK;
     SymArgs sy;
     if (p->sym) {
@@ -625,6 +632,31 @@ extern "C" ie_status ie_cvfcnn_set_weights(ie_plan p, const float *W1, const flo
     }
     cudaStream_t st = (cudaStream_t)stream;
     IE_CK(cudaMemcpyAsync(p->d_cvW, w.data(), w.size() * sizeof(float2), cudaMemcpyHostToDevice, st));
+    IE_TRY(build_cvfcnn_images(p, st));
     IE_CK(cudaStreamSynchronize(st));
+    return IE_OK;
+}
+
+extern "C" ie_status ie_cvfcnn_get_weights(ie_plan p, float *W1, float *b1, float *W2, float *b2, void *stream) {
+    if (!p || !W1 || !b1 || !W2 || !b2) return set_error("null argument"), IE_ERR_INVALID;
+    if (!p->d_cvW) return set_error("the plan holds no CVFCNN surrogates"), IE_ERR_UNSUPPORTED;
+    const int H = p->cv_hidden;
+    const int64_t nblk = p->n_blocks;
+    std::vector<float2> w((size_t)nblk * kCvBlockElems);
+    cudaStream_t st = (cudaStream_t)stream;
+    IE_CK(cudaMemcpyAsync(w.data(), p->d_cvW, w.size() * sizeof(float2), cudaMemcpyDeviceToHost, st));
+    IE_CK(cudaStreamSynchronize(st));
+    auto put = [](float *a, size_t i, float2 v) { a[2 * i] = v.x, a[2 * i + 1] = v.y; };
+    for (int64_t c = 0; c < nblk; ++c) {
+        const float2 *o = w.data() + (size_t)c * kCvBlockElems;
+        for (int h = 0; h < H; ++h) {
+            for (int u = 0; u < kNU; ++u) {
+                put(W1, ((size_t)c * H + h) * kNU + u, o[kCvW1 + (size_t)u * kCvHp + h]);
+                put(W2, ((size_t)c * kNU + u) * H + h, o[kCvW2 + (size_t)h * kNU + u]);
+            }
+            put(b1, (size_t)c * H + h, o[kCvB1 + h]);
+        }
+        for (int u = 0; u < kNU; ++u) put(b2, (size_t)c * kNU + u, o[kCvB2 + u]);
+    }
     return IE_OK;
 }

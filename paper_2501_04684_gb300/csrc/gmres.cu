@@ -862,7 +862,7 @@ ie_status ie_solver_create(ie_plan p, int nrhs, const ie_solve_opts *opts, ie_so
     }
     // work lists must exist before graph capture (they allocate)
     WorkList *wl = nullptr;
-    e = work_list(p, is_tc(o.prec), R, &wl);
+    e = work_list_for(p, o.prec, R, &wl);
     if (e != IE_OK) return fail(e);
     if (cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess) {

@@ -30,10 +30,13 @@ constexpr int kLattice = 4;
 constexpr int kSites = 64;          // 4^3 dipole sites per box
 constexpr int kNU = 192;            // 3 unknowns per site
 constexpr int kSlabs = 8;           // FP32 partial-sum slabs of the far field (see translate_simt.cu)
-// Precisions whose products use the fp16 split store (per-block power-of-two scaling).
-inline bool is_fp16(int prec) { return prec == IE_PREC_FP16X3 || prec == IE_PREC_FP16X1; }
-// Precisions whose translation runs on the tensor cores (split 16-bit inputs).
+// Precisions whose products read fp16 split inputs (power-of-two column scaling).
+inline bool is_fp16(int prec) { return prec == IE_PREC_FP16X3 || prec == IE_PREC_FP16X1 || prec == IE_PREC_CVFCNN; }
+// Precisions whose translation is the block product on the tensor cores.
 inline bool is_tc(int prec) { return prec >= IE_PREC_BF16X3 && prec <= IE_PREC_FP16X1; }
+// Precisions whose translation reads the split 16-bit inputs (block products and networks
+// on the tensor cores); their work lists are the tensor-core ones.
+inline bool uses_split(int prec) { return is_tc(prec) || prec == IE_PREC_CVFCNN; }
 constexpr int kSym = 48;             // signed permutations of the three axes
 constexpr int64_t kCouplingChunk = 4096;   // displacements per staging chunk of the 16-bit coupling images
 
@@ -179,9 +182,12 @@ struct ie_plan_s {
     float2 *d_Xsym = nullptr;          // [48][max_rhs][nbox][192] signed-permuted FP32 translation inputs
     // CVFCNN surrogates (IE_PREC_CVFCNN), one network per stored block
     int cv_hidden = 0;
+    int cv_trained = 0;                // 1 once ie_cvfcnn_train has replaced the closed-form weights
     int cv_sweeps = 0;
     double cv_tail = 0;
     float2 *d_cvW = nullptr;           // [n_blocks][kCvBlockElems]
+    uint16_t *d_cvimg = nullptr;       // [n_blocks][12 images] fp16 networks for the tensor cores
+    int32_t *d_cvexp = nullptr;        // [n_blocks][2] power-of-two scales of the two layers' images
 
     // near zone: per target box a run of (source box, block offset)
     int64_t n_near_pairs = 0;
@@ -196,6 +202,7 @@ struct ie_plan_s {
     float2 *d_Yslab = nullptr;         // [kSlabs][max_rhs][nbox][192]
     uint16_t *d_Xtc = nullptr;         // [48 with symmetry][2 hl][max_rhs][nbox][6 chunk][2 reim][32] 16-bit
     int32_t *d_Xexp = nullptr;         // [max_rhs][nbox] power-of-two scale of d_Xtc columns
+    float *d_Xinf = nullptr;           // [max_rhs][nbox] max_u |x_u| of each translation input column
     int *d_err = nullptr;              // device error word of bounded waits
     float2 *d_tmp = nullptr;           // [max_rhs][n] scratch of products
 
@@ -267,7 +274,12 @@ ie_status far_product(ie_plan p, int prec, const float2 *c, float2 *y, int nrhs,
                       const int *gate = nullptr);
 ie_status apply(ie_plan p, int which, int prec, const float2 *c, float2 *y, int nrhs, cudaStream_t st,
                 const int *gate = nullptr);
-ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out);
+// max_cols > 0 (tensor-core lists): no item wider than max_cols columns
+ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out, int max_cols = 0);
+// The work list the translation of precision `prec` launches with (the same cache entry):
+// made ahead of a stream capture, since building one allocates.
+ie_status work_list_for(ie_plan p, int prec, int nrhs, WorkList **out);
+int cvfcnn_tc_tile_columns();
 void destroy_cached_solvers(ie_plan p);
 // launch the translation kernel of `prec` (with the profiling brackets when enabled)
 ie_status translate_timed(ie_plan p, int prec, const float2 *X, float2 *Yslab, int nrhs, cudaStream_t st,
@@ -280,5 +292,20 @@ ie_status bounded_wait_selftest(double limit_ms, cudaStream_t st);
 ie_status take_device_error(ie_plan p, cudaStream_t st);
 
 size_t slab_stride(const ie_plan p);   // elements between far-field slabs
+
+// canonical c = sorted |d| of a displacement and the signed permutation Q with Q c = d
+int canon_of_disp(const int32_t d[3], int32_t c[3]);
+// map[Q][u] = U_Q(u) | 0x100 when negated, 48 x 192 (see the symmetric store)
+void symmetry_map_host(std::vector<uint16_t> &map);
+// every stored block's network from the canonical ones (Wc [ncanon][kCvBlockElems]),
+// turned into the block's frame
+void launch_cvfcnn_expand(const float2 *Wc, const int32_t *gcanon, const int32_t *gsigma, const uint16_t *map,
+                          int64_t nblk, float2 *Wd, cudaStream_t st);
+// tensor-core networks: images (after a fit, training or loaded weights) and inference
+size_t cvfcnn_image_elems();
+ie_status build_cvfcnn_images(ie_plan p, cudaStream_t st);
+ie_status launch_translate_cvfcnn_tc(ie_plan p, float2 *Yslab, int nrhs, cudaStream_t st, const int *gate);
+// trains the plan's networks (§3, first stage) and stores them in the plan
+ie_status launch_cvfcnn_train(ie_plan p, const ie_cvfcnn_train_opts &o, ie_cvfcnn_train_info *info, cudaStream_t st);
 
 }  // namespace ie

@@ -53,7 +53,7 @@ __global__ void copy_kernel(const float4 *__restrict__ a, float4 *__restrict__ b
 // x^Q[u] = +-x[U_Q(u)] at Xtc + z * (2 planes); the scale is the same for every copy.
 template <bool FP16>
 __global__ void split_kernel(const float2 *__restrict__ X, int nbox, int nrhs, uint16_t *__restrict__ Xtc,
-                             int32_t *__restrict__ Xexp, const uint16_t *__restrict__ symmap,
+                             int32_t *__restrict__ Xexp, float *__restrict__ Xinf, const uint16_t *__restrict__ symmap,
                              const int *__restrict__ gate) {
     if (gate && *gate == 0) return;
     int b = blockIdx.x, r = blockIdx.y, u = threadIdx.x;
@@ -70,15 +70,20 @@ __global__ void split_kernel(const float2 *__restrict__ X, int nbox, int nrhs, u
     const bool write_exp = sg == 0;
     float scale = 1.f;
     if (FP16) {
-        __shared__ float red[8];
+        __shared__ float red[8], red2[8];
         __shared__ float s_scale;
         float m = fmaxf(fabsf(x.x), fabsf(x.y));
-        for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if ((u & 31) == 0) red[u >> 5] = m;
+        float m2 = x.x * x.x + x.y * x.y;     // for max_u |x_u| (the networks' input norm)
+        for (int o = 16; o; o >>= 1) {
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            m2 = fmaxf(m2, __shfl_xor_sync(0xffffffffu, m2, o));
+        }
+        if ((u & 31) == 0) red[u >> 5] = m, red2[u >> 5] = m2;
         __syncthreads();
         if (u == 0) {
-            float mm = 0.f;
-            for (int w = 0; w < kNU / 32; ++w) mm = fmaxf(mm, red[w]);
+            float mm = 0.f, mm2 = 0.f;
+            for (int w = 0; w < kNU / 32; ++w) mm = fmaxf(mm, red[w]), mm2 = fmaxf(mm2, red2[w]);
+            if (write_exp && Xinf) Xinf[col] = sqrtf(mm2);
             int e = 0;
             if (mm > 0.f) {
                 frexpf(mm, &e);
@@ -273,9 +278,9 @@ ie_status launch_split_tc(const ie_plan p, const float2 *X, int nrhs, bool fp16,
     const dim3 grid(p->nbox, nrhs, p->sym ? kSym : 1);
     const uint16_t *map = p->sym ? p->d_symmap : nullptr;
     if (fp16)
-        split_kernel<true><<<grid, kNU, 0, st>>>(X, p->nbox, nrhs, p->d_Xtc, p->d_Xexp, map, gate);
+        split_kernel<true><<<grid, kNU, 0, st>>>(X, p->nbox, nrhs, p->d_Xtc, p->d_Xexp, p->d_Xinf, map, gate);
     else
-        split_kernel<false><<<grid, kNU, 0, st>>>(X, p->nbox, nrhs, p->d_Xtc, p->d_Xexp, map, gate);
+        split_kernel<false><<<grid, kNU, 0, st>>>(X, p->nbox, nrhs, p->d_Xtc, p->d_Xexp, nullptr, map, gate);
     IE_CK_LAUNCH();
     return IE_OK;
 }

@@ -186,7 +186,7 @@ ie_status prepare_translate_simt() {
 ie_status launch_translate_simt(ie_plan p, const float2 *X, float2 *Yslab, int nrhs, cudaStream_t st,
                                 const int *gate) {
     WorkList *wl = nullptr;
-    IE_TRY(work_list(p, false, nrhs, &wl));
+    IE_TRY(work_list_for(p, IE_PREC_FP32, nrhs, &wl));
     if (wl->n == 0) return IE_OK;
     if (!p->d_Csimt) return set_error("the plan holds no FP32 coupling store"), IE_ERR_UNSUPPORTED;
     SymArgs sy;

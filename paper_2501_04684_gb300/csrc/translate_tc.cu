@@ -76,6 +76,7 @@ constexpr uint32_t kTmemCols = 512;
 constexpr long long kWaitCycles = 1ll << 31;     // bounded waits give up after ~1 s of SM clock
 static_assert(kAStages * kAStageBytes % 1024 == 0 && kBChunkBytes % 1024 == 0, "operand tiles 1 KB aligned");
 static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+static_assert(kGath >= kTcTileCols, "one gatherer thread per column of an item");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -655,7 +656,7 @@ ie_status launch_translate_tc(ie_plan p, int prec, float2 *Yslab, int nrhs, cuda
     if ((int64_t)p->max_rhs * p->nbox * kNU > (int64_t)INT32_MAX)
         return set_error("plan too large for the tensor-core translation's 32-bit offsets"), IE_ERR_UNSUPPORTED;
     WorkList *wl = nullptr;
-    IE_TRY(work_list(p, true, nrhs, &wl));
+    IE_TRY(work_list_for(p, prec, nrhs, &wl));
     if (wl->n == 0) return IE_OK;
     TcArgs a;
     a.items = wl->d_items;

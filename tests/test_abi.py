@@ -78,7 +78,8 @@ def test_footprint_is_host_only_and_counts_pairs(built):
     dict(box_group=np.zeros(64), group_alpha=[1.0], group_nrhs=[0]),            # count below 1
     dict(prec_mask=ie.precmask(ie.IE_PREC_CVFCNN), cvfcnn_hidden=65),           # hidden width above 64
     dict(prec_mask=ie.precmask(ie.IE_PREC_CVFCNN), cvfcnn_hidden=-1),
-    dict(prec_mask=1 << 7),                                                     # unknown precision
+    dict(prec_mask=ie.precmask(ie.IE_PREC_CVFCNN_FP32), cvfcnn_hidden=65),
+    dict(prec_mask=1 << 8),                                                     # unknown precision
 ])
 def test_validation_rejects(built, bad):
     pr = _tiny_problem(**bad)

@@ -1,19 +1,28 @@
-"""Translation networks of §3 (IE_PREC_CVFCNN) on the GPU against the FP64 oracle.
+"""Translation networks of §3 on the GPU against the FP64 oracle.
 
-The library evaluates, per stored block, the network s (W2 relu(W1 x / s + b1) + b2)
-with s = ||x||_inf in FP32, inside Alg. 2 in place of G_d x.  Fitted weights put the
-network in its linear regime, equal to the truncated SVD of G_c; each side fits its own
-(Jacobi SVD on the GPU, LAPACK in the oracle), and the networks' outputs are unique.
+Per stored block the network s (W2 relu(W1 x / s + b1) + b2), s = ||x||_inf, replaces
+G_d x inside Alg. 2.  Two evaluations: IE_PREC_CVFCNN_FP32 (FP32 SIMT) and IE_PREC_CVFCNN
+(tcgen05, fp16 operands, FP32 accumulation).  Weights are the closed-form fit (the
+truncated SVD put into the ReLU's linear regime; each side fits its own, Jacobi SVD on
+the GPU, LAPACK in the oracle), weights loaded through ie_cvfcnn_set_weights, or the
+networks ie_cvfcnn_train trains (§3, first stage), read back with ie_cvfcnn_get_weights.
 
 Uniqueness: where sigma_H = sigma_H+1 the truncation (hence the network) is not unique.  At
 H = 50 that happens on seven of shell16's 473 classes, all with sigma_50 <= 1.1e-8 sigma_1,
 so either choice moves the output by less than that; widths whose cutoff splits a large
 degenerate pair (H = 1 for axis and diagonal displacements) are not compared.
 
-Tolerances.  Network against network: FP32 sums of 192 and H terms plus the hidden bias,
-which is up to sqrt(192) times the hidden signal and cancels in the output bias: about
-25 x 6e-8 x sqrt(H) ~ 1e-5 relative, so 3e-5.  Network against the exact translation:
-the SVD tail of the blocks (the oracle computes 8.7e-6 on the 4^3 grid), plus the above.
+Tolerances.  FP32 network against the oracle's: FP32 sums of 192 and H terms plus the
+hidden bias, which is up to sqrt(192) times the hidden signal and cancels in the output
+bias: about 25 x 6e-8 x sqrt(H) ~ 1e-5 relative, so NET_TOL = 3e-5.  Tensor-core network:
+four fp16 roundings (the scaled input, the W1 image, the hidden activation, the W2 image),
+each at most u = 2^-11 relative per element; their first-order sum is at most 4u = 2e-3
+(TC_TOL) as long as the network does not cancel, i.e. |W2| |h| ~ |W2 h| (random and
+trained weights; measured 2.6e-4 on trained ones).  The closed-form fit does cancel (its
+hidden bias is ~sqrt(192) times the signal), which multiplies the fp16 error by ~25
+(1.2e-2 measured): fitted weights are for the FP32 evaluation.  Network against the exact
+translation: the SVD tail of the blocks (the oracle computes 8.7e-6 on the 4^3 grid), or
+the trained networks' e^u of eq. 171, plus the above.
 """
 import numpy as np
 import pytest
@@ -25,6 +34,8 @@ from gpu_util import dev, empty, host, rel_l2
 
 pytestmark = pytest.mark.gpu
 NET_TOL = 3e-5
+TC_TOL = 2e-3
+FP32NET = ie.IE_PREC_CVFCNN_FP32
 
 
 def _plan(p, precs, symmetry, max_rhs=1, hidden=0):
@@ -44,7 +55,7 @@ def _svd_tail(C, H):
 
 
 def test_fit_statistics_and_block_order(tiny):
-    with _plan(tiny, [ie.IE_PREC_CVFCNN], symmetry=1) as plan:
+    with _plan(tiny, [FP32NET], symmetry=1) as plan:
         st = plan.stats
         blocks = ie.ie_plan_blocks(plan.handle)
     ds, _ = oracle.pair_groups(tiny, oracle.FAR)
@@ -60,7 +71,7 @@ def test_random_weights_match_the_oracle_network(tiny):
     displacement (full store), loaded through ie_cvfcnn_set_weights."""
     H = 7
     c = W.coefficients(tiny, 2, 970)
-    with _plan(tiny, [ie.IE_PREC_CVFCNN], symmetry=0, max_rhs=2, hidden=H) as plan:
+    with _plan(tiny, [FP32NET], symmetry=0, max_rhs=2, hidden=H) as plan:
         blocks = ie.ie_plan_blocks(plan.handle)
         g = W.rng(971)
         nb = len(blocks)
@@ -70,7 +81,7 @@ def test_random_weights_match_the_oracle_network(tiny):
         b2 = W.complex_normal(g, (nb, 192)) * 0.1
         ie.ie_cvfcnn_set_weights(plan.handle, W1, b1, W2, b2)
         y = empty((2, tiny.n))
-        ie.ie_matvec(plan.handle, ie.IE_FAR, ie.IE_PREC_CVFCNN, dev(c), y, 2)
+        ie.ie_matvec(plan.handle, ie.IE_FAR, FP32NET, dev(c), y, 2)
         got = host(y)
     # the oracle takes the weights as the library stored them (complex64)
     r = lambda a: a.astype(np.complex64).astype(np.complex128)  # noqa: E731
@@ -88,9 +99,9 @@ def test_fitted_far_product(symmetry, tiny):
     c = W.coefficients(tiny, 1, 972)
     ref_net = oracle.cvfcnn_far_matvec(tiny, c, H=50)
     ref = oracle.far_matvec(tiny, c)
-    with _plan(tiny, [ie.IE_PREC_FP32, ie.IE_PREC_CVFCNN], symmetry=symmetry) as plan:
+    with _plan(tiny, [ie.IE_PREC_FP32, FP32NET], symmetry=symmetry) as plan:
         y = empty((1, tiny.n))
-        ie.ie_matvec(plan.handle, ie.IE_FAR, ie.IE_PREC_CVFCNN, dev(c), y, 1)
+        ie.ie_matvec(plan.handle, ie.IE_FAR, FP32NET, dev(c), y, 1)
         got = host(y)
         tail = plan.stats["cvfcnn_tail"]
     assert rel_l2(got, ref_net) <= NET_TOL
@@ -105,9 +116,9 @@ def test_fitted_far_product_at_the_papers_box_edges(tag):
     c = W.coefficients(p, 1, 973)
     ref_net = oracle.cvfcnn_far_matvec(p, c, H=50)
     ref = oracle.far_matvec(p, c)
-    with _plan(p, [ie.IE_PREC_CVFCNN], symmetry=1) as plan:
+    with _plan(p, [FP32NET], symmetry=1) as plan:
         y = empty((1, p.n))
-        ie.ie_matvec(plan.handle, ie.IE_FAR, ie.IE_PREC_CVFCNN, dev(c), y, 1)
+        ie.ie_matvec(plan.handle, ie.IE_FAR, FP32NET, dev(c), y, 1)
         got = host(y)
         tail = plan.stats["cvfcnn_tail"]
     assert rel_l2(got, ref_net) <= NET_TOL
@@ -122,9 +133,9 @@ def test_surrogate_solve_with_refinement(tiny):
     kh, pol = W.plane_wave_spec(1)
     v = oracle.plane_wave_rhs(tiny, kh, pol)
     ref = np.linalg.solve(Z, v[0])
-    with _plan(tiny, [ie.IE_PREC_FP16X3, ie.IE_PREC_CVFCNN], symmetry=1) as plan:
+    with _plan(tiny, [ie.IE_PREC_FP16X3, FP32NET], symmetry=1) as plan:
         x = empty((1, tiny.n))
-        opts = ie.solve_opts(tol=1e-5, prec=ie.IE_PREC_CVFCNN, refine=1, refine_prec=ie.IE_PREC_FP16X3,
+        opts = ie.solve_opts(tol=1e-5, prec=FP32NET, refine=1, refine_prec=ie.IE_PREC_FP16X3,
                              inner_tol=1e-3)
         st, info = ie.ie_solve(plan.handle, dev(v), x, 1, opts)
         assert st == ie.IE_OK, info
@@ -142,10 +153,10 @@ def test_shell16_sampled(tiny):
     rows = oracle.basis_rows(p, targets)
     ref_net = oracle.cvfcnn_far_matvec(p, c, H=50, targets=targets)
     ref = oracle.far_matvec(p, c, targets=targets)
-    with _plan(p, [ie.IE_PREC_CVFCNN], symmetry=1) as plan:
+    with _plan(p, [FP32NET], symmetry=1) as plan:
         assert plan.stats["n_coupling_blocks"] == 473
         y = empty((1, p.n))
-        ie.ie_matvec(plan.handle, ie.IE_FAR, ie.IE_PREC_CVFCNN, dev(c), y, 1)
+        ie.ie_matvec(plan.handle, ie.IE_FAR, FP32NET, dev(c), y, 1)
         got = host(y)[:, rows]
     assert rel_l2(got, ref_net) <= NET_TOL
     assert rel_l2(got, ref) <= 2 * rel_l2(ref_net, ref) + NET_TOL
@@ -158,7 +169,7 @@ def test_weights_need_a_surrogate_plan(tiny):
         assert ie.lib().ie_cvfcnn_set_weights(plan.handle, ptr, ptr, ptr, ptr, None) == ie.IE_ERR_UNSUPPORTED
         with pytest.raises(ie.IEError) as e:
             y = empty((1, tiny.n))
-            ie.ie_matvec(plan.handle, ie.IE_FAR, ie.IE_PREC_CVFCNN, dev(W.coefficients(tiny, 1, 1)), y, 1)
+            ie.ie_matvec(plan.handle, ie.IE_FAR, FP32NET, dev(W.coefficients(tiny, 1, 1)), y, 1)
         assert e.value.status == ie.IE_ERR_UNSUPPORTED
 
 
@@ -172,10 +183,10 @@ def test_batch_of_scatterers_with_their_own_rhs_counts(symmetry):
     for g, m in enumerate(b.members):
         members[g][b.nrhs[g]:] = 0.0                      # padding columns stay zero
     refs = [oracle.cvfcnn_far_matvec(m, c[:b.nrhs[g]], H=50) for g, (m, c) in enumerate(zip(b.members, members))]
-    pr = ie.problem_from_batch(b, ie.precmask(ie.IE_PREC_CVFCNN), symmetry=symmetry, exact_rhs=True)
+    pr = ie.problem_from_batch(b, ie.precmask(FP32NET), symmetry=symmetry, exact_rhs=True)
     with ie.Plan(pr) as plan:
         y = empty((R, b.n))
-        ie.ie_matvec(plan.handle, ie.IE_FAR, ie.IE_PREC_CVFCNN, dev(np.concatenate(members, axis=1)), y, R)
+        ie.ie_matvec(plan.handle, ie.IE_FAR, FP32NET, dev(np.concatenate(members, axis=1)), y, R)
         for g, got in enumerate(b.split(host(y))):
             q = b.nrhs[g]
             assert rel_l2(got[:q], refs[g]) <= NET_TOL, g
@@ -188,7 +199,7 @@ def test_footprint_covers_the_surrogate_plan(symmetry):
     device (it also counts the fit's scratch, freed before the plan returns)."""
     p = W.shell16()
     p.alpha = W.alpha_for("shell16")
-    pr = ie.problem_from(p, ie.precmask(ie.IE_PREC_FP32, ie.IE_PREC_CVFCNN), symmetry=symmetry)
+    pr = ie.problem_from(p, ie.precmask(ie.IE_PREC_FP32, FP32NET), symmetry=symmetry)
     fp = ie.ie_plan_footprint(pr)
     with ie.Plan(pr) as plan:
         held = plan.stats["device_bytes"]
@@ -206,9 +217,190 @@ def test_hidden_width_limits(hidden, tiny):
     is unique on this grid (relative gap 0.2 or more)."""
     c = W.coefficients(tiny, 1, 974)
     ref_net = oracle.cvfcnn_far_matvec(tiny, c, H=hidden)
-    with _plan(tiny, [ie.IE_PREC_CVFCNN], symmetry=1, hidden=hidden) as plan:
+    with _plan(tiny, [FP32NET], symmetry=1, hidden=hidden) as plan:
         assert plan.stats["cvfcnn_hidden"] == hidden
         y = empty((1, tiny.n))
-        ie.ie_matvec(plan.handle, ie.IE_FAR, ie.IE_PREC_CVFCNN, dev(c), y, 1)
+        ie.ie_matvec(plan.handle, ie.IE_FAR, FP32NET, dev(c), y, 1)
         got = host(y)
     assert rel_l2(got, ref_net) <= NET_TOL
+
+
+# ------------------------------------------------------------ tensor-core evaluation
+def _random_weights(g, nb, H):
+    """Weights whose hidden pre-activations change sign often (ReLU active) and whose
+    biases are of the order of the signal (no cancelling bias)."""
+    return (W.complex_normal(g, (nb, H, 192)) / 14, W.complex_normal(g, (nb, H)) * 0.3,
+            W.complex_normal(g, (nb, 192, H)) / 3, W.complex_normal(g, (nb, 192)) * 0.1)
+
+
+def _as_stored(blocks, arrs):
+    """The oracle's weight dict, from the weights as the library stores them (complex64)."""
+    r = lambda a: np.asarray(a).astype(np.complex64).astype(np.complex128)  # noqa: E731
+    return {tuple(int(v) for v in d): tuple(r(a[i]) for a in arrs) for i, d in enumerate(blocks)}
+
+
+@pytest.mark.parametrize("symmetry,H,nrhs", [(0, 50, 2), (1, 50, 3), (1, 2, 1), (0, 64, 1), (1, 64, 2)])
+def test_tensor_core_network_on_loaded_weights(symmetry, H, nrhs, tiny):
+    """IE_PREC_CVFCNN against the oracle's network on the same loaded weights (and the FP32
+    evaluation beside it).  With 2 and 3 right-hand sides a displacement's run holds up to
+    128 and 192 columns: several 80-column items with a ragged last one."""
+    c = W.coefficients(tiny, nrhs, 975 + H)
+    with _plan(tiny, [ie.IE_PREC_CVFCNN, FP32NET], symmetry=symmetry, max_rhs=nrhs, hidden=H) as plan:
+        blocks = ie.ie_plan_blocks(plan.handle)
+        arrs = _random_weights(W.rng(976 + H), len(blocks), H)
+        ie.ie_cvfcnn_set_weights(plan.handle, *arrs)
+        back = ie.ie_cvfcnn_get_weights(plan.handle)
+        y, y32 = empty((nrhs, tiny.n)), empty((nrhs, tiny.n))
+        cd = dev(c)
+        ie.ie_matvec(plan.handle, ie.IE_FAR, ie.IE_PREC_CVFCNN, cd, y, nrhs)
+        ie.ie_matvec(plan.handle, ie.IE_FAR, FP32NET, cd, y32, nrhs)
+        got, got32 = host(y), host(y32)
+    for a, b in zip(arrs, back):
+        assert np.array_equal(b, a.astype(np.complex64))
+    ref = oracle.cvfcnn_far_matvec(tiny, c, weights=_as_stored(blocks, arrs), frames=bool(symmetry))
+    assert rel_l2(got32, ref) <= NET_TOL
+    assert rel_l2(got, ref) <= TC_TOL
+    for r in range(nrhs):                        # every column, not only the whole block
+        assert rel_l2(got[r], ref[r]) <= TC_TOL, r
+
+
+@pytest.mark.parametrize("symmetry", [0, 1])
+def test_tensor_core_network_on_a_batch(symmetry):
+    """Batched plan (four scatterers, their own right-hand-side counts): the network kernel
+    splits each member's runs into 80-column items; padding columns stay zero."""
+    b = W.small_batch()
+    R = b.max_rhs
+    members = [W.coefficients(m, R, 990 + g) for g, m in enumerate(b.members)]
+    for g, m in enumerate(b.members):
+        members[g][b.nrhs[g]:] = 0.0
+    pr = ie.problem_from_batch(b, ie.precmask(ie.IE_PREC_CVFCNN), symmetry=symmetry, exact_rhs=True)
+    with ie.Plan(pr) as plan:
+        blocks = ie.ie_plan_blocks(plan.handle)
+        arrs = _random_weights(W.rng(994), len(blocks), 50)
+        ie.ie_cvfcnn_set_weights(plan.handle, *arrs)
+        y = empty((R, b.n))
+        ie.ie_matvec(plan.handle, ie.IE_FAR, ie.IE_PREC_CVFCNN, dev(np.concatenate(members, axis=1)), y, R)
+        outs = b.split(host(y))
+    weights = _as_stored(blocks, arrs)
+    for g, (m, cm) in enumerate(zip(b.members, members)):
+        q = b.nrhs[g]
+        ref = oracle.cvfcnn_far_matvec(m, cm[:q], weights=weights, frames=bool(symmetry))
+        assert rel_l2(outs[g][:q], ref) <= TC_TOL, g
+        assert not np.any(outs[g][q:]), g
+
+
+def test_tensor_core_network_shell16_sampled():
+    """Full-size launch (shell16, symmetric store, 473 networks, 1,575,248 far pairs) on
+    loaded weights; 8 sampled target boxes against the oracle, worst box reported."""
+    p = W.shell16()
+    p.alpha = W.alpha_for("shell16")
+    c = W.coefficients(p, 1, W.SEED_C["shell16"])
+    targets = W.subsample_boxes(p, 8, W.SEED_SUBSAMPLE["shell16"])
+    rows = oracle.basis_rows(p, targets)
+    with _plan(p, [ie.IE_PREC_CVFCNN], symmetry=1) as plan:
+        blocks = ie.ie_plan_blocks(plan.handle)
+        arrs = _random_weights(W.rng(995), len(blocks), 50)
+        ie.ie_cvfcnn_set_weights(plan.handle, *arrs)
+        y = empty((1, p.n))
+        ie.ie_matvec(plan.handle, ie.IE_FAR, ie.IE_PREC_CVFCNN, dev(c), y, 1)
+        got = host(y)[:, rows]
+    ref = oracle.cvfcnn_far_matvec(p, c, weights=_as_stored(blocks, arrs), frames=True, targets=targets)
+    assert rel_l2(got, ref) <= TC_TOL
+    off = np.concatenate([[0], np.cumsum(np.asarray(p.nb)[targets])])
+    worst = max(rel_l2(got[:, off[i]:off[i + 1]], ref[:, off[i]:off[i + 1]]) for i in range(len(targets)))
+    assert worst <= TC_TOL, worst
+
+
+# ------------------------------------------------------------ training (§3, first stage)
+@pytest.fixture(scope="module")
+def trained(tiny):
+    """A tiny symmetric plan whose 16 networks ie_cvfcnn_train trained (default options:
+    the paper's stopping tolerance 1e-3), with the weights read back."""
+    plan = _plan(tiny, [ie.IE_PREC_CVFCNN, FP32NET, ie.IE_PREC_FP16X3], symmetry=1, max_rhs=2)
+    info = ie.ie_cvfcnn_train(plan.handle)
+    weights = ie.ie_cvfcnn_get_weights(plan.handle)
+    yield plan, info, weights
+    plan.close()
+
+
+def test_training_reaches_the_papers_error_level(trained, tiny):
+    """e^u of eq. 171 recomputed by the oracle on its own 64 uniform inputs per network,
+    against the FP64 DGFA block; the ReLU acts and the hidden bias is ordinary."""
+    plan, info, (W1, b1, W2, b2) = trained
+    blocks = ie.ie_plan_blocks(plan.handle)
+    assert info["networks"] == len(blocks) == 16
+    assert info["converged"] >= 14 and info["eu_max"] < 2e-3 and info["steps_max"] <= 8000
+    g = W.rng(996)
+    eus, cut = [], []
+    for i, d in enumerate(blocks):
+        C = oracle.coupling_block(tiny, np.array(d, dtype=np.int32))
+        x = g.uniform(-1, 1, (64, 192)) + 1j * g.uniform(-1, 1, (64, 192))
+        net = tuple(np.asarray(a[i], dtype=np.complex128) for a in (W1, b1, W2, b2))
+        o = oracle.cvfcnn_forward(*net, x)
+        t = x @ C.T
+        eus.append(np.mean(np.linalg.norm(o - t, axis=1) / np.linalg.norm(t, axis=1)))
+        z = (x / np.abs(x).max(axis=1, keepdims=True)) @ net[0].T + net[1]
+        cut.append(np.mean(np.concatenate([z.real.ravel(), z.imag.ravel()]) < 0))
+    assert max(eus) < 2.5e-3 and np.mean(eus) < 1.5e-3, eus
+    assert 0.2 < np.mean(cut) < 0.8, cut
+    # the closed-form fit's hidden bias is sum_u |W1_hu| (1 + j), about 17 in modulus
+    assert np.abs(b1).max() < 2.0
+
+
+def test_training_is_reproducible(trained, tiny):
+    """The inputs come from a counter-based generator: the same seed trains the same
+    weights, another seed others."""
+    _, _, first = trained
+    with _plan(tiny, [ie.IE_PREC_CVFCNN], symmetry=1) as plan:
+        ie.ie_cvfcnn_train(plan.handle)
+        again = ie.ie_cvfcnn_get_weights(plan.handle)
+        ie.ie_cvfcnn_train(plan.handle, ie.cvfcnn_train_opts(seed=7, max_steps=250))
+        other = ie.ie_cvfcnn_get_weights(plan.handle)
+    for a, b in zip(first, again):
+        assert np.array_equal(a, b)
+    assert not np.array_equal(first[0], other[0])
+
+
+def test_trained_far_products(trained, tiny):
+    """Tensor-core and FP32 evaluations of the trained networks against the oracle's
+    network on the read-back weights, and against the exact far product (e^u level)."""
+    plan, _, wts = trained
+    blocks = ie.ie_plan_blocks(plan.handle)
+    c = W.coefficients(tiny, 2, 997)
+    cd = dev(c)
+    y, y32 = empty((2, tiny.n)), empty((2, tiny.n))
+    ie.ie_matvec(plan.handle, ie.IE_FAR, ie.IE_PREC_CVFCNN, cd, y, 2)
+    ie.ie_matvec(plan.handle, ie.IE_FAR, FP32NET, cd, y32, 2)
+    got, got32 = host(y), host(y32)
+    ref_net = oracle.cvfcnn_far_matvec(tiny, c, weights=_as_stored(blocks, wts), frames=True)
+    ref = oracle.far_matvec(tiny, c)
+    assert rel_l2(got32, ref_net) <= NET_TOL
+    assert rel_l2(got, ref_net) <= TC_TOL
+    assert rel_l2(ref_net, ref) <= 4e-3                # the networks' own error (e^u ~ 1e-3)
+    assert rel_l2(got, ref) <= rel_l2(ref_net, ref) + TC_TOL
+
+
+def test_trained_surrogate_solve_with_refinement(trained, tiny):
+    """The paper's use of the networks: GMRES on tensor-core network products to 1e-3,
+    FP64 residuals of FP16X3 products outside, answer to 1e-5 (dense LU reference)."""
+    plan, _, _ = trained
+    Z = oracle.dense_operator(tiny)
+    kh, pol = W.plane_wave_spec(1)
+    v = oracle.plane_wave_rhs(tiny, kh, pol)
+    x = empty((1, tiny.n))
+    opts = ie.solve_opts(tol=1e-5, prec=ie.IE_PREC_CVFCNN, refine=1, refine_prec=ie.IE_PREC_FP16X3, inner_tol=1e-3)
+    st, info = ie.ie_solve(plan.handle, dev(v), x, 1, opts)
+    assert st == ie.IE_OK, info
+    xs = host(x)[0]
+    true_res = np.linalg.norm(v[0] - Z @ xs) / np.linalg.norm(v[0])
+    assert true_res <= 2e-5
+
+
+def test_training_needs_a_surrogate_plan(tiny):
+    with _plan(tiny, [ie.IE_PREC_FP32], symmetry=1) as plan:
+        with pytest.raises(ie.IEError) as e:
+            ie.ie_cvfcnn_train(plan.handle)
+        assert e.value.status == ie.IE_ERR_UNSUPPORTED
+        with pytest.raises(ie.IEError) as e:
+            ie.ie_cvfcnn_get_weights(plan.handle)
+        assert e.value.status == ie.IE_ERR_UNSUPPORTED

@@ -639,3 +639,19 @@ def test_cvfcnn_far_matvec_pair_by_pair():
     want = oracle.disaggregate(p, Y[None])
     got = oracle.cvfcnn_far_matvec(p, c, weights=weights)
     assert np.allclose(got, want, rtol=1e-13, atol=1e-13 * np.abs(want).max())
+
+
+def test_cvfcnn_canonical_frames_reproduce_the_exact_far_product():
+    """Weights keyed by canonical c and applied in the frame of c (frames=True): with
+    full-rank linear networks (H = 192, net_c = G_c on the unit ball) the product is the
+    brute-force far product, which a transposed or mis-signed frame map would break."""
+    boxes = [[0, 0, 0], [2, 0, 0], [0, 3, 1], [3, 1, 3], [0, -2, -3]]
+    p = Tiny(boxes, G=4, L=4, nb=5, seed=964)
+    ds, _ = oracle.pair_groups(p, oracle.FAR)
+    canon = {tuple(sorted(int(v) for v in np.abs(d))) for d in ds}
+    assert len(canon) < len(ds)                    # frames are exercised
+    weights = {cc: oracle.cvfcnn_fit(oracle.coupling_block(p, np.array(cc, dtype=np.int32)), 192) for cc in canon}
+    c = W.complex_normal(W.rng(965), (2, int(p.nb.sum())))
+    got = oracle.cvfcnn_far_matvec(p, c, weights=weights, frames=True)
+    want = oracle.far_matvec(p, c)
+    assert np.linalg.norm(got - want) <= 1e-10 * np.linalg.norm(want)
