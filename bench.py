@@ -57,6 +57,8 @@ def parse():
                     help="shell32 is the headline line (with a bounded serving record); the others measure "
                          "the plain-path shell, batching and serving workloads on their own")
     ap.add_argument("--no-serve", action="store_true", help="shell32: leave out the bounded serving record")
+    ap.add_argument("--no-surrogate", action="store_true",
+                    help="shell32: leave out the translation-network record (shell16, trained networks)")
     ap.add_argument("--lfb", default=None, choices=["lfb8", "lfb256"],
                     help="shell16 only: the same geometry with box edge lambda/8 or lambda/256 "
                          "(low-frequency regime)")
@@ -386,13 +388,6 @@ def run_shell16(ctx):
     plan = ie.Plan(ie.problem_from(p, ie.precmask(*precs), symmetry=args.symmetry), stream)
     plan_s = time.perf_counter() - t0
     st = plan.stats
-    # the translation networks in a plan of their own (their fit is FP64 plan-time work), with
-    # the FP16X3 store for the refinement residuals
-    t0 = time.perf_counter()
-    plan_cv = ie.Plan(ie.problem_from(p, ie.precmask(ie.IE_PREC_FP16X3, ie.IE_PREC_CVFCNN),
-                                      symmetry=args.symmetry), stream)
-    plan_cv_s = time.perf_counter() - t0
-    st_cv = plan_cv.stats
     kh, pol = W.plane_wave_spec(1)
     v = torch.zeros((1, p.n), dtype=torch.complex64, device=ctx.dev)
     ie.ie_rhs_plane_wave(plan.handle, kh, pol, v, stream)
@@ -404,14 +399,12 @@ def run_shell16(ctx):
 
     # ---- timed region: K solves of the headline path (CUDA events on the solve stream)
     head = time_solves(ctx, plan, v, x, 1, paths[HEADLINE]["opts"], args.steps, warm, clocks=True)
-    others = {name: time_solves(ctx, plan_cv if path["opts"].prec == ie.IE_PREC_CVFCNN else plan, v, x, 1,
-                                path["opts"], args.steps, warm)
+    others = {name: time_solves(ctx, plan, v, x, 1, path["opts"], args.steps, warm)
               for name, path in paths.items() if name != HEADLINE}
 
     # ---- far-zone products per precision and the translation kernel's own time
     c = torch.from_numpy(W.coefficients(p, 1, W.SEED_C["shell16"]).astype(np.complex64)).to(ctx.dev)
     far = time_far(ctx, plan, c, 1, precs, max(5, args.steps))
-    far |= time_far(ctx, plan_cv, c, 1, [ie.IE_PREC_CVFCNN], max(5, args.steps))
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     e2e = time_e2e(ctx, plan, v, x, paths[HEADLINE]["opts"], args.steps)
@@ -428,16 +421,6 @@ def run_shell16(ctx):
                      "frac": simt_ach / FP32_SIMT_PEAK_TFLOPS, "kernel": "translate_simt_kernel",
                      "traffic": profiled_traffic("translate_simt_fp32_shell16.md", "translate_simt.cu"),
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
-    # translation networks: 2 x 192 x H complex multiply-adds per pair (H = 50), FP32 SIMT
-    cv_ach = pairs * 8 * 2 * 192 * st_cv["cvfcnn_hidden"] / (far["cvfcnn"]["translate_kernel_ms"] / 1e3) / 1e12
-    roofline_cvfcnn = {"bound": "alu", "achieved": cv_ach, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
-                       "frac": cv_ach / FP32_SIMT_PEAK_TFLOPS, "kernel": "cvfcnn_translate_kernel",
-                       "traffic": profiled_traffic("cvfcnn_translate_fp32_shell16.md",
-                                                           "cvfcnn.cu:struct SmemCv {",
-                                                           "cvfcnn.cu:cvfcnn_translate_kernel(const WorkItem"),
-                       "hidden": st_cv["cvfcnn_hidden"], "svd_tail_max": st_cv["cvfcnn_tail"],
-                       "jacobi_sweeps_max": st_cv["cvfcnn_sweeps"], "plan_seconds": plan_cv_s,
-                       "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
 
     hp = paths[HEADLINE]
     result = {
@@ -463,15 +446,15 @@ def run_shell16(ctx):
         "e2e": e2e,
         "roofline": roofline,
         "roofline_fp32": roofline_fp32,
-        "roofline_cvfcnn": roofline_cvfcnn,
     }
+    plan.close()
+    if not args.no_surrogate and args.lfb is None and not args.mapped:
+        result["surrogate"] = surrogate_record(ctx, args.symmetry)
     if mapping is not None:
         result["mapping"] = mapping
     if ctx.rank == 0 and world == 1:
         result["cpu_baseline"] = cpu_baseline(p, "shell16", oracle_products(p.name, HEADLINE_TOL) or head["matvecs"],
                                               "the oracle's own GMRES(50) to the same tolerance")
-    plan.close()
-    plan_cv.close()
     return result
 
 
@@ -594,7 +577,75 @@ def run_shell32(ctx):
         result["cpu_baseline"] = cpu_baseline(p, "shell32", prods, basis)
     if not args.no_serve:
         result["serve"] = serve_record(ctx)
+    if not args.no_surrogate:
+        result["surrogate"] = surrogate_record(ctx)
     return result
+
+
+def surrogate_record(ctx, symmetry: int = 1) -> dict:
+    """Translation networks of §3 on shell16: trained on the GPU (first stage, e^u < 1e-3),
+    then far products with the networks on the tensor cores and in FP32 beside the FP16X3
+    block product on the same plan, their distance from it, and a refined solve to 1e-5
+    whose inner GMRES runs on the tensor-core networks."""
+    args, ie, W, torch, np = ctx.args, ctx.ie, ctx.W, ctx.torch, ctx.np
+    p = W.shell16()
+    p.alpha = W.alpha_for("shell16")
+    precs = [ie.IE_PREC_FP16X3, ie.IE_PREC_CVFCNN, ie.IE_PREC_CVFCNN_FP32]
+    t0 = time.perf_counter()
+    plan = ie.Plan(ie.problem_from(p, ie.precmask(*precs), symmetry=symmetry), ctx.stream)
+    plan_s = time.perf_counter() - t0
+    st = plan.stats
+    info = ie.ie_cvfcnn_train(plan.handle, None, ctx.stream)
+    c = torch.from_numpy(W.coefficients(p, 1, W.SEED_C["shell16"]).astype(np.complex64)).to(ctx.dev)
+    far = time_far(ctx, plan, c, 1, precs, 10)
+    ys = {}
+    for q in precs:
+        y = torch.zeros_like(c)
+        ie.ie_matvec(plan.handle, ie.IE_FAR, q, c, y, 1, ctx.stream)
+        ys[ie.PREC_NAMES[q]] = y
+    torch.cuda.synchronize()
+    rel = lambda a, b: float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))  # noqa: E731
+    kh, pol = W.plane_wave_spec(1)
+    v = torch.zeros((1, p.n), dtype=torch.complex64, device=ctx.dev)
+    ie.ie_rhs_plane_wave(plan.handle, kh, pol, v, ctx.stream)
+    x = torch.zeros_like(v)
+    opts_net = ie.solve_opts(tol=1e-5, restart=50, prec=ie.IE_PREC_CVFCNN, refine=1, refine_prec=ie.IE_PREC_FP16X3,
+                             inner_tol=1e-3)
+    opts_blk = ie.solve_opts(tol=1e-5, restart=50, prec=ie.IE_PREC_FP16X3)
+    keys = ("solves_per_s", "p50_ms", "iterations", "matvecs", "refinements", "relres")
+    solves = {"cvfcnn_refined": time_solves(ctx, plan, v, x, 1, opts_net, 3, 1),
+              "fp16x3": time_solves(ctx, plan, v, x, 1, opts_blk, 3, 1)}
+    H = st["cvfcnn_hidden"]
+    pairs = st["n_far_pairs"]
+    peaks = measured_peaks()
+    # algorithmic work: 2 x 192 x H complex multiply-adds (8 real flops each) per pair
+    ach = pairs * 8 * 2 * 192 * H / (far["cvfcnn"]["translate_kernel_ms"] / 1e3) / 1e12
+    ach32 = pairs * 8 * 2 * 192 * H / (far["cvfcnn_fp32"]["translate_kernel_ms"] / 1e3) / 1e12
+    out = {
+        "workload": ("shell16 (1,264 boxes, 1,575,248 far pairs), symmetry-compressed store: one network per "
+                     f"canonical displacement ({st['n_coupling_blocks']}), H = {H}"),
+        "plan_seconds": plan_s,
+        "training": {k: info[k] for k in ("networks", "converged", "eu_max", "eu_mean", "steps_max", "seconds")},
+        "far_matvecs": far,
+        "network_vs_block": {"cvfcnn": rel(ys["cvfcnn"], ys["fp16x3"]),
+                             "cvfcnn_fp32": rel(ys["cvfcnn_fp32"], ys["fp16x3"]),
+                             "cvfcnn_vs_cvfcnn_fp32": rel(ys["cvfcnn"], ys["cvfcnn_fp32"])},
+        "kernel_vs_fp16x3_block": far["fp16x3"]["translate_kernel_ms"] / far["cvfcnn"]["translate_kernel_ms"],
+        "solves": {name: {k: r[k] for k in keys} for name, r in solves.items()},
+        "roofline_fp32": {"bound": "alu", "achieved": ach32, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
+                          "frac": ach32 / FP32_SIMT_PEAK_TFLOPS, "kernel": "cvfcnn_translate_kernel",
+                          "traffic": profiled_traffic("cvfcnn_translate_fp32_shell16.md", "cvfcnn.cu:struct SmemCv {",
+                                                      "cvfcnn.cu:cvfcnn_translate_kernel(const WorkItem"),
+                          "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
+        "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16"], "unit": "TFLOP/s",
+                     "frac": ach / peaks["bf16"], "kernel": "cvfcnn_tc_kernel", "traffic": None,
+                     "peak_source": peaks["source"] + " (fp16 runs at the bf16 rate)",
+                     "algorithmic_flops_per_launch": pairs * 8 * 2 * 192 * H},
+    }
+    plan.close()
+    del v, x, c, ys
+    torch.cuda.empty_cache()
+    return out
 
 
 def time_e2e(ctx, plan, v, x, opts, steps):
@@ -707,6 +758,7 @@ def serve_run(ctx, reqs, problems, form, rate, batch, budget, symmetry, foot):
     from paper_2501_04684_gb300 import serve as S
     precs, opts = serve_forms(ie)[form]
     srv = S.Server(precs, opts, budget, workers=ctx.args.serve_workers, batch=batch, symmetry=symmetry)
+    srv.prepare_stores(problems)        # shared coupling-block stores: server state, made before the clock
     gaps = np.diff([0.0] + [q["t_arrival"] for q in reqs])
     todo = [S.Request(rid=i, problem=pr, khat=q["khat"], pol=q["pol"]) for i, (q, pr) in
             enumerate(zip(reqs, problems))]
@@ -731,7 +783,9 @@ def serve_run(ctx, reqs, problems, form, rate, batch, budget, symmetry, foot):
             "errors": sorted({r.error or ie.lib().ie_status_str(r.status).decode() for r in bad})[:3],
             "solves_per_s": len(lat) / wall, "p50_s": pc["p50"], "p99_s": pc["p99"],
             "mean_service_s": float(np.mean([r.t_done - r.t_start for r in done])),
-            "peak_device_bytes": srv.peak_used, "wall_s": wall}
+            "peak_device_bytes": srv.peak_used, "wall_s": wall,
+            "mode": "stepped" if srv.stepped else "blocking", "max_live_solves": srv.max_live,
+            "shared_store_bytes": srv.store_bytes}
 
 
 def serve_record(ctx):
@@ -749,7 +803,9 @@ def serve_record(ctx):
     rate = load * cap["plain"]["solves_per_s"] / max(1e-9, len(reqs) / max(1e-9, reqs[-1]["t_arrival"]))
     loaded = {form: serve_run(ctx, reqs, problems, form, rate, 1, budget, sym, foot) for form in ("mixed", "plain")}
     return {"workload": (f"{len(reqs)} Poisson arrivals (seed 51) of sphere-shell scatterers of 200..20,000 boxes "
-                         f"(log-uniform), nb=32, 1..4 plane waves each, tol 1e-5, symmetry-compressed stores"),
+                         f"(log-uniform), nb=32, 1..4 plane waves each, tol 1e-5; plans attached to one shared "
+                         f"symmetry-compressed coupling store made before the clock; solves stepped one GMRES(50) "
+                         f"cycle at a time on 4 streams"),
             "capacity_solves_per_s": {f: cap[f]["solves_per_s"] for f in cap},
             "load_x_plain_capacity": load,
             "p50_s": {f: loaded[f]["p50_s"] for f in loaded}, "p99_s": {f: loaded[f]["p99_s"] for f in loaded},
@@ -817,11 +873,6 @@ def solve_paths(ie) -> dict:
                              desc="refinement (FP16X3 residual) around GMRES(50) on single fp16 products to 1e-3"),
         "plain": dict(opts=dict(tol=1e-6, restart=50, prec=ie.IE_PREC_FP32), dtype="f32",
                       desc="plain FP32 path: GMRES(50) on FP32 SIMT products to 1e-6"),
-        "cvfcnn_refined": dict(opts=dict(tol=1e-5, restart=50, prec=ie.IE_PREC_CVFCNN, refine=1,
-                                         refine_prec=ie.IE_PREC_FP16X3, inner_tol=1e-3),
-                               dtype="f32 translation networks (H = 50), f32 GMRES, f64 refinement",
-                               desc="refinement (FP16X3 residual) around GMRES(50) on products whose translations "
-                                    "are the closed-form networks of §3, to 1e-3"),
     }
 
 

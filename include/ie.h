@@ -43,6 +43,7 @@ extern "C" {
 #endif
 
 typedef struct ie_plan_s *ie_plan;
+typedef struct ie_store_s *ie_store;
 typedef struct ie_solver_s *ie_solver;
 
 typedef enum {
@@ -177,6 +178,50 @@ ie_status ie_plan_create(const ie_problem *prob, void *stream, ie_plan *out);
 /* Device bytes ie_plan_create would allocate for `prob` (for admission control);
  * host-only, no device work.  Errors: as ie_plan_create's validation. */
 ie_status ie_plan_footprint(const ie_problem *prob, size_t *bytes);
+
+/* ---- shared coupling-block stores ------------------------------------------------
+ *
+ * The translation matrices depend on the box edge, k, eta and the displacement only
+ * (end of §2: one set serves every scatterer discretised with the same boxes), and
+ * with the symmetry of §2.2 on the sorted |d| only.  A store holds the canonical far
+ * blocks G_c of every c = (c0 <= c1 <= c2) with c2 <= max_disp and c2 >= 2, in the
+ * coupling-block precisions of prec_mask (FP32, BF16X3/X1, FP16X3/X1), generated once;
+ * symmetry-compressed plans of any scatterer whose displacements stay within max_disp
+ * then attach to it instead of generating their own (ie_plan_create_shared).
+ * Ownership: the store is reference counted; ie_store_release drops the creator's
+ * reference and every plan attached to it holds one until ie_plan_destroy, so the
+ * blocks live while any plan reads them.  Thread safety: creating and destroying
+ * plans on one store from several host threads is safe.                           */
+typedef struct {
+    double k, eta, box_edge;   /* as in ie_problem                                       */
+    int lattice;               /* 4                                                      */
+    int max_disp;              /* largest |d_i| of a far displacement served, 2..1024    */
+    unsigned prec_mask;        /* coupling-block precisions only (no CVFCNN)            */
+} ie_store_spec;
+
+/* Device bytes ie_store_create would hold (host only).  Errors: IE_ERR_INVALID. */
+ie_status ie_store_footprint(const ie_store_spec *spec, size_t *bytes);
+
+/* Generate the store on `stream` and wait for it.  Errors: IE_ERR_INVALID (spec),
+ * IE_ERR_OOM, IE_ERR_CUDA. */
+ie_status ie_store_create(const ie_store_spec *spec, void *stream, ie_store *out);
+
+/* Canonical blocks held and device bytes (either pointer may be NULL). */
+ie_status ie_store_info(ie_store store, int64_t *n_blocks, size_t *bytes);
+
+/* Drop the caller's reference (the blocks are freed once no plan holds one). */
+ie_status ie_store_release(ie_store store);
+
+/* ie_plan_create for a symmetry-compressed problem (symmetry = 1) whose coupling
+ * blocks come from `store`: same k, eta, box_edge and lattice (compared exactly),
+ * every coupling-block precision of prob->prec_mask held by the store, no CVFCNN,
+ * every far |d_i| <= max_disp.  The plan's n_coupling_blocks is the store's count and
+ * its device_bytes excludes the store.  Errors: IE_ERR_INVALID (mismatch, reach),
+ * IE_ERR_UNSUPPORTED (symmetry 0, CVFCNN), else as ie_plan_create. */
+ie_status ie_plan_create_shared(const ie_problem *prob, ie_store store, void *stream, ie_plan *out);
+
+/* Device bytes ie_plan_create_shared would allocate (host only; the store excluded). */
+ie_status ie_plan_footprint_shared(const ie_problem *prob, ie_store store, size_t *bytes);
 
 ie_status ie_plan_stats_get(ie_plan plan, ie_plan_stats *out);
 
@@ -332,8 +377,17 @@ ie_status ie_solver_start(ie_solver s, const void *v, void *c, void *stream);
 ie_status ie_solver_advance(ie_solver s, int cycles, void *stream);
 
 /* Non-blocking: *done = 1 once everything enqueued on the solver has finished and
- * every right-hand side converged or hit max_iters; then info is filled. */
+ * every right-hand side converged or hit max_iters; then info is filled.  Start and
+ * advance end with an asynchronous copy of the solver's status into pinned host
+ * memory, so polling makes no synchronous device call. */
 ie_status ie_solver_poll(ie_solver s, int *done, ie_solve_info *info);
+
+/* Non-blocking state for request loops: IE_SOLVER_BUSY while enqueued work runs,
+ * IE_SOLVER_IDLE once it has finished with some system still iterating (advance
+ * again), IE_SOLVER_DONE once every system converged or hit max_iters (info filled
+ * in the last two states). */
+enum { IE_SOLVER_BUSY = 0, IE_SOLVER_IDLE = 1, IE_SOLVER_DONE = 2 };
+ie_status ie_solver_state(ie_solver s, int *state, ie_solve_info *info);
 
 ie_status ie_solver_destroy(ie_solver s);
 

@@ -34,7 +34,8 @@ EXPORTED = [
     "ie_plan_profile", "ie_kernel_launches", "ie_translate_noalloc", "ie_plan_check", "ie_diag_bounded_wait",
     "ie_plan_tune", "ie_map_basis", "ie_plan_blocks", "ie_cvfcnn_set_weights", "ie_cvfcnn_get_weights",
     "ie_cvfcnn_train",
-    "ie_cvfcnn_train_opts_default",
+    "ie_cvfcnn_train_opts_default", "ie_store_footprint", "ie_store_create", "ie_store_info", "ie_store_release",
+    "ie_plan_create_shared", "ie_plan_footprint_shared", "ie_solver_state",
 ]
 
 
@@ -43,6 +44,11 @@ def precmask(*precs) -> int:
     for p in precs:
         m |= 1 << p
     return m
+
+
+class ie_store_spec(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_double), ("eta", ctypes.c_double), ("box_edge", ctypes.c_double),
+                ("lattice", ctypes.c_int), ("max_disp", ctypes.c_int), ("prec_mask", ctypes.c_uint)]
 
 
 class ie_problem(ctypes.Structure):
@@ -112,6 +118,12 @@ def lib() -> ctypes.CDLL:
     P = ctypes.POINTER
     L.ie_plan_create.argtypes = [P(ie_problem), vp, P(vp)]
     L.ie_plan_footprint.argtypes = [P(ie_problem), P(sz)]
+    L.ie_store_footprint.argtypes = [P(ie_store_spec), P(sz)]
+    L.ie_store_create.argtypes = [P(ie_store_spec), vp, P(vp)]
+    L.ie_store_info.argtypes = [vp, P(ctypes.c_int64), P(sz)]
+    L.ie_store_release.argtypes = [vp]
+    L.ie_plan_create_shared.argtypes = [P(ie_problem), vp, vp, P(vp)]
+    L.ie_plan_footprint_shared.argtypes = [P(ie_problem), vp, P(sz)]
     L.ie_plan_stats_get.argtypes = [vp, P(ie_plan_stats)]
     L.ie_plan_destroy.argtypes = [vp]
     L.ie_plan_profile.argtypes = [vp, i]
@@ -131,6 +143,7 @@ def lib() -> ctypes.CDLL:
     L.ie_solver_start.argtypes = [vp, vp, vp, vp]
     L.ie_solver_advance.argtypes = [vp, i, vp]
     L.ie_solver_poll.argtypes = [vp, P(i), P(ie_solve_info)]
+    L.ie_solver_state.argtypes = [vp, P(i), P(ie_solve_info)]
     L.ie_solver_destroy.argtypes = [vp]
     L.ie_status_str.argtypes = [i]
     L.ie_status_str.restype = ctypes.c_char_p
@@ -250,6 +263,51 @@ def ie_plan_create(problem: ie_problem, stream=None) -> int:
     h = ctypes.c_void_p()
     _check(lib().ie_plan_create(ctypes.byref(problem), _stream(stream), ctypes.byref(h)), "ie_plan_create")
     return h.value
+
+
+def ie_plan_create_shared(problem: ie_problem, store: int, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().ie_plan_create_shared(ctypes.byref(problem), store, _stream(stream), ctypes.byref(h)),
+           "ie_plan_create_shared")
+    return h.value
+
+
+def ie_plan_footprint_shared(problem: ie_problem, store: int) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().ie_plan_footprint_shared(ctypes.byref(problem), store, ctypes.byref(b)), "ie_plan_footprint_shared")
+    return b.value
+
+
+def store_spec(k: float, eta: float, a: float, max_disp: int, prec_mask: int, lattice: int = 4) -> ie_store_spec:
+    return ie_store_spec(k=k, eta=eta, box_edge=a, lattice=lattice, max_disp=int(max_disp), prec_mask=prec_mask)
+
+
+def ie_store_footprint(spec: ie_store_spec) -> int:
+    b = ctypes.c_size_t()
+    _check(lib().ie_store_footprint(ctypes.byref(spec), ctypes.byref(b)), "ie_store_footprint")
+    return b.value
+
+
+def ie_store_create(spec: ie_store_spec, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().ie_store_create(ctypes.byref(spec), _stream(stream), ctypes.byref(h)), "ie_store_create")
+    return h.value
+
+
+def ie_store_info(store: int) -> dict:
+    n, b = ctypes.c_int64(), ctypes.c_size_t()
+    _check(lib().ie_store_info(store, ctypes.byref(n), ctypes.byref(b)), "ie_store_info")
+    return {"n_blocks": n.value, "bytes": b.value}
+
+
+def ie_store_release(store: int):
+    _check(lib().ie_store_release(store), "ie_store_release")
+
+
+def max_far_disp(box_ijk) -> int:
+    """Largest |d_i| between two boxes of a scatterer: the reach a shared store needs."""
+    ijk = np.asarray(box_ijk).reshape(-1, 3)
+    return int((ijk.max(axis=0) - ijk.min(axis=0)).max()) if len(ijk) else 0
 
 
 def ie_plan_footprint(problem: ie_problem) -> int:
@@ -445,6 +503,17 @@ def ie_solver_poll(solver):
     return bool(done.value), {f: getattr(info, f) for f, _ in info._fields_}
 
 
+IE_SOLVER_BUSY, IE_SOLVER_IDLE, IE_SOLVER_DONE = 0, 1, 2
+
+
+def ie_solver_state(solver):
+    """(state, info): IE_SOLVER_BUSY, IE_SOLVER_IDLE (advance again) or IE_SOLVER_DONE."""
+    state = ctypes.c_int()
+    info = ie_solve_info()
+    _check(lib().ie_solver_state(solver, ctypes.byref(state), ctypes.byref(info)), "ie_solver_state")
+    return state.value, {f: getattr(info, f) for f, _ in info._fields_}
+
+
 def ie_solver_destroy(solver):
     _solver_sizes.pop(solver, None)
     return _check(lib().ie_solver_destroy(solver), "ie_solver_destroy")
@@ -492,12 +561,42 @@ def ie_version() -> str:
     return lib().ie_version().decode()
 
 
-class Plan:
-    """Owning wrapper of an ie_plan handle."""
+class Store:
+    """Owning wrapper of an ie_store handle (a shared coupling-block store)."""
 
-    def __init__(self, problem: ie_problem, stream=None):
+    def __init__(self, spec: ie_store_spec, stream=None):
+        self.spec = spec
+        self.handle = ie_store_create(spec, stream)
+        self.info = ie_store_info(self.handle)
+
+    def close(self):
+        if self.handle:
+            ie_store_release(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """Owning wrapper of an ie_plan handle; with `store` the plan attaches to a shared
+    coupling-block store (ie_plan_create_shared)."""
+
+    def __init__(self, problem: ie_problem, stream=None, store: Store | None = None):
         self.problem = problem
-        self.handle = ie_plan_create(problem, stream)
+        if store is not None:
+            self.handle = ie_plan_create_shared(problem, store.handle, stream)
+        else:
+            self.handle = ie_plan_create(problem, stream)
         self.stats = ie_plan_stats_get(self.handle)
 
     @property

@@ -50,6 +50,11 @@ ie_status prepare_translate_tc();
 ie_status prepare_translate_cvfcnn();
 ie_status prepare_cvfcnn_tc();
 
+std::recursive_mutex &device_mutex() {
+    static std::recursive_mutex mu;
+    return mu;
+}
+
 ie_status prepare_kernels() {
     IE_TRY(prepare_translate_simt());
     IE_TRY(prepare_translate_tc());
@@ -320,7 +325,7 @@ void near_lists(const ie_problem *pr, const BoxGrid &g, const std::vector<int32_
 }
 
 size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, int64_t nnear, int64_t near_elems,
-                  int64_t nblk) {
+                  int64_t nblk, bool shared = false) {
     size_t b = 0;
     auto add = [&](size_t x) { b += (x + 255) / 256 * 256; };
     int64_t nbox = pr->n_boxes;
@@ -342,14 +347,16 @@ size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, i
         if (wants_x32(pr->prec_mask))                        // permuted FP32 inputs
             add((size_t)kSym * pr->max_rhs * nbox * kNU * sizeof(float2));
     }
-    if (pr->prec_mask & IE_PRECMASK(IE_PREC_FP32))
-        add((size_t)nblk * kNU * kNU * sizeof(float2));
-    else   // staging of the 16-bit images, freed before the plan returns
-        add((size_t)std::min<int64_t>(nblk, kCouplingChunk) * kNU * kNU * sizeof(float2));
-    if (wants_bf16(pr->prec_mask)) add((size_t)nblk * kTcDispElems * sizeof(uint16_t));
-    if (wants_fp16(pr->prec_mask)) {
-        add((size_t)nblk * kTcDispElems * sizeof(uint16_t));
-        add(nblk * sizeof(int32_t));
+    if (!shared) {   // the blocks themselves (a shared store holds them instead)
+        if (pr->prec_mask & IE_PRECMASK(IE_PREC_FP32))
+            add((size_t)nblk * kNU * kNU * sizeof(float2));
+        else   // staging of the 16-bit images, freed before the plan returns
+            add((size_t)std::min<int64_t>(nblk, kCouplingChunk) * kNU * kNU * sizeof(float2));
+        if (wants_bf16(pr->prec_mask)) add((size_t)nblk * kTcDispElems * sizeof(uint16_t));
+        if (wants_fp16(pr->prec_mask)) {
+            add((size_t)nblk * kTcDispElems * sizeof(uint16_t));
+            add(nblk * sizeof(int32_t));
+        }
     }
     if (wants_cvfcnn(pr->prec_mask)) {
         add((size_t)nblk * kCvBlockElems * sizeof(float2));
@@ -448,6 +455,27 @@ ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out, int max_cols) 
     *out = &cache[key];
     return IE_OK;
 }
+
+ie_status generate_blocks(double k, double eta, double a, const int32_t *d_disp, int64_t nd, float2 *C32,
+                          uint16_t *bf16, uint16_t *fp16, int32_t *exp16, cudaStream_t st) {
+    if (nd <= 0) return IE_OK;
+    const bool keep32 = C32 != nullptr;
+    const int64_t chunk = keep32 ? nd : std::min<int64_t>(nd, kCouplingChunk);
+    float2 *stage = C32;
+    if (!keep32) IE_CK(cudaMallocAsync(&stage, (size_t)chunk * kNU * kNU * sizeof(float2), st));
+    ie_status cst = IE_OK;
+    for (int64_t d0 = 0; d0 < nd && cst == IE_OK; d0 += chunk) {
+        const int64_t m = std::min(chunk, nd - d0);
+        float2 *blk = keep32 ? C32 + d0 * kNU * kNU : stage;
+        cst = launch_coupling_fp32(k, eta, a, d_disp + 3 * d0, m, blk, false, st);
+        if (cst == IE_OK && bf16) cst = launch_coupling_tc(blk, m, bf16 + d0 * kTcDispElems, nullptr, false, st);
+        if (cst == IE_OK && fp16) cst = launch_coupling_tc(blk, m, fp16 + d0 * kTcDispElems, exp16 + d0, true, st);
+    }
+    if (!keep32) cudaFreeAsync(stage, st);
+    return cst;
+}
+
+bool block_prec_only(unsigned mask) { return !wants_cvfcnn(mask); }
 
 ie_status work_list_for(ie_plan p, int prec, int nrhs, WorkList **out) {
     if (prec == IE_PREC_FP32 || prec == IE_PREC_CVFCNN_FP32) return work_list(p, false, nrhs, out);
@@ -570,18 +598,39 @@ ie_status ie_plan_footprint(const ie_problem *pr, size_t *bytes) {
     return IE_OK;
 }
 
-ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
+}  // extern "C"
+
+// What a shared store requires of a problem (before any far group is looked at).
+static ie_status check_store(const ie_problem *pr, ie_store store) {
+    if (pr->symmetry != 1)
+        return set_error("a shared store serves symmetry-compressed plans (symmetry = 1)"), IE_ERR_UNSUPPORTED;
+    if (wants_cvfcnn(pr->prec_mask))
+        return set_error("the CVFCNN surrogates are fitted per plan: no shared store"), IE_ERR_UNSUPPORTED;
+    if (pr->k != store->k || pr->eta != store->eta || pr->box_edge != store->a)
+        return set_error("the store was built for another k, eta or box edge"), IE_ERR_INVALID;
+    if (pr->prec_mask & ~store->prec_mask)
+        return set_error("precisions 0x%x are not in the store (0x%x)", pr->prec_mask, store->prec_mask),
+               IE_ERR_INVALID;
+    return IE_OK;
+}
+
+static ie_status plan_create(const ie_problem *pr, ie_store store, void *stream, ie_plan *out) {
     ie::NvtxRange nvtx_range("ie_plan_create");
     auto t0 = std::chrono::steady_clock::now();
     if (!out) return set_error("null out"), IE_ERR_INVALID;
     *out = nullptr;
     IE_TRY(validate(pr));
+    if (store) IE_TRY(check_store(pr, store));
     BoxGrid g;
     IE_TRY(build_grid(pr, g));
     IE_TRY(prepare_kernels());
     cudaStream_t st = (cudaStream_t)stream;
 
     ie_plan p = new ie_plan_s();
+    if (store) {
+        store_retain(store);
+        p->store = store;
+    }
     auto fail = [&](ie_status s) {
         ie_plan_destroy(p);
         return s;
@@ -631,13 +680,23 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
         std::map<std::array<int32_t, 3>, int32_t> index;
         gcanon.resize(p->n_far_disp);
         gsigma.resize(p->n_far_disp);
+        const int D = store ? store->max_disp : 0;
         for (int64_t d = 0; d < p->n_far_disp; ++d) {
             int32_t c[3];
             gsigma[d] = canon_of(&fg.disp[3 * d], c);
+            if (store) {        // the store's block of c
+                if (c[2] > D) {
+                    set_error("far displacement |d| = (%d, %d, %d) beyond the store's reach %d", c[0], c[1], c[2], D);
+                    return fail(IE_ERR_INVALID);
+                }
+                gcanon[d] = store->index[((size_t)c[0] * (D + 1) + c[1]) * (D + 1) + c[2]];
+                continue;
+            }
             auto ins = index.emplace(std::array<int32_t, 3>{c[0], c[1], c[2]}, (int32_t)index.size());
             if (ins.second) canon_disp.insert(canon_disp.end(), c, c + 3);
             gcanon[d] = ins.first->second;
         }
+        if (store) canon_disp = store->canon;
     }
     p->n_blocks = p->sym ? (int64_t)canon_disp.size() / 3 : p->n_far_disp;
     std::vector<int32_t> nstart, nsrc;
@@ -715,34 +774,23 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
             p->h_canon_disp = canon_disp;
         }
         const int64_t nd = p->n_blocks;
-        if (wants_bf16(p->prec_mask)) PT(dalloc_t(p, &p->d_Cbf16, (size_t)nd * kTcDispElems));
-        if (wants_fp16(p->prec_mask)) {
-            PT(dalloc_t(p, &p->d_Cfp16, (size_t)nd * kTcDispElems));
-            PT(dalloc_t(p, &p->d_Cexp16, (size_t)nd));
-        }
-        // FP32 blocks: the FP32 store itself, or (FP32 not requested) a bounded
-        // staging buffer from which the 16-bit images are cut chunk by chunk
-        const bool keep32 = (p->prec_mask & IE_PRECMASK(IE_PREC_FP32)) != 0;
-        const int64_t chunk = keep32 ? nd : std::min<int64_t>(nd, kCouplingChunk);
-        float2 *C32 = nullptr;
-        if (keep32) {
-            PT(dalloc_t(p, &p->d_Csimt, (size_t)nd * kNU * kNU));
-            C32 = p->d_Csimt;
+        if (store) {            // the shared store's blocks (the plan does not own them)
+            p->d_Csimt = store->d_Csimt;
+            p->d_Cbf16 = store->d_Cbf16;
+            p->d_Cfp16 = store->d_Cfp16;
+            p->d_Cexp16 = store->d_Cexp16;
         } else {
-            PC(cudaMallocAsync(&C32, (size_t)chunk * kNU * kNU * sizeof(float2), st));
+            if (wants_bf16(p->prec_mask)) PT(dalloc_t(p, &p->d_Cbf16, (size_t)nd * kTcDispElems));
+            if (wants_fp16(p->prec_mask)) {
+                PT(dalloc_t(p, &p->d_Cfp16, (size_t)nd * kTcDispElems));
+                PT(dalloc_t(p, &p->d_Cexp16, (size_t)nd));
+            }
+            // FP32 blocks: the FP32 store itself, or (FP32 not requested) a bounded
+            // staging buffer from which the 16-bit images are cut chunk by chunk
+            if (p->prec_mask & IE_PRECMASK(IE_PREC_FP32)) PT(dalloc_t(p, &p->d_Csimt, (size_t)nd * kNU * kNU));
+            PT(generate_blocks(p->k, p->eta, p->a, gen_disp, nd, p->d_Csimt, p->d_Cbf16, p->d_Cfp16, p->d_Cexp16,
+                               st));
         }
-        ie_status cst = IE_OK;
-        for (int64_t d0 = 0; d0 < nd && cst == IE_OK; d0 += chunk) {
-            const int64_t m = std::min(chunk, nd - d0);
-            float2 *blk = keep32 ? C32 + d0 * kNU * kNU : C32;
-            cst = launch_coupling_simt(p, gen_disp + 3 * d0, m, blk, false, st);
-            if (cst == IE_OK && wants_bf16(p->prec_mask))
-                cst = launch_coupling_tc(blk, m, p->d_Cbf16 + d0 * kTcDispElems, nullptr, false, st);
-            if (cst == IE_OK && wants_fp16(p->prec_mask))
-                cst = launch_coupling_tc(blk, m, p->d_Cfp16 + d0 * kTcDispElems, p->d_Cexp16 + d0, true, st);
-        }
-        if (!keep32) cudaFreeAsync(C32, st);
-        PT(cst);
         if (wants_cvfcnn(p->prec_mask)) {
             const int64_t ncanon = (int64_t)canon_disp.size() / 3;
             if (p->sym) {
@@ -826,6 +874,39 @@ ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
     return IE_OK;
 #undef PT
 #undef PC
+}
+
+extern "C" {
+
+ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
+    std::lock_guard<std::recursive_mutex> lock(device_mutex());
+    return plan_create(pr, nullptr, stream, out);
+}
+
+ie_status ie_plan_create_shared(const ie_problem *pr, ie_store store, void *stream, ie_plan *out) {
+    if (!store) return set_error("null store"), IE_ERR_INVALID;
+    std::lock_guard<std::recursive_mutex> lock(device_mutex());
+    return plan_create(pr, store, stream, out);
+}
+
+ie_status ie_plan_footprint_shared(const ie_problem *pr, ie_store store, size_t *bytes) {
+    if (!store || !bytes) return set_error("null argument"), IE_ERR_INVALID;
+    IE_TRY(validate(pr));
+    IE_TRY(check_store(pr, store));
+    BoxGrid g;
+    IE_TRY(build_grid(pr, g));
+    std::vector<int32_t> nb(pr->n_boxes);
+    int64_t n = 0;
+    for (int b = 0; b < pr->n_boxes; ++b) n += (nb[b] = pr->nb ? pr->nb[b] : kNU);
+    FarGroups fg;
+    int64_t npairs = 0, nd = 0;
+    far_groups(pr, g, false, fg, npairs, nd, nullptr);
+    std::vector<int32_t> st, src;
+    std::vector<int64_t> boff;
+    int64_t elems = 0;
+    near_lists(pr, g, nb, st, src, boff, elems);
+    *bytes = plan_bytes(pr, n, npairs, nd, (int64_t)src.size(), elems, store->n_blocks, true);
+    return IE_OK;
 }
 
 ie_status ie_plan_tune(ie_plan p, int prec, int nrhs, ie_tune_info *info, void *stream) {
@@ -933,11 +1014,13 @@ ie_status ie_plan_profile(ie_plan p, int enable) {
 
 ie_status ie_plan_destroy(ie_plan p) {
     if (!p) return IE_OK;
+    std::lock_guard<std::recursive_mutex> lock(device_mutex());
     cudaDeviceSynchronize();
     destroy_cached_solvers(p);
     for (void *q : p->allocs) cudaFree(q);
     for (auto &e : p->prof_ev)
         if (e) cudaEventDestroy(e);
+    if (p->store) store_release(p->store);
     delete p;
     return IE_OK;
 }

@@ -205,16 +205,20 @@ __global__ void near_blocks_identity_kernel(const float2 *__restrict__ Cnear, co
 
 }  // namespace
 
-ie_status launch_coupling_simt(const ie_plan p, const int32_t *d_disp, int64_t nd, float2 *out, bool row_major,
-                               cudaStream_t st) {
+ie_status launch_coupling_fp32(double k, double eta, double a, const int32_t *d_disp, int64_t nd, float2 *out,
+                               bool row_major, cudaStream_t st) {
     if (nd <= 0) return IE_OK;
     int64_t threads = nd * kSites * kSites;
     int bs = 256;
     int64_t grid = (threads + bs - 1) / bs;
-    coupling_fp32_kernel<<<(unsigned)grid, bs, 0, st>>>(p->k, p->eta, p->a / kLattice, d_disp, nd, out,
-                                                        row_major ? 1 : 0);
+    coupling_fp32_kernel<<<(unsigned)grid, bs, 0, st>>>(k, eta, a / kLattice, d_disp, nd, out, row_major ? 1 : 0);
     IE_CK_LAUNCH();
     return IE_OK;
+}
+
+ie_status launch_coupling_simt(const ie_plan p, const int32_t *d_disp, int64_t nd, float2 *out, bool row_major,
+                               cudaStream_t st) {
+    return launch_coupling_fp32(p->k, p->eta, p->a, d_disp, nd, out, row_major, st);
 }
 
 ie_status launch_coupling_tc(const float2 *Cs, int64_t nd, uint16_t *out, int32_t *exps, bool fp16, cudaStream_t st) {

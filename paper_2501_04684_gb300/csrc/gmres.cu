@@ -53,6 +53,8 @@ struct ie_solver_s {
     cudaEvent_t ev = nullptr;
     int matvecs_per_cycle = 0;
     int cycles_run = 0;
+    int *h_st = nullptr;                 // pinned host mirror of st and relres, copied at the end of
+    double *h_rel = nullptr;             // every start and advance (read by ie_solver_poll / _state)
     std::vector<void *> allocs;
     size_t bytes = 0;
 };
@@ -764,6 +766,39 @@ ie_status read_info(ie_solver s, ie_solve_info *info, int *done) {
     return IE_OK;
 }
 
+// The same from the pinned mirror (valid once the solver's event has completed).
+void read_info_mirror(ie_solver s, ie_solve_info *info, int *done) {
+    const int S = s->S;
+    const int *st = s->h_st;
+    if (done) *done = st[1] == 0;
+    if (!info) return;
+    int it = 0;
+    double rr = 0;
+    bool conv = true;
+    for (int q = 0; q < S; ++q) {
+        it = std::max(it, st[2 + 3 * S + q]);
+        rr = std::max(rr, s->h_rel[q]);
+        if (s->h_rel[q] > s->tol) conv = false;
+    }
+    info->iterations = it;
+    info->relres = rr;
+    info->converged = conv ? 1 : 0;
+    const int64_t body = st[3 + 4 * S];
+    info->matvecs = (int)(s->use_while ? body + s->cycles_run : (int64_t)s->cycles_run * s->matvecs_per_cycle);
+    if (s->use_while && body > s->body_runs_seen) {
+        count_launches((body - s->body_runs_seen) * s->body_kernels);
+        s->body_runs_seen = body;
+    }
+}
+
+// Enqueue the copy of the status into the pinned mirror and record the solver's event.
+ie_status mirror_status(ie_solver s, cudaStream_t st) {
+    IE_CK(cudaMemcpyAsync(s->h_st, s->st, (4 + 4 * s->S) * sizeof(int), cudaMemcpyDeviceToHost, st));
+    IE_CK(cudaMemcpyAsync(s->h_rel, s->relres, s->S * sizeof(double), cudaMemcpyDeviceToHost, st));
+    IE_CK(cudaEventRecord(s->ev, st));
+    return IE_OK;
+}
+
 // Cycles until every system is done (or the cycle cap), synchronising once per cycle.
 ie_status run_cycles(ie_solver s, const ie_solve_opts &o, void *stream, ie_solve_info *inf) {
     cudaStream_t st = (cudaStream_t)stream;
@@ -772,7 +807,7 @@ ie_status run_cycles(ie_solver s, const ie_solve_opts &o, void *stream, ie_solve
     for (int cyc = 0; !done && cyc < max_cycles; ++cyc) {
         IE_TRY(ie_solver_advance(s, 1, stream));
         IE_CK(cudaStreamSynchronize(st));
-        IE_TRY(read_info(s, inf, &done));
+        read_info_mirror(s, inf, &done);     // the advance copied the status to the host
     }
     return read_info(s, inf, &done);
 }
@@ -797,6 +832,7 @@ ie_status ie_solver_footprint(ie_plan p, int nrhs, const ie_solve_opts *opts, si
 
 ie_status ie_solver_create(ie_plan p, int nrhs, const ie_solve_opts *opts, ie_solver *out) {
     if (!p || !out) return set_error("null argument"), IE_ERR_INVALID;
+    std::lock_guard<std::recursive_mutex> lock(device_mutex());
     *out = nullptr;
     ie_solve_opts o;
     fill_defaults(&o);
@@ -869,6 +905,19 @@ ie_status ie_solver_create(ie_plan p, int nrhs, const ie_solve_opts *opts, ie_so
         set_error("stream/event creation failed");
         return fail(IE_ERR_CUDA);
     }
+    {
+        void *h = nullptr;
+        const size_t ib = ((4 + 4 * (size_t)S) * sizeof(int) + 7) / 8 * 8;
+        if (cudaMallocHost(&h, ib + S * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("pinned status mirror allocation failed");
+            return fail(IE_ERR_OOM);
+        }
+        s->h_st = static_cast<int *>(h);
+        s->h_rel = reinterpret_cast<double *>(static_cast<char *>(h) + ib);
+        std::fill(s->h_st, s->h_st + 4 + 4 * S, 0);
+        std::fill(s->h_rel, s->h_rel + S, 0.0);
+    }
     s->matvecs_per_cycle = m + 1;
     *out = s;
     return IE_OK;
@@ -876,11 +925,13 @@ ie_status ie_solver_create(ie_plan p, int nrhs, const ie_solve_opts *opts, ie_so
 
 ie_status ie_solver_destroy(ie_solver s) {
     if (!s) return IE_OK;
+    std::lock_guard<std::recursive_mutex> lock(device_mutex());
     cudaDeviceSynchronize();
     if (s->exec) cudaGraphExecDestroy(s->exec);
     if (s->cap) cudaStreamDestroy(s->cap);
     if (s->ev) cudaEventDestroy(s->ev);
     for (void *q : s->allocs) cudaFree(q);
+    if (s->h_st) cudaFreeHost(s->h_st);
     delete s;
     return IE_OK;
 }
@@ -904,6 +955,7 @@ ie_status ie_solver_start(ie_solver s, const void *v, void *c, void *stream) {
     scale_v0_kernel<<<cg, kDotThreads, 0, st>>>(s->V, s->Vcur, sg, S, m, s->hbuf, s->st);
     count_launches(3);
     IE_CK_LAUNCH();
+    IE_TRY(mirror_status(s, st));
     // the captured cycle reads v and x through fixed pointers: recapture if they moved
     if (s->exec && (s->cap_v != s->v || s->cap_x != s->x)) {
         cudaGraphExecDestroy(s->exec);
@@ -918,6 +970,7 @@ ie_status ie_solver_advance(ie_solver s, int cycles, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     for (int c = 0; c < cycles; ++c) {
         if (!s->exec) {
+            std::lock_guard<std::recursive_mutex> lock(device_mutex());
             // build the cycle graph on the private stream, ordered after `st`
             IE_CK(cudaEventRecord(s->ev, st));
             IE_CK(cudaStreamWaitEvent(s->cap, s->ev, 0));
@@ -934,8 +987,7 @@ ie_status ie_solver_advance(ie_solver s, int cycles, void *stream) {
         count_launches(s->end_kernels);
         s->cycles_run++;
     }
-    IE_CK(cudaEventRecord(s->ev, st));
-    return IE_OK;
+    return mirror_status(s, st);
 }
 
 ie_status ie_solver_poll(ie_solver s, int *done, ie_solve_info *info) {
@@ -946,7 +998,22 @@ ie_status ie_solver_poll(ie_solver s, int *done, ie_solve_info *info) {
         return IE_OK;
     }
     IE_CK(q);
-    return read_info(s, info, done);
+    read_info_mirror(s, info, done);
+    return IE_OK;
+}
+
+ie_status ie_solver_state(ie_solver s, int *state, ie_solve_info *info) {
+    if (!s || !state) return set_error("null argument"), IE_ERR_INVALID;
+    cudaError_t q = cudaEventQuery(s->ev);
+    if (q == cudaErrorNotReady) {
+        *state = IE_SOLVER_BUSY;
+        return IE_OK;
+    }
+    IE_CK(q);
+    int done = 0;
+    read_info_mirror(s, info, &done);
+    *state = done ? IE_SOLVER_DONE : IE_SOLVER_IDLE;
+    return IE_OK;
 }
 
 ie_status ie_solve(ie_plan p, const void *v, void *c, int nrhs, const ie_solve_opts *opts, ie_solve_info *info,

@@ -6,7 +6,9 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -134,6 +136,24 @@ struct WorkList {
 
 }  // namespace ie
 
+// A coupling-block store shared by plans (ie_store_create): the canonical far blocks of
+// every displacement with |d_i| <= max_disp, in the precisions of prec_mask.
+struct ie_store_s {
+    double k = 0, eta = 0, a = 0;
+    int max_disp = 0;
+    unsigned prec_mask = 0;
+    int64_t n_blocks = 0;
+    std::vector<int32_t> canon;        // [n_blocks][3] sorted |d|
+    std::vector<int32_t> index;        // [(max_disp + 1)^3] canonical triple -> block, -1 if near
+    float2 *d_Csimt = nullptr;         // FP32 blocks (IE_PREC_FP32)
+    uint16_t *d_Cbf16 = nullptr, *d_Cfp16 = nullptr;
+    int32_t *d_Cexp16 = nullptr;
+    std::vector<void *> allocs;
+    size_t bytes = 0;
+    double seconds = 0;
+    std::atomic<int> refs{1};
+};
+
 struct ie_plan_s {
     // problem constants
     double k = 0, eta = 0, a = 0, alpha = 0;
@@ -210,6 +230,7 @@ struct ie_plan_s {
     std::map<int, std::pair<int, int>> tc_tuned;      // nrhs -> (tile columns, item order) from ie_plan_tune
     std::vector<void *> allocs;
     size_t bytes = 0;
+    ie_store store = nullptr;          // shared coupling-block store the plan reads (not owned)
     double plan_seconds = 0;
     int64_t n_work_simt = 0, n_work_tc = 0;
     int tc_sms = 0;
@@ -279,6 +300,20 @@ ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out, int max_cols =
 // The work list the translation of precision `prec` launches with (the same cache entry):
 // made ahead of a stream capture, since building one allocates.
 ie_status work_list_for(ie_plan p, int prec, int nrhs, WorkList **out);
+ie_status launch_coupling_fp32(double k, double eta, double a, const int32_t *d_disp, int64_t nd, float2 *out,
+                               bool row_major, cudaStream_t st);
+// FP32 blocks of nd displacements (kept in C32 when given, else cut chunk by chunk from a
+// staging buffer) and their 16-bit images where the buffers are given
+ie_status generate_blocks(double k, double eta, double a, const int32_t *d_disp, int64_t nd, float2 *C32,
+                          uint16_t *bf16, uint16_t *fp16, int32_t *exp16, cudaStream_t st);
+bool block_prec_only(unsigned mask);
+// Process-wide lock around graph capture and instantiation, and around the calls that
+// allocate, free or synchronise the whole device (plan, solver and store creation and
+// destruction): host threads that serve different plans then never capture a graph while
+// another one frees memory or synchronises the device.  Recursive (destruction nests).
+std::recursive_mutex &device_mutex();
+void store_retain(ie_store s);
+void store_release(ie_store s);
 int cvfcnn_tc_tile_columns();
 void destroy_cached_solvers(ie_plan p);
 // launch the translation kernel of `prec` (with the profiling brackets when enabled)
