@@ -411,7 +411,7 @@ def run_shell16(ctx):
 
     # ---- roofline of the dominant kernel of the headline path
     pairs = st["n_far_pairs"]
-    roofline = tc_roofline(pairs, far["fp16x3"]["translate_kernel_ms"], 3, "translate_tc_fp16x3_shell16.md",
+    roofline = tc_roofline(pairs, far["fp16x3"]["translate_kernel_ms"], 3, None if args.symmetry else "translate_tc_fp16x3_shell16.md",
                            "translate_tc_kernel<fp16,x3>")
     if args.lfb is not None and roofline.get("traffic") is not None:
         roofline["traffic_note"] = ("captured at a=lambda/4: the box edge changes only the values, not the "
@@ -419,7 +419,7 @@ def run_shell16(ctx):
     simt_ach = pairs * 8 * 192 * 192 / (far["fp32"]["translate_kernel_ms"] / 1e3) / 1e12
     roofline_fp32 = {"bound": "alu", "achieved": simt_ach, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": simt_ach / FP32_SIMT_PEAK_TFLOPS, "kernel": "translate_simt_kernel",
-                     "traffic": profiled_traffic("translate_simt_fp32_shell16.md", "translate_simt.cu"),
+                     "traffic": None,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
 
     hp = paths[HEADLINE]
@@ -544,12 +544,14 @@ def run_shell32(ctx):
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     e2e = time_e2e(ctx, plan, v, x, paths[HEAD32]["opts"], args.steps)
     pairs = st["n_far_pairs"]
-    roofline = tc_roofline(pairs, far["fp16x3"]["translate_kernel_ms"], 3, "translate_tc_fp16x3_shell32.md",
+    roofline = tc_roofline(pairs, far["fp16x3"]["translate_kernel_ms"], 3, None if args.symmetry else "translate_tc_fp16x3_shell32.md",
                            "translate_tc_kernel<fp16,x3>")
     simt_ach = pairs * 8 * 192 * 192 / (far["fp32"]["translate_kernel_ms"] / 1e3) / 1e12
     roofline_fp32 = {"bound": "alu", "achieved": simt_ach, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": simt_ach / FP32_SIMT_PEAK_TFLOPS, "kernel": "translate_simt_kernel",
-                     "traffic": None, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+                     "traffic": (profiled_traffic("translate_simt_fp32_shell32.md", "translate_simt.cu")
+                                 if not args.symmetry else None),
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
     keys = ("solves_per_s", "p50_ms", "p99_ms", "iterations", "matvecs", "refinements", "relres")
     result = {
         "metric": METRIC, "value": head["solves_per_s"], "unit": "solves/s", "n_gpus": world,
@@ -634,11 +636,11 @@ def surrogate_record(ctx, symmetry: int = 1) -> dict:
         "solves": {name: {k: r[k] for k in keys} for name, r in solves.items()},
         "roofline_fp32": {"bound": "alu", "achieved": ach32, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
                           "frac": ach32 / FP32_SIMT_PEAK_TFLOPS, "kernel": "cvfcnn_translate_kernel",
-                          "traffic": profiled_traffic("cvfcnn_translate_fp32_shell16.md", "cvfcnn.cu:struct SmemCv {",
-                                                      "cvfcnn.cu:cvfcnn_translate_kernel(const WorkItem"),
+                          "traffic": None,
                           "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"},
         "roofline": {"bound": "tensor", "achieved": ach, "peak": peaks["bf16"], "unit": "TFLOP/s",
-                     "frac": ach / peaks["bf16"], "kernel": "cvfcnn_tc_kernel", "traffic": None,
+                     "frac": ach / peaks["bf16"], "kernel": "cvfcnn_tc_kernel",
+                     "traffic": None if symmetry else profiled_traffic("cvfcnn_tc_shell16.md", "cvfcnn_tc.cu"),
                      "peak_source": peaks["source"] + " (fp16 runs at the bf16 rate)",
                      "algorithmic_flops_per_launch": pairs * 8 * 2 * 192 * H},
     }

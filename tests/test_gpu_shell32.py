@@ -1,17 +1,24 @@
 """Full-size shell32 (32^3 grid, radius-14 sphere shell: 5,000 boxes, 160,000 basis
 unknowns, 24.9 M far pairs in 112,160 displacement groups): every product form on a
 seeded 64-box target subsample against the FP64 oracle, and the mixed solve's true
-residual on the same subsample (the FP64 refinement reports the full residual)."""
+residual on the same subsample (the FP64 refinement reports the full residual).
+
+Per-box errors: beside the vector-wide relative error, every sampled box's own relative
+error must stay within PER_BOX x the precision's bound.  The bounds hold per product
+term, so a box's error exceeds the vector's only by how much its field cancels (the
+ratio of sum |G||x| to |sum G x| over its sources), a few units on these shells; a fault
+in one displacement class or box gives O(1) errors there."""
 import numpy as np
 import pytest
 
 import oracle
 import paper_2501_04684_gb300 as ie
 import workloads as W
-from gpu_util import dev, empty, host, rel_l2
+from gpu_util import box_errors, dev, empty, host, rel_l2
 
 pytestmark = pytest.mark.gpu
 BOUND = {ie.IE_PREC_FP32: 1e-6, ie.IE_PREC_BF16X3: 5e-5, ie.IE_PREC_FP16X3: 2e-6, ie.IE_PREC_FP16X1: 2e-3}
+PER_BOX = 10
 
 
 @pytest.fixture(scope="module")
@@ -46,8 +53,10 @@ def test_shell32_far_products_sampled(p, targets, plan):
     for prec, bound in BOUND.items():
         y = empty((1, p.n))
         ie.ie_matvec(plan.handle, ie.IE_FAR, prec, cd, y, 1)
-        err = rel_l2(host(y)[:, rows], ref)
-        assert err <= bound, (ie.PREC_NAMES[prec], err)
+        got = host(y)[:, rows]
+        err = rel_l2(got, ref)
+        worst = box_errors(got, ref, np.asarray(p.nb)[targets]).max()
+        assert err <= bound and worst <= PER_BOX * bound, (ie.PREC_NAMES[prec], err, worst)
 
 
 SOLVES = {

@@ -5,8 +5,8 @@ import os
 import re
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-KERNEL_SUMMARIES = ("translate_tc_fp16x3_shell16.md", "translate_simt_fp32_shell16.md",
-                    "cvfcnn_translate_fp32_shell16.md")
+KERNEL_SUMMARIES = ("translate_tc_fp16x3_shell16.md", "translate_tc_fp16x3_shell32.md",
+                    "translate_simt_fp32_shell32.md", "cvfcnn_tc_shell16.md")
 
 
 def test_profiles_are_short_text_with_their_commands():
