@@ -20,6 +20,10 @@ namespace ie {
 constexpr int kTileN = 64;
 constexpr int kKC = 16;
 constexpr int kThreads = 256;
+constexpr int kAVec = kKC * kNU / 2 / kThreads;   // 16-byte copies of A per thread and chunk
+constexpr int kBPer = kKC * kTileN / kThreads;    // consecutive k of one B column per thread and chunk
+static_assert(kKC * kNU % (2 * kThreads) == 0 && kKC * kTileN % kThreads == 0 && kThreads % kTileN == 0,
+              "loader shapes");
 
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
     uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
@@ -66,23 +70,23 @@ __device__ __forceinline__ void simt_tile(const WorkItem it, const float2 *__res
     const float2 *Cd = C + (int64_t)(sy.gcanon ? sy.gcanon[it.disp] : it.disp) * kNU * kNU;
     if (sy.gcanon) X += (size_t)sigma * sy.stride;
 
-    // B loader: thread -> (column, 4 consecutive k)
-    const int lcol = tid & (kTileN - 1);
-    const int lkq = tid >> 6;                    // 0..3
+    // B loader: thread -> (column, kBPer consecutive k)
+    const int lcol = tid % kTileN;
+    const int lkq = tid / kTileN;
     int lc = lcol < ncols ? lcol : 0;
     const int lpair = it.pair0 + lc / it.nr;
     const int lr = lc % it.nr;
     const float2 *xcol = X + ((int64_t)lr * nbox + src[lpair]) * kNU;
 
     auto load_chunk = [&](int kc, int buf) {
-        // A: 16 x 192 float2 = 1536 x 16 B, 6 per thread
+        // A: kKC x 192 float2 in 16-byte copies, kAVec per thread
         const float4 *ga = reinterpret_cast<const float4 *>(Cd + (int64_t)kc * kKC * kNU);
         float4 *sa = reinterpret_cast<float4 *>(&S.A[buf][0][0]);
 #pragma unroll
-        for (int t = 0; t < 6; ++t) cp_async16(sa + tid + t * kThreads, ga + tid + t * kThreads);
+        for (int t = 0; t < kAVec; ++t) cp_async16(sa + tid + t * kThreads, ga + tid + t * kThreads);
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-            int kk = lkq * 4 + t;
+        for (int t = 0; t < kBPer; ++t) {
+            int kk = lkq * kBPer + t;
             cp_async8(&S.B[buf][kk][lcol], xcol + kc * kKC + kk);
         }
         cp_commit();
