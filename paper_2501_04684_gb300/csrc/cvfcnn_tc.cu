@@ -71,6 +71,7 @@ static_assert(kBPlane % 512 == 0, "operand planes hold whole 8-row groups");
 static_assert(kGath >= kCvTileCols, "one gatherer thread per column of an item");
 static_assert(kSmemBytes <= 227 * 1024, "shared memory");
 static_assert(kCvHp == 64, "two K-chunks of hidden units");
+static_assert(kMidWarps % 4 == 0 && kOutWarps % 4 == 0, "whole TMEM lane quarters per role");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
@@ -98,7 +99,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
         if (clock64() - t0 > kWaitCycles) break;
-        if (SLEEP && i > 32) __nanosleep(64);
+        if (SLEEP) __nanosleep(64);   // a waiting warp leaves the issue slots to the working ones
     }
     *abort_flag = 1;
     return false;
@@ -621,7 +622,7 @@ __global__ void __launch_bounds__(kThreads, 1) cvfcnn_tc_kernel(const CvArgs a) 
                     sgn = (e & 0x100) ? -1.f : 1.f;
                 }
                 float *Yrow = Yslab + row_f;
-                for (int c0 = 32 * half; c0 < 2 * ncols; c0 += 64) {
+                for (int c0 = 32 * half; c0 < 2 * ncols; c0 += 32 * (kOutWarps / 4)) {
                     uint32_t r[32];
                     tmem_ld32(tbase + (uint32_t)c0, r);
                     tmem_wait_ld();
