@@ -258,6 +258,14 @@ ie_status ie_plan_check(ie_plan plan, void *stream);
  * it, as designed; any other status means the bound does not work. */
 ie_status ie_diag_bounded_wait(double limit_ms, void *stream);
 
+/* Diagnostics of the abort path: sets, process-wide, the give-up limit (SM clock cycles) of
+ * the tensor-core translation's pipeline waits for later launches (0 restores the default
+ * 2^31, about 1 s).  With a limit far below a wait's normal duration a launch gives up: its
+ * roles leave uniformly, the drains (which keep the default limit) wait for the copies and
+ * MMAs in flight, TMEM is freed, the plan's error word is set (ie_plan_check then returns
+ * IE_ERR_TIMEOUT) and the product is incomplete.  Synchronous.  For tests only. */
+ie_status ie_diag_wait_limit(int64_t cycles);
+
 /* Release every device allocation of the plan (synchronises the device first). */
 ie_status ie_plan_destroy(ie_plan plan);
 

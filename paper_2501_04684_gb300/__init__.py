@@ -35,7 +35,7 @@ EXPORTED = [
     "ie_plan_tune", "ie_map_basis", "ie_plan_blocks", "ie_cvfcnn_set_weights", "ie_cvfcnn_get_weights",
     "ie_cvfcnn_train",
     "ie_cvfcnn_train_opts_default", "ie_store_footprint", "ie_store_create", "ie_store_info", "ie_store_release",
-    "ie_plan_create_shared", "ie_plan_footprint_shared", "ie_solver_state",
+    "ie_plan_create_shared", "ie_plan_footprint_shared", "ie_solver_state", "ie_diag_wait_limit",
 ]
 
 
@@ -144,6 +144,7 @@ def lib() -> ctypes.CDLL:
     L.ie_solver_advance.argtypes = [vp, i, vp]
     L.ie_solver_poll.argtypes = [vp, P(i), P(ie_solve_info)]
     L.ie_solver_state.argtypes = [vp, P(i), P(ie_solve_info)]
+    L.ie_diag_wait_limit.argtypes = [ctypes.c_int64]
     L.ie_solver_destroy.argtypes = [vp]
     L.ie_status_str.argtypes = [i]
     L.ie_status_str.restype = ctypes.c_char_p
@@ -501,6 +502,11 @@ def ie_solver_poll(solver):
     info = ie_solve_info()
     _check(lib().ie_solver_poll(solver, ctypes.byref(done), ctypes.byref(info)), "ie_solver_poll")
     return bool(done.value), {f: getattr(info, f) for f, _ in info._fields_}
+
+
+def ie_diag_wait_limit(cycles: int):
+    """Give-up limit of the tensor-core translation's pipeline waits (0 = default); tests only."""
+    _check(lib().ie_diag_wait_limit(int(cycles)), "ie_diag_wait_limit")
 
 
 IE_SOLVER_BUSY, IE_SOLVER_IDLE, IE_SOLVER_DONE = 0, 1, 2

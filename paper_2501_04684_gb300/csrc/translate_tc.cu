@@ -55,7 +55,9 @@ namespace {
 constexpr int kTcTileCols = 96;                  // complex columns per work item (N <= 192)
 constexpr int kN = 2 * kTcTileCols;              // real B rows of a full item
 constexpr int kAStages = 4;
-constexpr int kAcc = 2;                          // TMEM accumulators (256-column slots)
+constexpr int kAcc = 2;                          // TMEM accumulators
+constexpr uint32_t kAccCols = 256;               // TMEM columns of one accumulator slot (>= kN)
+constexpr int kCtasPerSm = 1;                    // resident CTAs per SM (shared memory, TMEM, registers)
 constexpr int kGathWarps = 4;
 constexpr int kGath = 32 * kGathWarps;
 constexpr int kEpiWarps = 8;
@@ -72,10 +74,15 @@ constexpr int kEpiBytes = kRing * kTcTileCols * 8 + kRing * 16; // column offset
 constexpr int kColBytes = 2 * kTcTileCols * 8;                  // gather base of each column, 2 items
 constexpr int kSmemBytes = kAStages * kAStageBytes + kBBytes + kEpiBytes + kColBytes + 512 /*barriers*/ +
                            1024 /*alignment*/;
-constexpr uint32_t kTmemCols = 512;
+constexpr uint32_t kTmemCols = kAcc * kAccCols;
 constexpr long long kWaitCycles = 1ll << 31;     // bounded waits give up after ~1 s of SM clock
+// diagnostics (ie_diag_wait_limit): a shorter give-up limit for the pipeline's waits, so that
+// a test can drive a real launch through its abort path; the drains keep kWaitCycles
+__device__ long long g_wait_limit = 0;
 static_assert(kAStages * kAStageBytes % 1024 == 0 && kBChunkBytes % 1024 == 0, "operand tiles 1 KB aligned");
-static_assert(kSmemBytes <= 227 * 1024, "shared memory");
+static_assert(kSmemBytes <= 227 * 1024 && kCtasPerSm * (kSmemBytes + 1024) <= 228 * 1024, "shared memory");
+static_assert(kN <= (int)kAccCols && kCtasPerSm * kTmemCols <= 512, "tensor memory");
+static_assert(kEpiWarps % 4 == 0, "whole TMEM lane quarters per epilogue warp group");
 static_assert(kGath >= kTcTileCols, "one gatherer thread per column of an item");
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -116,9 +123,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     return false;
 }
 // Whole warp: lane 0 waits, the outcome is broadcast.
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          long long limit = kWaitCycles) {
     int ok = 0;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag) ? 1 : 0;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag, limit) ? 1 : 0;
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 __device__ __forceinline__ void named_sync_gatherers() { asm volatile("bar.sync 1, %0;" ::"n"(kGath) : "memory"); }
@@ -231,7 +239,7 @@ struct TcArgs {
 };
 
 template <bool FP16, bool X3>
-__global__ void __launch_bounds__(kThreadsTc, 1)
+__global__ void __launch_bounds__(kThreadsTc, kCtasPerSm)
 translate_tc_kernel(const TcArgs a) {
     if (a.gate && *a.gate == 0) return;
     extern __shared__ unsigned char smem_raw[];
@@ -255,6 +263,7 @@ translate_tc_kernel(const TcArgs a) {
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long lim = g_wait_limit > 0 ? g_wait_limit : kWaitCycles;   // give-up limit of the pipeline's waits
     if (threadIdx.x == 0) {
         for (int s = 0; s < kAStages; ++s) {
             mbar_init(smem_u32(&afull[s]), 1);              // the A producer's expect_tx arrive
@@ -307,7 +316,7 @@ translate_tc_kernel(const TcArgs a) {
                 for (int q = 0; q < 3 * kTcKChunks; ++q, ++g) {      // q = mb * 6 + kc
                     const int s = (int)(g % kAStages);
                     const uint32_t ph = (uint32_t)((g / kAStages) & 1);
-                    if (!mbar_wait(smem_u32(&aempty[s]), ph ^ 1, abort_flag)) {
+                    if (!mbar_wait(smem_u32(&aempty[s]), ph ^ 1, abort_flag, lim)) {
                         ok = false;
                         break;
                     }
@@ -349,16 +358,16 @@ translate_tc_kernel(const TcArgs a) {
                 for (int mb = 0; mb < 3 && ok; ++mb) {
                     const int64_t qa = il * 3 + mb;          // accumulator use
                     const int buf = (int)(qa % kAcc);
-                    if (!mbar_wait<false>(smem_u32(&accempty[buf]), (uint32_t)(((qa / kAcc) & 1) ^ 1), abort_flag)) {
+                    if (!mbar_wait<false>(smem_u32(&accempty[buf]), (uint32_t)(((qa / kAcc) & 1) ^ 1), abort_flag, lim)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t dt = tmem_base + (uint32_t)(buf * 256);
+                    const uint32_t dt = tmem_base + (uint32_t)buf * kAccCols;
                     for (int kc = 0; kc < kTcKChunks; ++kc, ++g) {
                         const int s = (int)(g % kAStages);
-                        if (!mbar_wait<false>(smem_u32(&afull[s]), (uint32_t)((g / kAStages) & 1), abort_flag) ||
-                            (mb == 0 && !mbar_wait<false>(smem_u32(&bfull[kc]), bph, abort_flag))) {
+                        if (!mbar_wait<false>(smem_u32(&afull[s]), (uint32_t)((g / kAStages) & 1), abort_flag, lim) ||
+                            (mb == 0 && !mbar_wait<false>(smem_u32(&bfull[kc]), bph, abort_flag, lim))) {
                             ok = false;
                             break;
                         }
@@ -407,7 +416,7 @@ translate_tc_kernel(const TcArgs a) {
             bool ok = true;
             for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
                 for (int kc = 0; kc < kTcKChunks; ++kc) {
-                    if (!mbar_wait<false>(smem_u32(&blanded[kc]), (uint32_t)(il & 1), abort_flag)) {
+                    if (!mbar_wait<false>(smem_u32(&blanded[kc]), (uint32_t)(il & 1), abort_flag, lim)) {
                         ok = false;
                         break;
                     }
@@ -504,7 +513,7 @@ translate_tc_kernel(const TcArgs a) {
             for (int kc = 0; kc < kTcKChunks && ok; ++kc) {
                 if (kc == 2) meta_scales(m_nxt);
                 // the previous item's last M-block has finished with this chunk
-                if (!warp_wait(smem_u32(&bfree[kc]), (uint32_t)((il & 1) ^ 1), abort_flag)) {
+                if (!warp_wait(smem_u32(&bfree[kc]), (uint32_t)((il & 1) ^ 1), abort_flag, lim)) {
                     ok = false;
                     break;
                 }
@@ -534,7 +543,7 @@ translate_tc_kernel(const TcArgs a) {
         bool ok = true;
         for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
             const int rb = (int)(il % kRing);
-            if (!warp_wait(smem_u32(&staged[rb]), (uint32_t)((il / kRing) & 1), abort_flag)) break;
+            if (!warp_wait(smem_u32(&staged[rb]), (uint32_t)((il / kRing) & 1), abort_flag, lim)) break;
             const int4 hd = ep_head[rb];
             const int ncols = hd.x, disp = hd.y, sig = hd.z;
             const int32_t *offs = ep_off + rb * kTcTileCols;
@@ -543,7 +552,7 @@ translate_tc_kernel(const TcArgs a) {
             for (int mb = 0; mb < 3; ++mb) {
                 const int64_t qa = il * 3 + mb;
                 const int buf = (int)(qa % kAcc);
-                if (!warp_wait(smem_u32(&accfull[buf]), (uint32_t)((qa / kAcc) & 1), abort_flag)) {
+                if (!warp_wait(smem_u32(&accfull[buf]), (uint32_t)((qa / kAcc) & 1), abort_flag, lim)) {
                     ok = false;
                     break;
                 }
@@ -558,12 +567,12 @@ translate_tc_kernel(const TcArgs a) {
                     sgn = (e & 0x100) ? -1.f : 1.f;
                 }
                 float *Yrow = Yslab + row_f;
-                const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 256);
+                const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * kAccCols;
                 // 32 TMEM columns = 16 complex columns per load.  Lanes 2m', 2m'+1 hold the Re G
                 // and Im G rows of complex row m'; per pair of columns (k, k+1) they exchange
                 // two values, then the even lane owns the complex result of column k and the
                 // odd lane that of column k+1.
-                for (int c0 = 32 * half; c0 < 2 * ncols; c0 += 64) {
+                for (int c0 = 32 * half; c0 < 2 * ncols; c0 += 32 * (kEpiWarps / 4)) {
                     uint32_t r[32];
                     tmem_ld32(tbase + (uint32_t)c0, r);
                     tmem_wait_ld();
@@ -678,7 +687,7 @@ ie_status launch_translate_tc(ie_plan p, int prec, float2 *Yslab, int nrhs, cuda
     a.gsigma = p->sym ? p->d_gsigma : nullptr;
     a.symmap = p->sym ? p->d_symmap : nullptr;
     a.sig_stride = 2 * a.plane;
-    int grid = (int)std::min<int64_t>(wl->n, p->tc_sms > 0 ? p->tc_sms : 148);
+    int grid = (int)std::min<int64_t>(wl->n, (int64_t)kCtasPerSm * (p->tc_sms > 0 ? p->tc_sms : 148));
     if (prec == IE_PREC_BF16X3)
         translate_tc_kernel<false, true><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
     else if (prec == IE_PREC_FP16X3)
@@ -694,3 +703,10 @@ ie_status launch_translate_tc(ie_plan p, int prec, float2 *Yslab, int nrhs, cuda
 }
 
 }  // namespace ie
+
+extern "C" ie_status ie_diag_wait_limit(int64_t cycles) {
+    if (cycles < 0) return ie::set_error("negative wait limit"), IE_ERR_INVALID;
+    const long long v = (long long)cycles;
+    IE_CK(cudaMemcpyToSymbol(ie::g_wait_limit, &v, sizeof(v)));
+    return IE_OK;
+}

@@ -122,6 +122,7 @@ def test_diagnostic_and_tuner_argument_checks(built):
     L = ie.lib()
     assert L.ie_diag_bounded_wait(0.0, None) == ie.IE_ERR_INVALID
     assert L.ie_diag_bounded_wait(1e6, None) == ie.IE_ERR_INVALID
+    assert L.ie_diag_wait_limit(-1) == ie.IE_ERR_INVALID
     info = ie.ie_tune_info()
     assert L.ie_plan_tune(None, ie.IE_PREC_FP16X3, 1, ctypes.byref(info), None) == ie.IE_ERR_INVALID
     assert L.ie_plan_check(None, None) == ie.IE_ERR_INVALID

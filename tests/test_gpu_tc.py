@@ -221,3 +221,25 @@ def test_autotuner_choice_is_valid_and_products_stay_correct():
             assert rel_l2(host(y), ref) <= BOUND[prec], _name(prec)
         with pytest.raises(ie.IEError):
             ie.ie_plan_tune(plan.handle, ie.IE_PREC_FP32, 1)
+
+
+def test_translation_abort_path_reports_timeout_and_recovers(tiny):
+    """A real tensor-core launch driven through its abort path: with the pipeline's waits
+    limited to 64 SM cycles the roles give up at once; the drains (default limit) still
+    wait for the copies and MMAs in flight, TMEM is freed, the plan reports IE_ERR_TIMEOUT,
+    and with the default limit back the next product on the same plan is correct."""
+    c = W.coefficients(tiny, 1, 211)
+    ref = oracle.far_matvec(tiny, c)
+    with plan_for(tiny, precs=[ie.IE_PREC_FP16X3]) as plan:
+        y = empty((1, tiny.n))
+        try:
+            ie.ie_diag_wait_limit(64)
+            ie.ie_matvec(plan.handle, ie.IE_FAR, ie.IE_PREC_FP16X3, dev(c), y, 1)
+            with pytest.raises(ie.IEError) as e:
+                ie.ie_plan_check(plan.handle)
+            assert e.value.status == ie.IE_ERR_TIMEOUT
+        finally:
+            ie.ie_diag_wait_limit(0)
+        ie.ie_matvec(plan.handle, ie.IE_FAR, ie.IE_PREC_FP16X3, dev(c), y, 1)
+        assert ie.ie_plan_check(plan.handle) == ie.IE_OK
+        assert rel_l2(host(y), ref) <= BOUND[ie.IE_PREC_FP16X3]
