@@ -164,3 +164,24 @@ def test_map_basis_of_no_functions_is_a_no_op(built):
     P, res = ie.ie_map_basis(W.K0, W.ETA0, W.BOX_EDGE, np.zeros(1, dtype=np.int64), np.zeros((0, 3)),
                              np.zeros((0, 3), dtype=np.complex128), stream=0)
     assert P.shape == (0, 192) and res.shape == (0,)
+
+
+def test_store_footprint_host_only(built):
+    """ie_store_footprint (no device work): every canonical far triple up to the reach, in the
+    requested coupling-block precisions; invalid specs are refused."""
+    p = W.tiny()
+    D = 15
+    nblk = (D + 1) * (D + 2) * (D + 3) // 6 - 4
+    b16 = ie.ie_store_footprint(ie.store_spec(p.k, p.eta, p.a, D, ie.precmask(ie.IE_PREC_FP16X3)))
+    b32 = ie.ie_store_footprint(ie.store_spec(p.k, p.eta, p.a, D, ie.precmask(ie.IE_PREC_FP32, ie.IE_PREC_FP16X3)))
+    # 16-bit hi + lo images 294,912 B per block (plus a staging buffer when FP32 is not kept),
+    # FP32 blocks 294,912 B more
+    assert b16 >= nblk * 294912 and b32 >= nblk * (294912 + 192 * 192 * 8)
+    for bad in (dict(max_disp=1), dict(max_disp=2000), dict(prec_mask=ie.precmask(ie.IE_PREC_CVFCNN)),
+                dict(prec_mask=0), dict(lattice=3)):
+        kw = dict(k=p.k, eta=p.eta, a=p.a, max_disp=D, prec_mask=ie.precmask(ie.IE_PREC_FP32)) | bad
+        lattice = kw.pop("lattice", 4)
+        with pytest.raises(ie.IEError) as e:
+            ie.ie_store_footprint(ie.store_spec(kw["k"], kw["eta"], kw["a"], kw["max_disp"], kw["prec_mask"],
+                                                lattice=lattice))
+        assert e.value.status == ie.IE_ERR_INVALID
