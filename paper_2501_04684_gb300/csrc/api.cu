@@ -342,6 +342,7 @@ size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, i
     if (!sym) nblk = nd;
     if (sym) {
         add(nd * 2 * sizeof(int32_t));                       // block and Q of each group
+        add(npairs * sizeof(int32_t));                       // group of each pair
         add((size_t)kSym * kNU * sizeof(uint16_t));
         add(nblk * 3 * sizeof(int32_t));
         if (wants_x32(pr->prec_mask))                        // permuted FP32 inputs
@@ -397,7 +398,7 @@ size_t plan_bytes(const ie_problem *pr, int64_t n, int64_t npairs, int64_t nd, i
 // images) run at the same time on neighbouring CTAs of the persistent kernel's static
 // round-robin; order 0 sorts runs by size (largest first).  The tensor-core tile width
 // and order come from ie_plan_tune (default: the full tile width, order 1).
-ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out, int max_cols) {
+ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out, int max_cols, bool pack) {
     auto &cache = tc ? p->tc_work : p->simt_work;
     int cols = tc ? tc_tile_columns() : simt_tile_columns(), order = 1;
     if (tc) {
@@ -405,7 +406,8 @@ ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out, int max_cols) 
         if (t != p->tc_tuned.end()) cols = t->second.first, order = t->second.second;
         if (max_cols > 0) cols = std::min(cols, max_cols);
     }
-    const int key = tc ? (nrhs * 1024 + cols) * 2 + order : nrhs;
+    pack = pack && p->sym && !p->h_pgroup.empty();
+    const int key = tc ? ((nrhs * 1024 + cols) * 2 + order) * 2 + (pack ? 1 : 0) : nrhs;
     auto it = cache.find(key);
     if (it != cache.end()) {
         *out = &it->second;
@@ -425,8 +427,16 @@ ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out, int max_cols) 
     };
     std::vector<WorkItem> items;
     auto emit = [&](int64_t d, int64_t q, int np, int nr) { items.push_back({(int32_t)d, (int32_t)q, np, 0, nr}); };
-    for (int64_t d = 0; d < p->n_far_disp; ++d) {
-        int64_t s = p->h_gstart[d], e = p->h_gstart[d + 1];
+    // symmetric store, packed: the groups of one stored block are contiguous, and an item's
+    // columns may come from several of them (each column carries its own group; `disp` is
+    // the group of the item's first pair)
+    int64_t d_step = 1;
+    for (int64_t d = 0; d < p->n_far_disp; d += d_step) {
+        int64_t d1 = d + 1;
+        if (pack)
+            while (d1 < p->n_far_disp && p->h_gcanon[d1] == p->h_gcanon[d]) ++d1;
+        d_step = d1 - d;
+        int64_t s = p->h_gstart[d], e = p->h_gstart[d1];
         // runs of pairs with the same column count (pairs of one scatterer are contiguous)
         int64_t q = s;
         while (q < e) {
@@ -434,7 +444,7 @@ ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out, int max_cols) 
             const int per = cols / nr;
             int np = 0;
             while (q + np < e && np < per && nr_of(q + np) == nr) ++np;
-            emit(d, q, np, nr);
+            emit(pack ? p->h_pgroup[q] : d, q, np, nr);
             q += np;
         }
     }
@@ -480,7 +490,7 @@ bool block_prec_only(unsigned mask) { return !wants_cvfcnn(mask); }
 ie_status work_list_for(ie_plan p, int prec, int nrhs, WorkList **out) {
     if (prec == IE_PREC_FP32 || prec == IE_PREC_CVFCNN_FP32) return work_list(p, false, nrhs, out);
     if (prec == IE_PREC_CVFCNN) return work_list(p, true, nrhs, out, cvfcnn_tc_tile_columns());
-    return work_list(p, true, nrhs, out);
+    return work_list(p, true, nrhs, out, 0, /*pack=*/true);
 }
 
 int canon_of_disp(const int32_t d[3], int32_t c[3]) { return canon_of(d, c); }
@@ -698,6 +708,44 @@ static ie_status plan_create(const ie_problem *pr, ie_store store, void *stream,
         }
         if (store) canon_disp = store->canon;
     }
+    if (p->sym && p->n_far_disp > 1) {
+        // groups of one stored block next to each other (displacement order within a block),
+        // so that a tensor-core item can take columns from several groups sharing its block
+        const int64_t nd = p->n_far_disp;
+        std::vector<int64_t> ord(nd);
+        for (int64_t d = 0; d < nd; ++d) ord[d] = d;
+        std::stable_sort(ord.begin(), ord.end(), [&](int64_t x, int64_t y) { return gcanon[x] < gcanon[y]; });
+        FarGroups r;
+        r.disp.resize(fg.disp.size());
+        r.start.resize(nd + 1);
+        r.src.resize(fg.src.size());
+        r.dst.resize(fg.dst.size());
+        std::vector<int32_t> gc(nd), gs(nd);
+        int64_t q = 0;
+        for (int64_t k = 0; k < nd; ++k) {
+            const int64_t d = ord[k];
+            for (int c = 0; c < 3; ++c) r.disp[3 * k + c] = fg.disp[3 * d + c];
+            r.start[k] = q;
+            for (int64_t t = fg.start[d]; t < fg.start[d + 1]; ++t, ++q) {
+                r.src[q] = fg.src[t];
+                r.dst[q] = fg.dst[t];
+            }
+            gc[k] = gcanon[d];
+            gs[k] = gsigma[d];
+        }
+        r.start[nd] = q;
+        fg = std::move(r);
+        gcanon.swap(gc);
+        gsigma.swap(gs);
+        p->h_disp = fg.disp;
+        p->h_gstart = fg.start;
+    }
+    if (p->sym) {
+        p->h_gcanon = gcanon;
+        p->h_pgroup.resize(p->n_far_pairs);
+        for (int64_t d = 0; d < p->n_far_disp; ++d)
+            for (int64_t t = p->h_gstart[d]; t < p->h_gstart[d + 1]; ++t) p->h_pgroup[t] = (int32_t)d;
+    }
     p->n_blocks = p->sym ? (int64_t)canon_disp.size() / 3 : p->n_far_disp;
     std::vector<int32_t> nstart, nsrc;
     std::vector<int64_t> nboff;
@@ -763,6 +811,9 @@ static ie_status plan_create(const ie_problem *pr, ie_store store, void *stream,
             symmetry_map(map);
             PT(dalloc_t(p, &p->d_gcanon, gcanon.size()));
             PT(dalloc_t(p, &p->d_gsigma, gsigma.size()));
+            PT(dalloc_t(p, &p->d_pgroup, p->h_pgroup.size()));
+            PC(cudaMemcpy(p->d_pgroup, p->h_pgroup.data(), p->h_pgroup.size() * sizeof(int32_t),
+                          cudaMemcpyHostToDevice));
             PT(dalloc_t(p, &p->d_symmap, map.size()));
             PT(dalloc_t(p, &p->d_canon_disp, canon_disp.size()));
             PC(cudaMemcpy(p->d_gcanon, gcanon.data(), gcanon.size() * sizeof(int32_t), cudaMemcpyHostToDevice));

@@ -195,6 +195,9 @@ struct ie_plan_s {
     bool sym = false;
     int64_t n_blocks = 0;              // stored far blocks (n_far_disp without symmetry)
     int32_t *d_gcanon = nullptr;       // [n_far_disp] stored block of each displacement group
+    std::vector<int32_t> h_gcanon;     // host copy (symmetric store: groups ordered by block)
+    int32_t *d_pgroup = nullptr;       // [n_far_pairs] group of each pair (symmetric store)
+    std::vector<int32_t> h_pgroup;
     int32_t *d_gsigma = nullptr;       // [n_far_disp] signed permutation Q (0..47) with Q c = d
     uint16_t *d_symmap = nullptr;      // [48][192] u -> U(u) | 0x100 when negated (G_d[U(u)][U(v)] = +-G_c[u][v])
     int32_t *d_canon_disp = nullptr;   // [n_blocks x 3]
@@ -296,7 +299,7 @@ ie_status far_product(ie_plan p, int prec, const float2 *c, float2 *y, int nrhs,
 ie_status apply(ie_plan p, int which, int prec, const float2 *c, float2 *y, int nrhs, cudaStream_t st,
                 const int *gate = nullptr);
 // max_cols > 0 (tensor-core lists): no item wider than max_cols columns
-ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out, int max_cols = 0);
+ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out, int max_cols = 0, bool pack = false);
 // The work list the translation of precision `prec` launches with (the same cache entry):
 // made ahead of a stream capture, since building one allocates.
 ie_status work_list_for(ie_plan p, int prec, int nrhs, WorkList **out);

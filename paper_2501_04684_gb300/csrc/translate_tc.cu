@@ -70,7 +70,8 @@ constexpr int kBPlane = kN * kTcK * 2;           // 12 KB: one chunk, one of hi 
 constexpr int kBChunkBytes = 2 * kBPlane;
 constexpr int kBBytes = kTcKChunks * kBChunkBytes;              // 144 KB
 constexpr int kRing = 4;                         // epilogue metadata buffers
-constexpr int kEpiBytes = kRing * kTcTileCols * 8 + kRing * 16; // column offset + scale, item header
+constexpr int kEpiBytes = kRing * kTcTileCols * (8 + 4 + 2) + kRing * 16;   // per column: target, scale, copy
+static_assert(kRing * kTcTileCols * (8 + 4 + 2) % 16 == 0, "item headers 16-byte aligned");
 constexpr int kColBytes = 2 * kTcTileCols * 8;                  // gather base of each column, 2 items
 constexpr int kSmemBytes = kAStages * kAStageBytes + kBBytes + kEpiBytes + kColBytes + 512 /*barriers*/ +
                            1024 /*alignment*/;
@@ -236,6 +237,8 @@ struct TcArgs {
     const int32_t *gsigma;      // [disp] input copy Q
     const uint16_t *symmap;     // [48][192] output map u -> U_Q(u) | 0x100 when negated
     int64_t sig_stride;         // elements between the input copies of Xtc
+    // with the symmetric store an item's columns may come from several groups of its block
+    const int32_t *pgroup;      // [pair] group of each pair (null: the item's own group)
 };
 
 template <bool FP16, bool X3>
@@ -246,9 +249,10 @@ translate_tc_kernel(const TcArgs a) {
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *sAbase = smem;                                                        // [kAStages][16 KB]
     unsigned char *sBbase = smem + kAStages * kAStageBytes;                              // [6][hi, lo][12 KB]
-    int32_t *ep_off = reinterpret_cast<int32_t *>(sBbase + kBBytes);                    // [kRing][96]
+    int64_t *ep_off = reinterpret_cast<int64_t *>(sBbase + kBBytes);                    // [kRing][96] target (floats)
     float *ep_scale = reinterpret_cast<float *>(ep_off + kRing * kTcTileCols);          // [kRing][96]
-    int4 *ep_head = reinterpret_cast<int4 *>(ep_scale + kRing * kTcTileCols);           // [kRing] ncols, disp, sig
+    uint16_t *ep_sig = reinterpret_cast<uint16_t *>(ep_scale + kRing * kTcTileCols);    // [kRing][96] input copy Q
+    int4 *ep_head = reinterpret_cast<int4 *>(ep_sig + kRing * kTcTileCols);             // [kRing] ncols, disp
     const uint16_t **colptr = reinterpret_cast<const uint16_t **>(ep_head + kRing);    // [2][96]
     uint64_t *afull = reinterpret_cast<uint64_t *>(colptr + 2 * kTcTileCols);           // [kAStages]
     uint64_t *aempty = afull + kAStages;                                                 // [kAStages]
@@ -435,15 +439,16 @@ translate_tc_kernel(const TcArgs a) {
         // and the epilogue's target offset and fp16 scale.  The metadata of an item is
         // fetched over the item before it (boxes and copy at its start, fp16 scales at
         // its third chunk), so no dependent global load stalls a chunk.
+        // Each column carries its own group (its slab d mod 8, and with the symmetric store
+        // its input copy Q and output map): a symmetric-store item spans the groups of its block.
         struct Meta {
-            int src, dst, rr, sig, ed, xe, ncols, disp;
+            int src, dst, rr, sig, slab, ed, xe, ncols, disp;
         };
         auto meta_issue = [&](const WorkItem &w, bool valid) {
-            Meta m{0, 0, 0, 0, 0, 0, 0, 0};
+            Meta m{0, 0, 0, 0, 0, 0, 0, 0, 0};
             if (!valid) return m;
             m.ncols = w.npairs * w.nr;
             m.disp = w.disp;
-            m.sig = a.gcanon ? __ldg(a.gsigma + w.disp) : 0;
             if (tid >= m.ncols) return m;
             int p;
             if (w.nr == 1) {
@@ -452,6 +457,9 @@ translate_tc_kernel(const TcArgs a) {
                 p = w.pair0 + tid / w.nr;
                 m.rr = tid % w.nr;
             }
+            const int grp = a.pgroup ? __ldg(a.pgroup + p) : w.disp;
+            m.slab = grp % kSlabs;
+            m.sig = a.gcanon ? __ldg(a.gsigma + grp) : 0;
             m.src = __ldg(a.src + p);
             m.dst = __ldg(a.dst + p);
             return m;
@@ -470,10 +478,12 @@ translate_tc_kernel(const TcArgs a) {
             if (tid < kTcTileCols) {
                 colptr[(il & 1) * kTcTileCols + tid] =
                     on ? a.Xtc + (int64_t)m.sig * a.sig_stride + ((int64_t)m.rr * a.nbox + m.src) * (2 * kNU) : nullptr;
-                ep_off[rb * kTcTileCols + tid] = on ? (m.rr * a.nbox + m.dst) * kNU : 0;
+                ep_off[rb * kTcTileCols + tid] =
+                    on ? (int64_t)m.slab * (2 * (int64_t)a.slab_stride) + 2 * ((int64_t)m.rr * a.nbox + m.dst) * kNU : 0;
                 ep_scale[rb * kTcTileCols + tid] = (FP16 && on) ? ldexpf(1.f, m.ed + m.xe) : 1.f;
+                ep_sig[rb * kTcTileCols + tid] = (uint16_t)(on ? m.sig : 0);
             }
-            if (tid == 0) ep_head[rb] = make_int4(m.ncols, m.disp, m.sig, 0);
+            if (tid == 0) ep_head[rb] = make_int4(m.ncols, m.disp, 0, 0);
             mbar_arrive(smem_u32(&staged[rb]));      // release: the epilogue reads after its wait
         };
         WorkItem w_nxt = first + step < a.n_items ? a.items[first + step] : WorkItem{0, 0, 0, 0, 1};
@@ -537,18 +547,16 @@ translate_tc_kernel(const TcArgs a) {
         // ---------------- epilogue warps 7-14 (TMEM lane quarter = warp mod 4)
         const int q = warp & 3;
         const int half = (warp - kWarpEpi0) >> 2;          // which alternate 32-column chunks
-        const int64_t slab_f = (int64_t)a.slab_stride * 2;
         const bool odd = lane & 1;
         int64_t il = 0;
         bool ok = true;
         for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
             const int rb = (int)(il % kRing);
             if (!warp_wait(smem_u32(&staged[rb]), (uint32_t)((il / kRing) & 1), abort_flag, lim)) break;
-            const int4 hd = ep_head[rb];
-            const int ncols = hd.x, disp = hd.y, sig = hd.z;
-            const int32_t *offs = ep_off + rb * kTcTileCols;
+            const int ncols = ep_head[rb].x;
+            const int64_t *offs = ep_off + rb * kTcTileCols;
             const float *scl = ep_scale + rb * kTcTileCols;
-            float *Yslab = a.Yslab + (int64_t)(disp % kSlabs) * slab_f;
+            const uint16_t *sigs = ep_sig + rb * kTcTileCols;
             for (int mb = 0; mb < 3; ++mb) {
                 const int64_t qa = il * 3 + mb;
                 const int buf = (int)(qa % kAcc);
@@ -557,16 +565,7 @@ translate_tc_kernel(const TcArgs a) {
                     break;
                 }
                 tc_fence_after();
-                const int m0 = 64 * mb + 16 * q;       // first complex row of this warp
-                // float offset of this lane's complex row (the mapped row for the symmetric store)
-                int row_f = 2 * (m0 + (lane >> 1));
-                float sgn = 1.f;
-                if (a.gcanon) {
-                    const uint16_t e = __ldg(a.symmap + sig * kNU + m0 + (lane >> 1));
-                    row_f = 2 * (e & 0xFF);
-                    sgn = (e & 0x100) ? -1.f : 1.f;
-                }
-                float *Yrow = Yslab + row_f;
+                const int mrow = 64 * mb + 16 * q + (lane >> 1);   // this lane's complex row
                 const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * kAccCols;
                 // 32 TMEM columns = 16 complex columns per load.  Lanes 2m', 2m'+1 hold the Re G
                 // and Im G rows of complex row m'; per pair of columns (k, k+1) they exchange
@@ -590,9 +589,16 @@ translate_tc_kernel(const TcArgs a) {
                         const float im = odd ? b0 + g1 : g0 + a1;
                         const int j = jb + 2 * pk + (odd ? 1 : 0);
                         if (j < ncols) {
-                            float sc = sgn;
-                            if (FP16) sc *= scl[j];
-                            red_add_v2(Yrow + 2 * (int64_t)offs[j], sc * re, sc * im);
+                            float sc = FP16 ? scl[j] : 1.f;
+                            // float offset of the row in the target (mapped by the column's Q
+                            // for the symmetric store)
+                            int row_f = 2 * mrow;
+                            if (a.gcanon) {
+                                const uint16_t e = __ldg(a.symmap + sigs[j] * kNU + mrow);
+                                row_f = 2 * (e & 0xFF);
+                                if (e & 0x100) sc = -sc;
+                            }
+                            red_add_v2(a.Yslab + offs[j] + row_f, sc * re, sc * im);
                         }
                     }
                 }
@@ -687,6 +693,7 @@ ie_status launch_translate_tc(ie_plan p, int prec, float2 *Yslab, int nrhs, cuda
     a.gsigma = p->sym ? p->d_gsigma : nullptr;
     a.symmap = p->sym ? p->d_symmap : nullptr;
     a.sig_stride = 2 * a.plane;
+    a.pgroup = p->sym ? p->d_pgroup : nullptr;   // the symmetric store's items are packed
     int grid = (int)std::min<int64_t>(wl->n, (int64_t)kCtasPerSm * (p->tc_sms > 0 ? p->tc_sms : 148));
     if (prec == IE_PREC_BF16X3)
         translate_tc_kernel<false, true><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
