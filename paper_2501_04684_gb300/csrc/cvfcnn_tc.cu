@@ -59,7 +59,8 @@ constexpr int kBBytes = kTcKChunks * kBPlane;                   // 60 KB
 constexpr int kHChunks = kCvHp / kTcK;                          // 2 K-chunks of the hidden operand
 constexpr int kHBytes = kHChunks * kBPlane;                     // 20 KB per hidden buffer
 constexpr int kRing = 8;
-constexpr int kEpiBytes = kRing * kCvTileCols * 12 + kRing * 16;
+constexpr int kEpiBytes = kRing * kCvTileCols * (8 + 4 + 4 + 2) + kRing * 16;   // per column: target, scales, Q
+static_assert(kRing * kCvTileCols * (8 + 4 + 4 + 2) % 16 == 0, "item headers 16-byte aligned");
 constexpr int kColBytes = 2 * kCvTileCols * 8;
 constexpr int kBars = 2 * kAStages + 3 * kTcKChunks + 2 + 4 * 2 + kRing + 1;
 constexpr int kSmemBytes = kAStages * kImgBytes + kBBytes + 2 * kHBytes + kEpiBytes + kColBytes + 8 * kBars + 16 + 1024;
@@ -247,8 +248,12 @@ struct CvArgs {
     const int32_t *gcanon, *gsigma;
     const uint16_t *symmap;
     int64_t sig_stride;
+    const int32_t *pgroup;      // [pair] group of each pair (null: the item's own group)
 };
 
+// SYM: symmetric store (the output maps each column's rows by its Q); one instantiation per
+// store mode keeps the other mode's code out of the output loop
+template <bool SYM>
 __global__ void __launch_bounds__(kThreads, 1) cvfcnn_tc_kernel(const CvArgs a) {
     if (a.gate && *a.gate == 0) return;
     extern __shared__ unsigned char smem_raw[];
@@ -256,10 +261,11 @@ __global__ void __launch_bounds__(kThreads, 1) cvfcnn_tc_kernel(const CvArgs a) 
     unsigned char *sA = smem;                                                // [kAStages][8 KB]
     unsigned char *sB = sA + kAStages * kImgBytes;                           // [6][10 KB]
     unsigned char *sH = sB + kBBytes;                                        // [2 buffers][2][10 KB]
-    int32_t *ep_off = reinterpret_cast<int32_t *>(sH + 2 * kHBytes);        // [kRing][80]
+    int64_t *ep_off = reinterpret_cast<int64_t *>(sH + 2 * kHBytes);        // [kRing][80] target (floats)
     float *ep_sc1 = reinterpret_cast<float *>(ep_off + kRing * kCvTileCols); // [kRing][80] layer-1 scale
     float *ep_s = ep_sc1 + kRing * kCvTileCols;                              // [kRing][80] ||x||_inf
-    int4 *ep_head = reinterpret_cast<int4 *>(ep_s + kRing * kCvTileCols);    // ncols, disp, sig, block
+    uint16_t *ep_sig = reinterpret_cast<uint16_t *>(ep_s + kRing * kCvTileCols);   // [kRing][80] input copy Q
+    int4 *ep_head = reinterpret_cast<int4 *>(ep_sig + kRing * kCvTileCols);  // ncols, disp, -, block
     const uint16_t **colptr = reinterpret_cast<const uint16_t **>(ep_head + kRing);
     uint64_t *afull = reinterpret_cast<uint64_t *>(colptr + 2 * kCvTileCols);
     uint64_t *aempty = afull + kAStages;
@@ -443,20 +449,24 @@ __global__ void __launch_bounds__(kThreads, 1) cvfcnn_tc_kernel(const CvArgs a) 
         // ---------------- input gatherers (warps 3-6)
         const int tid = threadIdx.x - 32 * kWarpGath0;
         bool ok = true;
+        // each column carries its own group (slab, and with the symmetric store its input
+        // copy Q and output map): a symmetric-store item spans the groups of its block
         struct Meta {
-            int src, dst, rr, sig, ncols, disp, blk;
+            int src, dst, rr, sig, slab, ncols, disp, blk;
             float sc1, s;
         };
         auto meta_issue = [&](const WorkItem &w, bool valid) {
-            Meta m{0, 0, 0, 0, 0, 0, 0, 0.f, 0.f};
+            Meta m{0, 0, 0, 0, 0, 0, 0, 0, 0.f, 0.f};
             if (!valid) return m;
             m.ncols = w.npairs * w.nr;
             m.disp = w.disp;
             m.blk = block_of(w.disp);
-            m.sig = a.gcanon ? __ldg(a.gsigma + w.disp) : 0;
             if (tid >= m.ncols) return m;
             const int p = w.pair0 + (w.nr == 1 ? tid : tid / w.nr);
             m.rr = w.nr == 1 ? 0 : tid % w.nr;
+            const int grp = a.pgroup ? __ldg(a.pgroup + p) : w.disp;
+            m.slab = grp % kSlabs;
+            m.sig = a.gcanon ? __ldg(a.gsigma + grp) : 0;
             m.src = __ldg(a.src + p);
             m.dst = __ldg(a.dst + p);
             return m;
@@ -476,11 +486,17 @@ __global__ void __launch_bounds__(kThreads, 1) cvfcnn_tc_kernel(const CvArgs a) 
             if (tid < kCvTileCols) {
                 colptr[(il & 1) * kCvTileCols + tid] =
                     on ? a.Xtc + (int64_t)m.sig * a.sig_stride + ((int64_t)m.rr * a.nbox + m.src) * (2 * kNU) : nullptr;
-                ep_off[rb * kCvTileCols + tid] = on ? (m.rr * a.nbox + m.dst) * kNU : 0;
+                if (SYM)   // float offset of the column's target, its slab included
+                    ep_off[rb * kCvTileCols + tid] =
+                        on ? (int64_t)m.slab * (2 * (int64_t)a.slab_stride) + 2 * ((int64_t)m.rr * a.nbox + m.dst) * kNU
+                           : 0;
+                else       // complex offset inside the item's slab (32 bits, in the same buffer)
+                    reinterpret_cast<int32_t *>(ep_off)[rb * kCvTileCols + tid] = on ? (m.rr * a.nbox + m.dst) * kNU : 0;
+                ep_sig[rb * kCvTileCols + tid] = (uint16_t)(on ? m.sig : 0);
                 ep_sc1[rb * kCvTileCols + tid] = on ? m.sc1 : 0.f;
                 ep_s[rb * kCvTileCols + tid] = on ? m.s : 0.f;
             }
-            if (tid == 0) ep_head[rb] = make_int4(m.ncols, m.disp, m.sig, m.blk);
+            if (tid == 0) ep_head[rb] = make_int4(m.ncols, m.disp, 0, m.blk);
             mbar_arrive(smem_u32(&staged[rb]));
         };
         if (nil > 0) {
@@ -590,19 +606,19 @@ __global__ void __launch_bounds__(kThreads, 1) cvfcnn_tc_kernel(const CvArgs a) 
         // ---------------- output, warps 15-22 (TMEM lane quarter = warp mod 4)
         const int q = warp & 3;
         const int half = (warp - kWarpOut0) >> 2;
-        const int64_t slab_f = (int64_t)a.slab_stride * 2;
         const bool odd = lane & 1;
         bool ok = true;
         for (int64_t il = 0; il < nil && ok; ++il) {
             const int rb = (int)(il % kRing);
             if (!warp_wait(smem_u32(&staged[rb]), (uint32_t)((il / kRing) & 1), abort_flag)) break;
             const int4 hd = ep_head[rb];
-            const int ncols = hd.x, disp = hd.y, sig = hd.z, blk = hd.w;
-            const int32_t *offs = ep_off + rb * kCvTileCols;
+            const int ncols = hd.x, blk = hd.w, slab = hd.y % kSlabs;   // the item's slab (full store)
+            const int64_t *offs = ep_off + rb * kCvTileCols;
+            const int32_t *offs32 = reinterpret_cast<const int32_t *>(ep_off) + rb * kCvTileCols;
             const float *sx = ep_s + rb * kCvTileCols;
+            const uint16_t *sigs = ep_sig + rb * kCvTileCols;
             const float2 *Wb = a.W + (size_t)blk * kCvBlockElems;
             const float s2 = ldexpf(1.f, __ldg(a.wexp + 2 * blk + 1));
-            float *Yslab = a.Yslab + (int64_t)(disp % kSlabs) * slab_f;
             for (int mb = 0; mb < 3; ++mb) {
                 const int64_t u = il * 3 + mb;
                 const int sl = (int)(u & 1);
@@ -613,15 +629,9 @@ __global__ void __launch_bounds__(kThreads, 1) cvfcnn_tc_kernel(const CvArgs a) 
                 tc_fence_after();
                 const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + d2col(sl);
                 const int mrow = 64 * mb + 16 * q + (lane >> 1);
-                const float2 bias = __ldg(Wb + kCvB2 + mrow);
-                int row_f = 2 * mrow;
-                float sgn = 1.f;
-                if (a.gcanon) {
-                    const uint16_t e = __ldg(a.symmap + sig * kNU + mrow);
-                    row_f = 2 * (e & 0xFF);
-                    sgn = (e & 0x100) ? -1.f : 1.f;
-                }
-                float *Yrow = Yslab + row_f;
+                const float2 bias = __ldg(Wb + kCvB2 + mrow);   // canonical row (frame of the block)
+                // the row itself without the symmetric store (one slab per item)
+                float *const Yrow = a.Yslab + (int64_t)slab * (2 * (int64_t)a.slab_stride) + 2 * mrow;
                 for (int c0 = 32 * half; c0 < 2 * ncols; c0 += 32 * (kOutWarps / 4)) {
                     uint32_t r[32];
                     tmem_ld32(tbase + (uint32_t)c0, r);
@@ -637,8 +647,14 @@ __global__ void __launch_bounds__(kThreads, 1) cvfcnn_tc_kernel(const CvArgs a) 
                         const float im = odd ? b0 + g1 : g0 + a1;
                         const int j = jb + 2 * pk + (odd ? 1 : 0);
                         if (j < ncols) {
-                            const float s = sgn * sx[j];
-                            red_add_v2(Yrow + 2 * (int64_t)offs[j], s * fmaf(re, s2, bias.x), s * fmaf(im, s2, bias.y));
+                            float s = sx[j];
+                            float *y = Yrow + 2 * (int64_t)offs32[j];
+                            if (SYM) {   // the row mapped by the column's Q
+                                const uint16_t e = __ldg(a.symmap + sigs[j] * kNU + mrow);
+                                y = a.Yslab + offs[j] + 2 * (e & 0xFF);
+                                if (e & 0x100) s = -s;
+                            }
+                            red_add_v2(y, s * fmaf(re, s2, bias.x), s * fmaf(im, s2, bias.y));
                         }
                     }
                 }
@@ -659,7 +675,8 @@ __global__ void __launch_bounds__(kThreads, 1) cvfcnn_tc_kernel(const CvArgs a) 
 }  // namespace
 
 ie_status prepare_cvfcnn_tc() {
-    IE_CK(cudaFuncSetAttribute(cvfcnn_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    IE_CK(cudaFuncSetAttribute(cvfcnn_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    IE_CK(cudaFuncSetAttribute(cvfcnn_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     return IE_OK;
 }
 
@@ -702,8 +719,12 @@ ie_status launch_translate_cvfcnn_tc(ie_plan p, float2 *Yslab, int nrhs, cudaStr
     a.gsigma = p->sym ? p->d_gsigma : nullptr;
     a.symmap = p->sym ? p->d_symmap : nullptr;
     a.sig_stride = 2 * a.plane;
+    a.pgroup = p->sym ? p->d_pgroup : nullptr;   // the symmetric store's items are packed
     const int grid = (int)std::min<int64_t>(wl->n, p->tc_sms > 0 ? p->tc_sms : 148);
-    cvfcnn_tc_kernel<<<grid, kThreads, kSmemBytes, st>>>(a);
+    if (p->sym)
+        cvfcnn_tc_kernel<true><<<grid, kThreads, kSmemBytes, st>>>(a);
+    else
+        cvfcnn_tc_kernel<false><<<grid, kThreads, kSmemBytes, st>>>(a);
     IE_CK_LAUNCH();
     return IE_OK;
 }

@@ -70,7 +70,7 @@ constexpr int kBPlane = kN * kTcK * 2;           // 12 KB: one chunk, one of hi 
 constexpr int kBChunkBytes = 2 * kBPlane;
 constexpr int kBBytes = kTcKChunks * kBChunkBytes;              // 144 KB
 constexpr int kRing = 4;                         // epilogue metadata buffers
-constexpr int kEpiBytes = kRing * kTcTileCols * (8 + 4 + 2) + kRing * 16;   // per column: target, scale, copy
+constexpr int kEpiBytes = kRing * kTcTileCols * (8 + 4 + 2) + kRing * 16;   // per column: target, scale, Q
 static_assert(kRing * kTcTileCols * (8 + 4 + 2) % 16 == 0, "item headers 16-byte aligned");
 constexpr int kColBytes = 2 * kTcTileCols * 8;                  // gather base of each column, 2 items
 constexpr int kSmemBytes = kAStages * kAStageBytes + kBBytes + kEpiBytes + kColBytes + 512 /*barriers*/ +
@@ -241,7 +241,9 @@ struct TcArgs {
     const int32_t *pgroup;      // [pair] group of each pair (null: the item's own group)
 };
 
-template <bool FP16, bool X3>
+// SYM: symmetric store (the epilogue maps each column's rows by its Q); one instantiation per
+// store mode keeps the other mode's code out of the epilogue loop
+template <bool FP16, bool X3, bool SYM>
 __global__ void __launch_bounds__(kThreadsTc, kCtasPerSm)
 translate_tc_kernel(const TcArgs a) {
     if (a.gate && *a.gate == 0) return;
@@ -478,8 +480,12 @@ translate_tc_kernel(const TcArgs a) {
             if (tid < kTcTileCols) {
                 colptr[(il & 1) * kTcTileCols + tid] =
                     on ? a.Xtc + (int64_t)m.sig * a.sig_stride + ((int64_t)m.rr * a.nbox + m.src) * (2 * kNU) : nullptr;
-                ep_off[rb * kTcTileCols + tid] =
-                    on ? (int64_t)m.slab * (2 * (int64_t)a.slab_stride) + 2 * ((int64_t)m.rr * a.nbox + m.dst) * kNU : 0;
+                if (SYM)   // float offset of the column's target, its slab included
+                    ep_off[rb * kTcTileCols + tid] =
+                        on ? (int64_t)m.slab * (2 * (int64_t)a.slab_stride) + 2 * ((int64_t)m.rr * a.nbox + m.dst) * kNU
+                           : 0;
+                else       // complex offset inside the item's slab (32 bits, in the same buffer)
+                    reinterpret_cast<int32_t *>(ep_off)[rb * kTcTileCols + tid] = on ? (m.rr * a.nbox + m.dst) * kNU : 0;
                 ep_scale[rb * kTcTileCols + tid] = (FP16 && on) ? ldexpf(1.f, m.ed + m.xe) : 1.f;
                 ep_sig[rb * kTcTileCols + tid] = (uint16_t)(on ? m.sig : 0);
             }
@@ -553,8 +559,9 @@ translate_tc_kernel(const TcArgs a) {
         for (int64_t i = first; i < a.n_items && ok; i += step, ++il) {
             const int rb = (int)(il % kRing);
             if (!warp_wait(smem_u32(&staged[rb]), (uint32_t)((il / kRing) & 1), abort_flag, lim)) break;
-            const int ncols = ep_head[rb].x;
+            const int ncols = ep_head[rb].x, slab = ep_head[rb].y % kSlabs;   // the item's slab (full store)
             const int64_t *offs = ep_off + rb * kTcTileCols;
+            const int32_t *offs32 = reinterpret_cast<const int32_t *>(ep_off) + rb * kTcTileCols;
             const float *scl = ep_scale + rb * kTcTileCols;
             const uint16_t *sigs = ep_sig + rb * kTcTileCols;
             for (int mb = 0; mb < 3; ++mb) {
@@ -566,6 +573,8 @@ translate_tc_kernel(const TcArgs a) {
                 }
                 tc_fence_after();
                 const int mrow = 64 * mb + 16 * q + (lane >> 1);   // this lane's complex row
+                // its target row without the symmetric store (one slab per item)
+                float *const Yrow = a.Yslab + (int64_t)slab * (2 * (int64_t)a.slab_stride) + 2 * mrow;
                 const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * kAccCols;
                 // 32 TMEM columns = 16 complex columns per load.  Lanes 2m', 2m'+1 hold the Re G
                 // and Im G rows of complex row m'; per pair of columns (k, k+1) they exchange
@@ -590,15 +599,13 @@ translate_tc_kernel(const TcArgs a) {
                         const int j = jb + 2 * pk + (odd ? 1 : 0);
                         if (j < ncols) {
                             float sc = FP16 ? scl[j] : 1.f;
-                            // float offset of the row in the target (mapped by the column's Q
-                            // for the symmetric store)
-                            int row_f = 2 * mrow;
-                            if (a.gcanon) {
+                            float *y = Yrow + 2 * (int64_t)offs32[j];
+                            if (SYM) {   // the row mapped by the column's Q
                                 const uint16_t e = __ldg(a.symmap + sigs[j] * kNU + mrow);
-                                row_f = 2 * (e & 0xFF);
+                                y = a.Yslab + offs[j] + 2 * (e & 0xFF);
                                 if (e & 0x100) sc = -sc;
                             }
-                            red_add_v2(a.Yslab + offs[j] + row_f, sc * re, sc * im);
+                            red_add_v2(y, sc * re, sc * im);
                         }
                     }
                 }
@@ -618,8 +625,19 @@ translate_tc_kernel(const TcArgs a) {
 
 template <bool FP16, bool X3>
 ie_status set_attr() {
-    IE_CK(cudaFuncSetAttribute(translate_tc_kernel<FP16, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    IE_CK(cudaFuncSetAttribute(translate_tc_kernel<FP16, X3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kSmemBytes));
+    IE_CK(cudaFuncSetAttribute(translate_tc_kernel<FP16, X3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               kSmemBytes));
     return IE_OK;
+}
+
+template <bool FP16, bool X3>
+void launch_tc(const TcArgs &a, int grid, bool sym, cudaStream_t st) {
+    if (sym)
+        translate_tc_kernel<FP16, X3, true><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
+    else
+        translate_tc_kernel<FP16, X3, false><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
 }
 
 }  // namespace
@@ -696,13 +714,13 @@ ie_status launch_translate_tc(ie_plan p, int prec, float2 *Yslab, int nrhs, cuda
     a.pgroup = p->sym ? p->d_pgroup : nullptr;   // the symmetric store's items are packed
     int grid = (int)std::min<int64_t>(wl->n, (int64_t)kCtasPerSm * (p->tc_sms > 0 ? p->tc_sms : 148));
     if (prec == IE_PREC_BF16X3)
-        translate_tc_kernel<false, true><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
+        launch_tc<false, true>(a, grid, p->sym, st);
     else if (prec == IE_PREC_FP16X3)
-        translate_tc_kernel<true, true><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
+        launch_tc<true, true>(a, grid, p->sym, st);
     else if (prec == IE_PREC_BF16X1)
-        translate_tc_kernel<false, false><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
+        launch_tc<false, false>(a, grid, p->sym, st);
     else if (prec == IE_PREC_FP16X1)
-        translate_tc_kernel<true, false><<<grid, kThreadsTc, kSmemBytes, st>>>(a);
+        launch_tc<true, false>(a, grid, p->sym, st);
     else
         return set_error("not a tensor-core precision: %d", prec), IE_ERR_INVALID;
     IE_CK_LAUNCH();
