@@ -65,8 +65,9 @@ def parse():
     ap.add_argument("--mapped", action="store_true",
                     help="shell16 only: P built on the GPU by the mapping construction (eq. 11) from seeded "
                          "point-dipole basis functions instead of random")
-    ap.add_argument("--symmetry", type=int, default=0, choices=[0, 1],
-                    help="1: symmetry-compressed coupling store (one block per sorted |d|)")
+    ap.add_argument("--symmetry", type=int, default=None, choices=[0, 1],
+                    help="1: symmetry-compressed coupling store (one block per sorted |d|); default 1 for shell32 "
+                         "(the headline), 0 otherwise")
     ap.add_argument("--requests", type=int, default=12, help="serve: requests per run")
     ap.add_argument("--record-requests", type=int, default=6,
                     help="shell32: requests of the bounded serving record")
@@ -74,7 +75,10 @@ def parse():
                     help="serve: offered loads as fractions of the plain form's capacity")
     ap.add_argument("--serve-batch", type=int, default=4, help="serve: most requests merged into one plan")
     ap.add_argument("--serve-workers", type=int, default=4, help="serve: worker threads (streams)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.symmetry is None:
+        args.symmetry = 1 if args.workload == "shell32" else 0
+    return args
 
 
 # ------------------------------------------------------------------ clocks
@@ -178,7 +182,9 @@ def shell32_config(symmetry: int = 0, world: int = 1) -> dict:
                           "in FP64) around GMRES(50) on FP16X3 tcgen05 products (fp16 hi+lo split, FP32 "
                           "accumulate, FP32 Krylov vectors, FP64 dots and Givens) to 5e-6; stop at 1e-5"),
             "tol": 1e-5, "nrhs": 1, "symmetry": symmetry,
-            "l2": "no flush needed: each product streams >= 33 GB of coupling images (> 129 MB L2)",
+            "l2": ("no flush needed: each product streams >= 33 GB of coupling images (> 129 MB L2)" if not symmetry
+                   else "symmetry-compressed store (2,780 blocks, 820 MB of images per 16-bit store, > 129 MB L2); "
+                        "inputs (48 permuted copies) and slabs are rewritten every product"),
             "parallelism": "replicas" if world > 1 else "single"}
 
 
@@ -449,7 +455,7 @@ def run_shell16(ctx):
     }
     plan.close()
     if not args.no_surrogate and args.lfb is None and not args.mapped:
-        result["surrogate"] = surrogate_record(ctx, args.symmetry)
+        result["surrogate"] = surrogate_record(ctx)
     if mapping is not None:
         result["mapping"] = mapping
     if ctx.rank == 0 and world == 1:
@@ -544,13 +550,14 @@ def run_shell32(ctx):
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     e2e = time_e2e(ctx, plan, v, x, paths[HEAD32]["opts"], args.steps)
     pairs = st["n_far_pairs"]
-    roofline = tc_roofline(pairs, far["fp16x3"]["translate_kernel_ms"], 3, None if args.symmetry else "translate_tc_fp16x3_shell32.md",
+    roofline = tc_roofline(pairs, far["fp16x3"]["translate_kernel_ms"], 3,
+                           "translate_tc_fp16x3_shell32_sym.md" if args.symmetry else "translate_tc_fp16x3_shell32.md",
                            "translate_tc_kernel<fp16,x3>")
     simt_ach = pairs * 8 * 192 * 192 / (far["fp32"]["translate_kernel_ms"] / 1e3) / 1e12
     roofline_fp32 = {"bound": "alu", "achieved": simt_ach, "peak": FP32_SIMT_PEAK_TFLOPS, "unit": "TFLOP/s",
                      "frac": simt_ach / FP32_SIMT_PEAK_TFLOPS, "kernel": "translate_simt_kernel",
-                     "traffic": (profiled_traffic("translate_simt_fp32_shell32.md", "translate_simt.cu")
-                                 if not args.symmetry else None),
+                     "traffic": profiled_traffic("translate_simt_fp32_shell32_sym.md" if args.symmetry
+                                                 else "translate_simt_fp32_shell32.md", "translate_simt.cu"),
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
     keys = ("solves_per_s", "p50_ms", "p99_ms", "iterations", "matvecs", "refinements", "relres")
     result = {
@@ -584,11 +591,11 @@ def run_shell32(ctx):
     return result
 
 
-def surrogate_record(ctx, symmetry: int = 1) -> dict:
-    """Translation networks of §3 on shell16: trained on the GPU (first stage, e^u < 1e-3),
-    then far products with the networks on the tensor cores and in FP32 beside the FP16X3
-    block product on the same plan, their distance from it, and a refined solve to 1e-5
-    whose inner GMRES runs on the tensor-core networks."""
+def surrogate_one(ctx, symmetry: int, solves_too: bool) -> dict:
+    """Translation networks of §3 on shell16 in one store mode: trained on the GPU (first
+    stage, e^u < 1e-3), then far products with the networks on the tensor cores and in FP32
+    beside the FP16X3 block product on the same plan, their distance from it, and (solves_too)
+    a refined solve to 1e-5 whose inner GMRES runs on the tensor-core networks."""
     args, ie, W, torch, np = ctx.args, ctx.ie, ctx.W, ctx.torch, ctx.np
     p = W.shell16()
     p.alpha = W.alpha_for("shell16")
@@ -615,8 +622,8 @@ def surrogate_record(ctx, symmetry: int = 1) -> dict:
                              inner_tol=1e-3)
     opts_blk = ie.solve_opts(tol=1e-5, restart=50, prec=ie.IE_PREC_FP16X3)
     keys = ("solves_per_s", "p50_ms", "iterations", "matvecs", "refinements", "relres")
-    solves = {"cvfcnn_refined": time_solves(ctx, plan, v, x, 1, opts_net, 3, 1),
-              "fp16x3": time_solves(ctx, plan, v, x, 1, opts_blk, 3, 1)}
+    solves = ({"cvfcnn_refined": time_solves(ctx, plan, v, x, 1, opts_net, 3, 1),
+               "fp16x3": time_solves(ctx, plan, v, x, 1, opts_blk, 3, 1)} if solves_too else {})
     H = st["cvfcnn_hidden"]
     pairs = st["n_far_pairs"]
     peaks = measured_peaks()
@@ -624,8 +631,10 @@ def surrogate_record(ctx, symmetry: int = 1) -> dict:
     ach = pairs * 8 * 2 * 192 * H / (far["cvfcnn"]["translate_kernel_ms"] / 1e3) / 1e12
     ach32 = pairs * 8 * 2 * 192 * H / (far["cvfcnn_fp32"]["translate_kernel_ms"] / 1e3) / 1e12
     out = {
-        "workload": ("shell16 (1,264 boxes, 1,575,248 far pairs), symmetry-compressed store: one network per "
-                     f"canonical displacement ({st['n_coupling_blocks']}), H = {H}"),
+        "workload": ("shell16 (1,264 boxes, 1,575,248 far pairs), " +
+                     ("symmetry-compressed store: one network per canonical displacement"
+                      if symmetry else "full store: the canonical networks turned into every displacement's frame") +
+                     f" ({st['n_coupling_blocks']} stored), H = {H}"),
         "plan_seconds": plan_s,
         "training": {k: info[k] for k in ("networks", "converged", "eu_max", "eu_mean", "steps_max", "seconds")},
         "far_matvecs": far,
@@ -648,6 +657,17 @@ def surrogate_record(ctx, symmetry: int = 1) -> dict:
     del v, x, c, ys
     torch.cuda.empty_cache()
     return out
+
+
+def surrogate_record(ctx) -> dict:
+    """The networks' record in both store modes (each trains its canonical networks): the
+    full store, where each displacement has its own network and block, and the symmetric
+    store, where items of the block product pack the groups of one stored block."""
+    full = surrogate_one(ctx, 0, False)
+    sym = surrogate_one(ctx, 1, True)
+    return {"full_store": full, "symmetric_store": sym,
+            "kernel_vs_fp16x3_block": {"full_store": full["kernel_vs_fp16x3_block"],
+                                       "symmetric_store": sym["kernel_vs_fp16x3_block"]}}
 
 
 def time_e2e(ctx, plan, v, x, opts, steps):

@@ -6,7 +6,8 @@ import re
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 KERNEL_SUMMARIES = ("translate_tc_fp16x3_shell16.md", "translate_tc_fp16x3_shell32.md",
-                    "translate_simt_fp32_shell32.md", "cvfcnn_tc_shell16.md")
+                    "translate_tc_fp16x3_shell32_sym.md", "translate_simt_fp32_shell32.md",
+                    "translate_simt_fp32_shell32_sym.md", "cvfcnn_tc_shell16.md")
 
 
 def test_profiles_are_short_text_with_their_commands():
