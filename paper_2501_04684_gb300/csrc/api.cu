@@ -407,7 +407,7 @@ ie_status work_list(ie_plan p, bool tc, int nrhs, WorkList **out, int max_cols, 
         if (max_cols > 0) cols = std::min(cols, max_cols);
     }
     pack = pack && p->sym && !p->h_pgroup.empty();
-    const int key = tc ? ((nrhs * 1024 + cols) * 2 + order) * 2 + (pack ? 1 : 0) : nrhs;
+    const int key = tc ? ((nrhs * 1024 + cols) * 2 + order) * 2 + (pack ? 1 : 0) : nrhs * 2 + (pack ? 1 : 0);
     auto it = cache.find(key);
     if (it != cache.end()) {
         *out = &it->second;
@@ -488,7 +488,8 @@ ie_status generate_blocks(double k, double eta, double a, const int32_t *d_disp,
 bool block_prec_only(unsigned mask) { return !wants_cvfcnn(mask); }
 
 ie_status work_list_for(ie_plan p, int prec, int nrhs, WorkList **out) {
-    if (prec == IE_PREC_FP32 || prec == IE_PREC_CVFCNN_FP32) return work_list(p, false, nrhs, out);
+    if (prec == IE_PREC_FP32) return work_list(p, false, nrhs, out, 0, /*pack=*/true);
+    if (prec == IE_PREC_CVFCNN_FP32) return work_list(p, false, nrhs, out);
     if (prec == IE_PREC_CVFCNN) return work_list(p, true, nrhs, out, cvfcnn_tc_tile_columns(), /*pack=*/true);
     return work_list(p, true, nrhs, out, 0, /*pack=*/true);
 }

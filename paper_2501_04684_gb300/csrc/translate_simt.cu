@@ -48,10 +48,14 @@ namespace {
 
 // Symmetry-compressed store: the block of displacement d is G_c (c canonical) and
 // G_d = S G_c S^T, so the tile reads G_c, takes its input from the signed-permuted
-// copy Q of X, and adds output row u at U_Q(u) with the map's sign.
+// copy Q of X, and adds output row u at U_Q(u) with the map's sign.  Items are packed:
+// the groups of one stored block are contiguous in the pair list, and an item's columns
+// may come from several of them, each column with its own group (pgroup), hence its own
+// input copy, slab and output map.
 struct SymArgs {
     const int32_t *gcanon = nullptr;     // [disp] stored block (null: no symmetry)
     const int32_t *gsigma = nullptr;     // [disp] copy Q of the input
+    const int32_t *pgroup = nullptr;     // [pair] group of the pair (packed items)
     const uint16_t *map = nullptr;       // [48][192]
     size_t stride = 0;                   // complex elements between input copies
 };
@@ -66,9 +70,8 @@ __device__ __forceinline__ void simt_tile(const WorkItem it, const float2 *__res
     SmemSimt &S = *reinterpret_cast<SmemSimt *>(smem_raw);
     const int tid = threadIdx.x;
     const int ncols = it.npairs * it.nr;
-    const int sigma = sy.gcanon ? sy.gsigma[it.disp] : 0;
     const float2 *Cd = C + (int64_t)(sy.gcanon ? sy.gcanon[it.disp] : it.disp) * kNU * kNU;
-    if (sy.gcanon) X += (size_t)sigma * sy.stride;
+    auto group_of = [&](int pair) { return sy.pgroup ? __ldg(sy.pgroup + pair) : it.disp; };
 
     // B loader: thread -> (column, kBPer consecutive k)
     const int lcol = tid % kTileN;
@@ -77,6 +80,7 @@ __device__ __forceinline__ void simt_tile(const WorkItem it, const float2 *__res
     const int lpair = it.pair0 + lc / it.nr;
     const int lr = lc % it.nr;
     const float2 *xcol = X + ((int64_t)lr * nbox + src[lpair]) * kNU;
+    if (sy.gcanon) xcol += (size_t)__ldg(sy.gsigma + group_of(lpair)) * sy.stride;
 
     auto load_chunk = [&](int kc, int buf) {
         // A: kKC x 192 float2 in 16-byte copies, kAVec per thread
@@ -141,24 +145,21 @@ __device__ __forceinline__ void simt_tile(const WorkItem it, const float2 *__res
         __syncthreads();
     }
 
-    float2 *Ys = Yslab + (size_t)(it.disp % kSlabs) * slab_stride;
-    uint16_t rmap[6];
-    if (sy.gcanon) {
-#pragma unroll
-        for (int i = 0; i < 6; ++i) rmap[i] = sy.map[sigma * kNU + 2 * tm + 64 * (i >> 1) + (i & 1)];
-    }
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         int col = 2 * tn + 16 * (j >> 1) + (j & 1);
         if (col >= ncols) continue;
         int pair = it.pair0 + col / it.nr;
         int r = col % it.nr;
-        float2 *ycol = Ys + ((int64_t)r * nbox + dst[pair]) * kNU;
+        const int grp = group_of(pair);
+        float2 *ycol = Yslab + (size_t)(grp % kSlabs) * slab_stride + ((int64_t)r * nbox + dst[pair]) * kNU;
         if (sy.gcanon) {
+            const uint16_t *map = sy.map + __ldg(sy.gsigma + grp) * kNU;
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
-                const float sg = (rmap[i] & 0x100) ? -1.f : 1.f;
-                atomicAdd(ycol + (rmap[i] & 0xFF), make_float2(sg * acc[i][j].x, sg * acc[i][j].y));
+                const uint16_t e = __ldg(map + 2 * tm + 64 * (i >> 1) + (i & 1));
+                const float sg = (e & 0x100) ? -1.f : 1.f;
+                atomicAdd(ycol + (e & 0xFF), make_float2(sg * acc[i][j].x, sg * acc[i][j].y));
             }
         } else {
 #pragma unroll
@@ -201,6 +202,7 @@ ie_status launch_translate_simt(ie_plan p, const float2 *X, float2 *Yslab, int n
         X = p->d_Xsym;
         sy.gcanon = p->d_gcanon;
         sy.gsigma = p->d_gsigma;
+        sy.pgroup = p->d_pgroup;
         sy.map = p->d_symmap;
         sy.stride = (size_t)nrhs * p->nbox * kNU;
     }
