@@ -297,7 +297,8 @@ ie_status ie_disaggregate(ie_plan plan, const void *Y, void *r, int nrhs, void *
  * scratch is a fixed 32 MiB device area inside libie (held by every GPU that loads the
  * library until exit) that must hold 8 x nrhs x n_boxes x 192 complex64 partial sums;
  * larger requests return IE_ERR_INVALID with the sizes in ie_last_error().  The first call on a device looks the area up and sets the kernel
- * up on that device (make it before any stream capture).  Every call reuses the same
+ * up on that device (make it before any stream capture); later calls launch kernels
+ * only and may be captured into a CUDA graph and replayed.  Every call reuses the same
  * area, so calls that overlap in time on the GPU (any streams, any plans) race; the
  * partial sums are cleared by each call.  X, Y: device complex64 [nrhs][n_boxes][192].
  * A plan built without IE_PREC_FP32, with symmetry = 1 or with group_nrhs returns

@@ -60,6 +60,31 @@ def test_noalloc_translate_batched_plan():
         _check_twice(plan, plan.stats["n_boxes"], nrhs, 301)
 
 
+def test_noalloc_translate_replays_from_a_captured_graph():
+    """After the first call has set the area up on the device, a call launches kernels
+    only (no allocation, no host copy), so it can be captured into a CUDA graph; each
+    replay clears the partial sums again and gives ie_translate's result."""
+    import torch
+    p = W.tiny()
+    nrhs = 2
+    with plan_for(p, max_rhs=nrhs) as plan:
+        X = dev(_dipole_moments(p.n_boxes, nrhs, 302))
+        ref = empty((nrhs, p.n_boxes, 192))
+        ie.ie_translate(plan.handle, ie.IE_PREC_FP32, X, ref, nrhs)
+        yref = host(ref)
+        out = empty((nrhs, p.n_boxes, 192))
+        ie.ie_translate_noalloc(plan.handle, X, out, nrhs)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            ie.ie_translate_noalloc(plan.handle, X, out, nrhs)
+        for _ in range(2):
+            out.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            assert rel_l2(host(out), yref) <= TOL
+
+
 def test_noalloc_rejects_requests_beyond_the_fixed_area():
     p = W.tiny()
     with plan_for(p, max_rhs=64) as plan:
