@@ -67,7 +67,7 @@ def parse():
                          "point-dipole basis functions instead of random")
     ap.add_argument("--symmetry", type=int, default=None, choices=[0, 1],
                     help="1: symmetry-compressed coupling store (one block per sorted |d|); default 1 for shell32 "
-                         "(the headline), 0 otherwise")
+                         "(the headline) and serve (one shared store for every request), 0 otherwise")
     ap.add_argument("--requests", type=int, default=12, help="serve: requests per run")
     ap.add_argument("--record-requests", type=int, default=6,
                     help="shell32: requests of the bounded serving record")
@@ -77,7 +77,7 @@ def parse():
     ap.add_argument("--serve-workers", type=int, default=4, help="serve: worker threads (streams)")
     args = ap.parse_args()
     if args.symmetry is None:
-        args.symmetry = 1 if args.workload == "shell32" else 0
+        args.symmetry = 1 if args.workload in ("shell32", "serve") else 0
     return args
 
 
