@@ -3,6 +3,7 @@
 code they were taken on (bench.py reports their DRAM traffic only while it matches)."""
 import os
 import re
+import sys
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 KERNEL_SUMMARIES = ("translate_tc_fp16x3_shell16.md", "translate_tc_fp16x3_shell32.md",
@@ -24,3 +25,15 @@ def test_kernel_summaries_record_code_digest_and_traffic():
         text = open(os.path.join(ROOT, "profiles", name)).read()
         assert re.search(r"^kernel_code_sha256_16: [0-9a-f]{16}$", text, re.M), name
         assert re.search(r"^traffic_bytes_per_launch: [0-9]+$", text, re.M), name
+
+
+def test_kernel_summaries_match_the_current_kernel_code():
+    """Every kernel summary was taken on the kernel code as committed: bench.py reads its
+    traffic (a stale summary would silently report none)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    source = {"translate_tc": "translate_tc.cu", "translate_simt": "translate_simt.cu", "cvfcnn_tc": "cvfcnn_tc.cu"}
+    for name in KERNEL_SUMMARIES:
+        src = [v for k, v in source.items() if name.startswith(k)]
+        assert len(src) == 1, name
+        assert bench.profiled_traffic(name, src[0]) is not None, name
