@@ -4,8 +4,10 @@
 // by every pair of the group), so each group is one dense complex GEMM
 //     Y[:, dst_p] += G_d X[:, src_p]   for the pairs p of the group,
 // with M = K = 192 and N = pairs x rhs.  A work item is one group's run of at most
-// 64 columns; one CTA computes its full 192 x 64 output tile over K = 192 in chunks
-// of 16 (cp.async double buffering) and scatter-adds the tile into the target boxes.
+// 64 columns (with the symmetry-compressed store: a run of columns over all the groups
+// that share one stored block); one CTA computes its full 192 x 64 output tile over
+// K = 192 in chunks of 16 (cp.async double buffering) and scatter-adds the tile into
+// the target boxes.
 //
 // Accuracy: each tile sums 192 complex products in FP32 registers.  Contributions
 // of different displacements meet in one of kSlabs FP32 partial fields (slab =
