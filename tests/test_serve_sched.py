@@ -183,3 +183,54 @@ def test_stepped_cycle_cap_and_failures():
     by = {r.rid: r for r in done}
     assert by[0].status == ie.IE_ERR_NOT_CONVERGED
     assert "plan creation failed" in by[1].error and srv.used == 0
+
+
+# ------------------------------------------------------------------ shared stores
+class _FakeStore:
+    """Stands in for ie.Store (no device memory): keeps its spec and a byte count."""
+
+    def __init__(self, spec):
+        self.spec = spec
+        self.info = {"bytes": 1000 * spec.max_disp}
+        self.closed = False
+
+    def close(self):
+        self.closed = True
+
+
+def _reach_problem(reach, k=1.0):
+    return SimpleNamespace(k=k, eta=2.0, a=0.25, box_ijk=np.array([[0, 0, 0], [reach, 1, 0]]))
+
+
+def test_shared_store_grows_in_steps_of_eight_and_counts_against_the_budget(monkeypatch):
+    """One store per (k, eta, a), reused while it reaches far enough, replaced by one of
+    larger reach (rounded up to a multiple of 8 boxes) when a scatterer reaches farther;
+    every store made counts against the budget (a replaced one may still be held by
+    plans attached to it)."""
+    monkeypatch.setattr(S.ie, "Store", _FakeStore)
+    srv = S.Server([ie.IE_PREC_FP16X3], None, budget=10 ** 9, workers=1, symmetry=1)
+    try:
+        assert srv.share
+        s1 = srv.store_for(_reach_problem(5))
+        assert s1.spec.max_disp == 8 and srv.store_bytes == srv.used == 8000
+        assert srv.store_for(_reach_problem(8)) is s1
+        s2 = srv.store_for(_reach_problem(9))
+        assert s2.spec.max_disp == 16 and s1.closed and not s2.closed
+        assert srv.store_bytes == srv.used == 8000 + 16000 and srv.peak_used == 24000
+        s3 = srv.store_for(_reach_problem(3, k=2.0))
+        assert s3 is not s2 and s3.spec.max_disp == 8 and len(srv.stores) == 2
+    finally:
+        srv.close()
+    assert s2.closed and s3.closed and not srv.stores
+
+
+def test_prepare_stores_makes_one_store_of_the_largest_reach(monkeypatch):
+    monkeypatch.setattr(S.ie, "Store", _FakeStore)
+    srv = S.Server([ie.IE_PREC_FP16X3], None, budget=10 ** 9, workers=1, symmetry=1)
+    try:
+        srv.prepare_stores([_reach_problem(r) for r in (4, 17, 9)])
+        (st,) = srv.stores.values()
+        assert st.spec.max_disp == 24
+        assert srv.store_for(_reach_problem(17)) is st
+    finally:
+        srv.close()
