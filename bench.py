@@ -188,6 +188,17 @@ def shell32_config(symmetry: int = 0, world: int = 1) -> dict:
             "parallelism": "replicas" if world > 1 else "single"}
 
 
+def shell16_config(ie, symmetry: int = 0, world: int = 1, workload: str = WORKLOAD) -> dict:
+    """`config` of the shell16 line, shared by both arms."""
+    hp = solve_paths(ie)[HEADLINE]
+    return {"workload": workload, "path": HEADLINE, "path_desc": hp["desc"], "tol": hp["opts"]["tol"],
+            "nrhs": 1, "symmetry": symmetry,
+            "l2": ("no flush needed: each product streams >= 4.9 GB of coupling blocks (> 129 MB L2)"
+                   if not symmetry else
+                   "symmetry-compressed store (473 blocks, 139 MB); inputs and slabs are rewritten each product"),
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def oracle_sample_time(p, nboxes: int, seed_c: int, seed_sub: int, reps: int = 1):
     """Wall time of the FP64 brute-force oracle product (near + far) on `nboxes` seeded
     target boxes; the median of `reps` runs."""
@@ -239,7 +250,11 @@ def run_reference(args):
     sample = (f"each step: brute-force FP64 oracle product (near + far, site pair by site pair) on {len(targets)} of "
               f"{p.n_boxes} target boxes ({1e3 * t_step:.0f} ms); value extrapolated: x {p.n_boxes / len(targets):.0f} "
               f"to a full product, x {prods} products (the oracle's own GMRES(50) on this system to {tol:g})")
-    config = shell32_config() if name == "shell32" else {"workload": WORKLOAD}
+    if name == "shell32":
+        config = shell32_config(args.symmetry, world)
+    else:
+        import paper_2501_04684_gb300 as ie
+        config = shell16_config(ie, args.symmetry, world)
     line = {"impl": "reference", "metric": METRIC, "value": solves_per_s, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -433,12 +448,7 @@ def run_shell16(ctx):
         "metric": METRIC, "value": head["solves_per_s"], "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": hp["dtype"], "data": "synthetic",
-        "config": {"workload": workload, "path": HEADLINE, "path_desc": hp["desc"], "tol": hp["opts"].tol,
-                   "nrhs": 1, "symmetry": args.symmetry,
-                   "l2": ("no flush needed: each product streams >= 4.9 GB of coupling blocks (> 129 MB L2)"
-                          if not args.symmetry else
-                          "symmetry-compressed store (473 blocks, 139 MB); inputs and slabs are rewritten each product"),
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": shell16_config(ie, args.symmetry, world, workload),
         "solve": {k: head[k] for k in ("p50_ms", "p99_ms", "iterations", "matvecs", "refinements", "relres")},
         "vs_plain_fp32": head["solves_per_s"] / others["plain"]["solves_per_s"],
         "paths": {name: {k: r[k] for k in ("solves_per_s", "p50_ms", "p99_ms", "iterations", "matvecs", "refinements",
