@@ -30,7 +30,9 @@
  *    call returns an ie_status, and ie_last_error() gives a message for the
  *    calling thread's last failure.
  *  - Calls on one plan must not overlap in time on different streams (the plan's
- *    scratch vectors are shared); distinct plans are independent.
+ *    scratch vectors are shared), nor come from several host threads at once (its
+ *    work-list and solver caches are unlocked); distinct plans are independent, and
+ *    plans, solvers and stores may be created and destroyed from any host thread.
  */
 #ifndef IE_H_
 #define IE_H_
