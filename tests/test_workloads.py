@@ -37,3 +37,40 @@ def test_every_bench_variant_has_its_frozen_alpha():
     """bench.py --lfb lfb8|lfb256 and --mapped solve systems whose alpha make_alpha.py froze."""
     for name in ["shell16", "shell32"] + [f"shell16_{t}" for t in W.LFB_EDGES] + ["shell16_mapped"]:
         assert W.alpha_for(name) > 0, name
+
+
+def _displacement_counts(p):
+    """{d: pairs of boxes (b, b + d)} of a scatterer, by the autocorrelation of its box
+    occupancy (FFT on a grid twice the size, so no displacement wraps around)."""
+    G = p.G
+    occ = np.zeros((2 * G,) * 3)
+    ijk = np.asarray(p.box_ijk)
+    occ[ijk[:, 0], ijk[:, 1], ijk[:, 2]] = 1.0
+    f = np.fft.rfftn(occ)
+    ac = np.rint(np.fft.irfftn(f * np.conj(f), s=occ.shape, axes=(0, 1, 2))).astype(np.int64)
+    out = {}
+    r = range(-G + 1, G)
+    for dx in r:
+        for dy in r:
+            for dz in r:
+                c = ac[dx % (2 * G), dy % (2 * G), dz % (2 * G)]
+                if c:
+                    out[(dx, dy, dz)] = int(c)
+    return out
+
+
+def test_shell_workload_counts():
+    """The shells' box, far-pair, displacement-group, canonical-block and adjacent-pair
+    counts (stated with the workloads and checked on the plans in the GPU tests), from the
+    occupancy alone: far = Chebyshev distance >= 2, canonical block = sorted abs(d)."""
+    want = {"shell16": (1264, 1575248, 16540, 473, 21184), "shell32": (5000, 24910952, 112160, 2780, None)}
+    for name, (boxes, pairs, groups, canon, adjacent) in want.items():
+        p = getattr(W, name)()
+        counts = _displacement_counts(p)
+        far = {d: c for d, c in counts.items() if max(map(abs, d)) >= 2}
+        assert len(p.box_ijk) == boxes
+        assert sum(far.values()) == pairs and len(far) == groups
+        assert len({tuple(sorted(map(abs, d))) for d in far}) == canon
+        if adjacent is not None:
+            near = sum(c for d, c in counts.items() if 0 < max(map(abs, d)) <= 1)
+            assert near == adjacent
