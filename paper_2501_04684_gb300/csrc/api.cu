@@ -488,8 +488,7 @@ ie_status generate_blocks(double k, double eta, double a, const int32_t *d_disp,
 bool block_prec_only(unsigned mask) { return !wants_cvfcnn(mask); }
 
 ie_status work_list_for(ie_plan p, int prec, int nrhs, WorkList **out) {
-    if (prec == IE_PREC_FP32) return work_list(p, false, nrhs, out, 0, /*pack=*/true);
-    if (prec == IE_PREC_CVFCNN_FP32) return work_list(p, false, nrhs, out);
+    if (prec == IE_PREC_FP32 || prec == IE_PREC_CVFCNN_FP32) return work_list(p, false, nrhs, out, 0, /*pack=*/true);
     if (prec == IE_PREC_CVFCNN) return work_list(p, true, nrhs, out, cvfcnn_tc_tile_columns(), /*pack=*/true);
     return work_list(p, true, nrhs, out, 0, /*pack=*/true);
 }

@@ -297,9 +297,15 @@ struct SmemCv {
     float inv[kTileN];
 };
 
+// Symmetry-compressed store: the network of displacement d is the stored block's
+// network in the frame of d, so a column reads the signed-permuted input copy Q of its
+// group and adds output row u at U_Q(u).  Items are packed: an item's columns may come
+// from every group of one stored block (pgroup: the group of each pair), each with its
+// own copy, slab and output map.
 struct SymArgs {
     const int32_t *gcanon = nullptr;     // [disp] stored block (null: no symmetry)
     const int32_t *gsigma = nullptr;     // [disp] copy Q of the input
+    const int32_t *pgroup = nullptr;     // [pair] group of the pair (packed items)
     const uint16_t *map = nullptr;       // [48][192]
     size_t stride = 0;                   // complex elements between input copies
 };
@@ -315,15 +321,20 @@ cvfcnn_translate_kernel(const WorkItem *__restrict__ items, const float2 *__rest
     const WorkItem it = items[blockIdx.x];
     const int tid = threadIdx.x;
     const int ncols = it.npairs * it.nr;
-    const int sigma = sy.gcanon ? sy.gsigma[it.disp] : 0;
     const float2 *Wb = Wall + (size_t)(sy.gcanon ? sy.gcanon[it.disp] : it.disp) * kCvBlockElems;
-    if (sy.gcanon) X += (size_t)sigma * sy.stride;
+    auto group_of = [&](int pair) { return sy.pgroup ? __ldg(sy.pgroup + pair) : it.disp; };
+    // input of column col (its pair's source box, right-hand side and input copy)
+    auto column_input = [&](int col) {
+        const int pair = it.pair0 + col / it.nr;
+        const float2 *x = X + ((int64_t)(col % it.nr) * nbox + src[pair]) * kNU;
+        return sy.gcanon ? x + (size_t)__ldg(sy.gsigma + group_of(pair)) * sy.stride : x;
+    };
 
     // column scales: 4 threads per column, 48 entries each
     {
         const int c = tid >> 2, qq = tid & 3;
         const int cc = c < ncols ? c : 0;
-        const float2 *xc = X + ((int64_t)(cc % it.nr) * nbox + src[it.pair0 + cc / it.nr]) * kNU;
+        const float2 *xc = column_input(cc);
         float m = 0.f;
         for (int u = qq; u < kNU; u += 4) {
             const float2 x = xc[u];
@@ -342,7 +353,7 @@ cvfcnn_translate_kernel(const WorkItem *__restrict__ items, const float2 *__rest
     const int lcol = tid & (kTileN - 1);
     const int lkq = tid >> 6;
     const int lc = lcol < ncols ? lcol : 0;
-    const float2 *xcol = X + ((int64_t)(lc % it.nr) * nbox + src[it.pair0 + lc / it.nr]) * kNU;
+    const float2 *xcol = column_input(lc);
     auto load1 = [&](int kc, int buf) {
         const float4 *gw = reinterpret_cast<const float4 *>(Wb + kCvW1 + (size_t)kc * kKC * kCvHp);
         float4 *sw = reinterpret_cast<float4 *>(&S.u.s1.W[buf][0][0]);
@@ -471,8 +482,7 @@ cvfcnn_translate_kernel(const WorkItem *__restrict__ items, const float2 *__rest
         __syncthreads();
     }
 
-    // output bias, rescale, scatter-add into slab (disp mod kSlabs)
-    float2 *Ys = Yslab + (size_t)(it.disp % kSlabs) * slab_stride;
+    // output bias, rescale, scatter-add into the slab of the column's group (group mod kSlabs)
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int col = 2 * tn + 16 * (j >> 1) + (j & 1);
@@ -486,11 +496,13 @@ cvfcnn_translate_kernel(const WorkItem *__restrict__ items, const float2 *__rest
         }
         const int pair = it.pair0 + col / it.nr;
         const int r = col % it.nr;
-        float2 *ycol = Ys + ((int64_t)r * nbox + dst[pair]) * kNU;
+        const int grp = group_of(pair);
+        float2 *ycol = Yslab + (size_t)(grp % kSlabs) * slab_stride + ((int64_t)r * nbox + dst[pair]) * kNU;
         if (sy.gcanon) {
+            const uint16_t *map = sy.map + __ldg(sy.gsigma + grp) * kNU;
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
-                const uint16_t e = sy.map[sigma * kNU + 2 * tm + 64 * (i >> 1) + (i & 1)];
+                const uint16_t e = __ldg(map + 2 * tm + 64 * (i >> 1) + (i & 1));
                 const float sg = (e & 0x100) ? -1.f : 1.f;
                 atomicAdd(ycol + (e & 0xFF), make_float2(sg * o[i].x, sg * o[i].y));
             }
@@ -598,6 +610,7 @@ ie_status launch_translate_cvfcnn(ie_plan p, const float2 *X, float2 *Yslab, int
         X = p->d_Xsym;
         sy.gcanon = p->d_gcanon;
         sy.gsigma = p->d_gsigma;
+        sy.pgroup = p->d_pgroup;
         sy.map = p->d_symmap;
         sy.stride = (size_t)nrhs * p->nbox * kNU;
     }
