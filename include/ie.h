@@ -451,6 +451,25 @@ ie_status ie_map_basis(const ie_mapping_spec *spec, int64_t n_fun, const int64_t
                        const double *pos, const double *mom, double *P, double *residual,
                        void *stream);
 
+/* ---- Symmetry of the translation matrices (§2.2), host only ------------------------ */
+
+/* Canonical displacement c = sorted |d| (c[0] <= c[1] <= c[2]) of a box displacement d,
+ * and the index q (0..47) of a signed axis permutation Q with d = Q c:
+ *     q = 8 p + s,   (Q c)_i = (-1)^(bit i of s) c[perm_p(i)],
+ *     perm_0..perm_5 = (0,1,2), (0,2,1), (1,0,2), (1,2,0), (2,0,1), (2,1,0);
+ * a zero component has its sign bit clear, and when components of |d| are equal one of
+ * the permutations that fit is returned.  d, c: HOST, 3 int32 each.  No device call.
+ * Errors: IE_ERR_INVALID for a null pointer. */
+ie_status ie_sym_canon(const int32_t *d, int32_t *c, int32_t *q);
+
+/* Unknown map of the 48 signed permutations, the table the symmetry-compressed store and
+ * the translation epilogues use: map[q * 192 + u] = U_q(u), with 0x100 added when the
+ * unknown changes sign, such that for d = Q c (Q of index q)
+ *     G_d[U_q(u)][U_q(v)] = sign_q(u) sign_q(v) G_c[u][v]
+ * (unknown u = 3 site + component, eq. 13).  map: HOST, 48 x 192 uint16.  No device
+ * call.  Errors: IE_ERR_INVALID for a null pointer. */
+ie_status ie_sym_map(uint16_t *map);
+
 /* ---- CVFCNN surrogates (§3) ------------------------------------------------------ */
 
 /* Displacements of the stored far blocks, in the plan's block order (the canonical

@@ -36,6 +36,7 @@ EXPORTED = [
     "ie_cvfcnn_train",
     "ie_cvfcnn_train_opts_default", "ie_store_footprint", "ie_store_create", "ie_store_info", "ie_store_release",
     "ie_plan_create_shared", "ie_plan_footprint_shared", "ie_solver_state", "ie_diag_wait_limit",
+    "ie_sym_canon", "ie_sym_map",
 ]
 
 
@@ -156,6 +157,8 @@ def lib() -> ctypes.CDLL:
     L.ie_plan_tune.argtypes = [vp, i, i, P(ie_tune_info), vp]
     L.ie_map_basis.argtypes = [P(ie_mapping_spec), ctypes.c_int64, vp, vp, vp, vp, vp, vp]
     L.ie_plan_blocks.argtypes = [vp, vp]
+    L.ie_sym_canon.argtypes = [vp, vp, P(ctypes.c_int32)]
+    L.ie_sym_map.argtypes = [vp]
     L.ie_cvfcnn_set_weights.argtypes = [vp, vp, vp, vp, vp, vp]
     L.ie_cvfcnn_get_weights.argtypes = [vp, vp, vp, vp, vp, vp]
     L.ie_cvfcnn_train_opts_default.argtypes = [P(ie_cvfcnn_train_opts)]
@@ -408,6 +411,23 @@ def ie_plan_blocks(plan) -> np.ndarray:
     n = int(ie_plan_stats_get(plan)["n_coupling_blocks"])
     out = np.zeros((n, 3), dtype=np.int32)
     _check(lib().ie_plan_blocks(plan, out.ctypes.data), "ie_plan_blocks")
+    return out
+
+
+def ie_sym_canon(d) -> tuple[np.ndarray, int]:
+    """(c, q): the canonical displacement sorted |d| and the signed permutation index
+    with d = Q c (host only)."""
+    dd = np.ascontiguousarray(d, dtype=np.int32).reshape(3)
+    c = np.zeros(3, dtype=np.int32)
+    q = ctypes.c_int32()
+    _check(lib().ie_sym_canon(dd.ctypes.data, c.ctypes.data, ctypes.byref(q)), "ie_sym_canon")
+    return c, int(q.value)
+
+
+def ie_sym_map() -> np.ndarray:
+    """(48, 192) uint16: U_q(u), plus 0x100 where the unknown changes sign (host only)."""
+    out = np.zeros((48, 192), dtype=np.uint16)
+    _check(lib().ie_sym_map(out.ctypes.data), "ie_sym_map")
     return out
 
 

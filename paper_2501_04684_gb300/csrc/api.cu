@@ -929,6 +929,20 @@ static ie_status plan_create(const ie_problem *pr, ie_store store, void *stream,
 
 extern "C" {
 
+ie_status ie_sym_canon(const int32_t *d, int32_t *c, int32_t *q) {
+    if (!d || !c || !q) return set_error("null argument"), IE_ERR_INVALID;
+    *q = canon_of_disp(d, c);
+    return IE_OK;
+}
+
+ie_status ie_sym_map(uint16_t *out) {
+    if (!out) return set_error("null argument"), IE_ERR_INVALID;
+    std::vector<uint16_t> map;
+    symmetry_map_host(map);
+    std::copy(map.begin(), map.end(), out);
+    return IE_OK;
+}
+
 ie_status ie_plan_create(const ie_problem *pr, void *stream, ie_plan *out) {
     std::lock_guard<std::recursive_mutex> lock(device_mutex());
     return plan_create(pr, nullptr, stream, out);
