@@ -7,7 +7,6 @@ fixed scratch area keeps the previous call's partial sums and must be cleared by
 each call.  This file is collected last so that a stop-at-first-failure run has
 already run every other test.
 """
-import numpy as np
 import pytest
 
 import paper_2501_04684_gb300 as ie
