@@ -185,3 +185,23 @@ def test_store_footprint_host_only(built):
             ie.ie_store_footprint(ie.store_spec(kw["k"], kw["eta"], kw["a"], kw["max_disp"], kw["prec_mask"],
                                                 lattice=lattice))
         assert e.value.status == ie.IE_ERR_INVALID
+
+
+def test_binding_refuses_host_buffers():
+    """The binding hands the library device buffers only: a numpy array or a CPU tensor is
+    refused before any library call (there is no CPU path)."""
+    import torch
+    with pytest.raises(TypeError):
+        ie._need(np.zeros(4, dtype=np.complex64), 4, "x")
+    with pytest.raises(TypeError):
+        ie._need(torch.zeros(4, dtype=torch.complex64), 4, "x")
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libie.so every call raises: nothing falls back to another implementation."""
+    monkeypatch.setattr(ie, "_lib", None)
+    monkeypatch.setattr(ie, "LIB_PATH", str(tmp_path / "libie.so"))
+    with pytest.raises(ImportError):
+        ie.lib()
+    with pytest.raises(ImportError):
+        ie.ie_sym_map()
