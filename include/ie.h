@@ -30,11 +30,10 @@
  *    call returns an ie_status, and ie_last_error() gives a message for the
  *    calling thread's last failure.
  *  - Errors common to every entry point (each declaration lists its others):
- *    IE_ERR_INVALID for a null handle or pointer argument, an nrhs outside
- *    [1, the plan's max_rhs], a precision the plan was not prepared for or another
- *    argument outside its stated range, detected before any device work;
- *    IE_ERR_UNSUPPORTED for an option the plan does not hold (its store, its
- *    surrogates); IE_ERR_OOM when a device allocation fails; IE_ERR_CUDA when a CUDA
+ *    IE_ERR_INVALID for a null handle or pointer argument, an unknown precision, an
+ *    nrhs outside [1, the plan's max_rhs] or another argument outside its stated
+ *    range, detected before any device work; IE_ERR_UNSUPPORTED for a precision the
+ *    plan was not prepared for or an option it does not hold; IE_ERR_OOM when a device allocation fails; IE_ERR_CUDA when a CUDA
  *    call or launch fails; IE_ERR_TIMEOUT (tensor-core translations, reported by
  *    ie_plan_check and ie_solve) when a bounded device wait gave up.  The destroy and
  *    release calls accept NULL and return IE_OK.
