@@ -74,3 +74,18 @@ def test_shell_workload_counts():
         if adjacent is not None:
             near = sum(c for d, c in counts.items() if 0 < max(map(abs, d)) <= 1)
             assert near == adjacent
+
+
+def test_frozen_alphas_stay_above_the_longer_sigma_estimates():
+    """The longer power iterations recorded beside the frozen alphas (make_alpha.py --check)
+    start from the same seed, so they reproduce the frozen histories; alpha stays above
+    their sigma, which keeps Z = alpha I + K nonsingular with GMRES contracting by sigma/alpha."""
+    import json
+    import os
+    table = json.load(open(os.path.join(os.path.dirname(W.__file__), "alpha.json")))
+    for name in ("shell16", "shell32"):
+        e = table[name]
+        h, hc = e["history"], e["history_check"]
+        assert len(hc) > len(h) and np.allclose(hc[:len(h)], h, rtol=1e-9, atol=0)
+        assert np.all(np.diff(hc) > 0) and e["sigma_check"] == hc[-1]
+        assert e["alpha"] == W.alpha_for(name) and e["alpha"] / e["sigma_check"] > 1.15
